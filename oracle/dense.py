@@ -1,0 +1,141 @@
+"""Dense global-matrix definitions for tiny chains (FP64 numpy).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring). These routines write the
+paper's global matrix equations out literally, with library dense solves as the
+only steps, so that the C oracle's recursions can be checked against them:
+
+* Eq. 2a-2d: (I - Gamma) V = S qd + c_V, (I - Gamma) Vd = S qdd - ad_{S qd}(Gamma V)
+  + c_Vd, (I - Gamma)^T F = J Vd - ad_V^T (J V), tau = S^T F. The sign of the
+  ad term is the reading in which it equals ad_{V_i}(S_i qd_i) link by link
+  (Eq. 1 and Eq. 2b disagree on the sign convention of ad).
+* Eq. 3 (definition after Eq. eq-motion): M(q) = S^T (I-Gamma)^{-T} J (I-Gamma)^{-1} S.
+* Eq. cfa-eq2 and Eq. fijany-final: T = (I-Gamma) J^{-1} (I-Gamma)^T,
+  A = W^T T W, B = W^T T S, C = S^T T S, M^{-1} = C - B^T A^{-1} B.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _skew(v):
+    return np.array([[0.0, -v[2], v[1]], [v[2], 0.0, -v[0]], [-v[1], v[0], 0.0]])
+
+
+def _rot(a, q):
+    K = _skew(a)
+    return np.eye(3) + np.sin(q) * K + (1.0 - np.cos(q)) * (K @ K)
+
+
+def _Ad(R, p):
+    A = np.zeros((6, 6))
+    A[:3, :3] = R
+    A[3:, 3:] = R
+    A[3:, :3] = _skew(p) @ R
+    return A
+
+
+def _ad(V):
+    A = np.zeros((6, 6))
+    A[:3, :3] = _skew(V[:3])
+    A[3:, 3:] = _skew(V[:3])
+    A[3:, :3] = _skew(V[3:])
+    return A
+
+
+def link_operators(model, q):
+    """Per link: X_i = Ad_{g_{i-1,i}(q_i)^{-1}} and S_i = (a_i; 0)."""
+    n = model.axes.shape[0]
+    X, S = [], []
+    for i in range(n):
+        fr = model.frames[i]
+        R = fr[:9].reshape(3, 3) @ _rot(model.axes[i], q[i])
+        p = fr[9:]
+        X.append(_Ad(R.T, -R.T @ p))
+        S.append(np.concatenate([model.axes[i], np.zeros(3)]))
+    return X, S
+
+
+def global_matrices(model, q):
+    """Gamma (6n x 6n, block sub-diagonal X_i), S (6n x n), J (6n x 6n)."""
+    n = model.axes.shape[0]
+    X, S = link_operators(model, q)
+    G = np.zeros((6 * n, 6 * n))
+    Sg = np.zeros((6 * n, n))
+    Jg = np.zeros((6 * n, 6 * n))
+    for i in range(n):
+        if i > 0:
+            G[6 * i:6 * i + 6, 6 * (i - 1):6 * i] = X[i]
+        Sg[6 * i:6 * i + 6, i] = S[i]
+        Jg[6 * i:6 * i + 6, 6 * i:6 * i + 6] = model.inertias[i].reshape(6, 6)
+    return G, Sg, Jg, X
+
+
+def mass_matrix(model, q):
+    """Eq. 3's definition M = S^T (I-Gamma)^{-T} J (I-Gamma)^{-1} S."""
+    G, S, J, _ = global_matrices(model, q)
+    I = np.eye(G.shape[0])
+    Y = np.linalg.solve(I - G, S)
+    return Y.T @ J @ Y
+
+
+def inverse_dynamics(model, q, qd, qdd, gravity=None):
+    """Eq. 2a-2d as dense linear systems; the base terms enter the first block."""
+    g = model.gravity if gravity is None else np.asarray(gravity)
+    G, S, J, X = global_matrices(model, q)
+    n = S.shape[1]
+    I = np.eye(6 * n)
+    V = np.linalg.solve(I - G, S @ qd)
+    GV = G @ V
+    Sqd = S @ qd
+    adterm = np.zeros(6 * n)
+    for i in range(n):
+        adterm[6 * i:6 * i + 6] = -_ad(Sqd[6 * i:6 * i + 6]) @ GV[6 * i:6 * i + 6]
+    c = np.zeros(6 * n)
+    c[:6] = X[0] @ np.concatenate([np.zeros(3), -g])
+    Vd = np.linalg.solve(I - G, S @ qdd + adterm + c)
+    rhs = J @ Vd
+    for i in range(n):
+        Vi = V[6 * i:6 * i + 6]
+        Ji = J[6 * i:6 * i + 6, 6 * i:6 * i + 6]
+        rhs[6 * i:6 * i + 6] -= _ad(Vi).T @ (Ji @ Vi)
+    F = np.linalg.solve((I - G).T, rhs)
+    return S.T @ F
+
+
+def projection(model, rng=None):
+    """Block-diagonal W (6n x 5n) with W_i^T S_i = 0; random orthonormal W_i if
+    ``rng`` is given, else a deterministic orthonormal complement."""
+    n = model.axes.shape[0]
+    W = np.zeros((6 * n, 5 * n))
+    Wb = np.zeros((n, 6, 5))
+    for i in range(n):
+        a = model.axes[i]
+        Q, _ = np.linalg.qr(np.column_stack([a, np.eye(3)]))
+        b, c = Q[:, 1], Q[:, 2]
+        Wi = np.zeros((6, 5))
+        Wi[:3, 0], Wi[:3, 1] = b, c
+        Wi[3:, 2:] = np.eye(3)
+        if rng is not None:
+            Z, _ = np.linalg.qr(rng.standard_normal((5, 5)))
+            Wi = Wi @ Z
+        W[6 * i:6 * i + 6, 5 * i:5 * i + 5] = Wi
+        Wb[i] = Wi
+    return W, Wb
+
+
+def cfa_matrices(model, q, W=None):
+    """T, A, B, C (Eq. cfa-eq2, Eq. fijany-final) with the given W (dense)."""
+    G, S, J, _ = global_matrices(model, q)
+    if W is None:
+        W, _ = projection(model)
+    I = np.eye(G.shape[0])
+    T = (I - G) @ np.linalg.inv(J) @ (I - G).T
+    return dict(T=T, A=W.T @ T @ W, B=W.T @ T @ S, C=S.T @ T @ S, W=W, S=S)
+
+
+def fd_cfa(model, q, qd, tau, W=None):
+    """qdd = C tau_d + B^T F_c with A F_c = -B tau_d (Eq. cfa-eq2, dense solve)."""
+    m = cfa_matrices(model, q, W)
+    td = tau - inverse_dynamics(model, q, qd, np.zeros_like(q))
+    Fc = np.linalg.solve(m["A"], -m["B"] @ td)
+    return m["C"] @ td + m["B"].T @ Fc
