@@ -1,0 +1,175 @@
+/*
+ * fd_gb300.h -- C ABI of the GB300 forward-dynamics library.
+ *
+ * Forward dynamics qdd = FD(q, qdot, tau) of serial chains of revolute joints by
+ * the three factorisations of M(q)^{-1} compared in Yang, Wu & Pan (arXiv
+ * 1609.06779): ABIA (Section II-C), JSIIA (Section II-C) and CFA (Section III,
+ * Algorithm 1, with the block tri-diagonal system solved by odd-even elimination,
+ * Section IV, Algorithm 2). Every algorithm first computes the bias torque by
+ * inverse dynamics (Eq. 2a-2d with qdd = 0, Eq. 4) and works on
+ * tau_delta = tau - tau_bias.
+ *
+ * Conventions (fixed by this library; the paper leaves them open):
+ *   twist V = (omega; v), wrench F = (n; f), both in the link's own frame;
+ *   joint i joins link i-1 to link i (link 0 of a chain is attached to the fixed
+ *   base): g_{i-1,i}(q_i) = (R0_i, p0_i) * exp([a_i; 0] q_i), S_i = (a_i; 0);
+ *   gravity enters as the base acceleration (0; -g), g given in the base frame;
+ *   no external wrench at the tip.
+ *
+ * Memory: arrays documented as "host" are read during the call and not retained.
+ * Arrays documented as "device" must be device memory of the chain set's device.
+ * Solves are asynchronous on the given CUDA stream (NULL = legacy default stream).
+ * Errors: every call returns an fd_status; fd_last_error() returns a message
+ * for the calling thread's last failing call. Arguments are validated before any
+ * launch; numerical failures of a problem (a non-positive pivot, a non-finite
+ * result) are written to the optional per-problem status array on the device.
+ * There is no CPU fallback: without a usable CUDA device calls that need one
+ * return FD_ERR_CUDA.
+ */
+#ifndef FD_GB300_H
+#define FD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FD_ABI_VERSION 1
+
+typedef struct fd_chain_s *fd_chain_t; /* a set of serial chains resident on one GPU */
+typedef struct fd_batch_s *fd_batch_t; /* a batch plan: which chain each problem uses */
+
+typedef enum fd_algo {
+  FD_ABIA = 0,  /* articulated-body inertia factorisation (Section II-C) */
+  FD_JSIIA = 1, /* joint-space inertia by ID columns + Cholesky (Section II-C) */
+  FD_CFA = 2    /* constraint force algorithm with OEE (Section III, Alg. 1-2) */
+} fd_algo;
+
+typedef enum fd_prec {
+  FD_FP64 = 0,  /* states and all arithmetic in double */
+  FD_FP32 = 1,  /* states and all arithmetic in float */
+  FD_MIXED = 2  /* float states and arithmetic; the OEE elimination, the
+                   articulated-inertia recursion and the JSIIA Cholesky in double */
+} fd_prec;
+
+typedef enum fd_status {
+  FD_OK = 0,
+  FD_ERR_INVALID_ARG = 1, /* bad pointer, size, shape or model (nothing launched) */
+  FD_ERR_NOT_SPD = 2,     /* a pivot that must be positive was not */
+  FD_ERR_OOM = 3,         /* device allocation failed */
+  FD_ERR_CUDA = 4,        /* a CUDA runtime call failed or no device */
+  FD_ERR_TIMEOUT = 5,     /* a bounded wait ran out */
+  FD_ERR_NUMERIC = 6,     /* a non-finite result */
+  FD_ERR_BUSY = 7,        /* the request cannot be admitted now; retry */
+  FD_ERR_UNSUPPORTED = 8  /* combination of options not built */
+} fd_status;
+
+/* Message of the calling thread's last failing call ("" if none). The pointer
+ * stays valid until the next call on this thread. */
+const char *fd_last_error(void);
+
+/* FD_ABI_VERSION of the loaded library. */
+int32_t fd_abi_version(void);
+
+/*
+ * fd_create_chain -- copy a set of chains to the device.
+ *
+ * The problem statement of Algorithm 1 (inputs tau, q, qdot; model J_i and the
+ * joints' twists and frames). Chain k owns links link_offsets[k] ..
+ * link_offsets[k+1]-1 of the packed host arrays:
+ *   joint_axes       [L][3]  joint axis a_i in child frame i (normalised here;
+ *                            a zero axis is FD_ERR_INVALID_ARG)
+ *   link_frames      [L][12] home transform parent -> child: R row-major (9),
+ *                            then p (3); R must be a rotation (|R^T R - I| < 1e-9)
+ *   spatial_inertias [L][36] 6x6 spatial inertia J_i of link i at the origin of
+ *                            frame i, (omega; v) order; symmetric positive
+ *                            definite (Eq. 1), else FD_ERR_INVALID_ARG
+ *   gravity          [3]     gravity vector in the base frame (e.g. 0, 0, -9.81)
+ * n_chains >= 0; link_offsets [n_chains+1] non-decreasing from 0; a chain may
+ * have zero links. All arrays are host memory and are not retained. The model is
+ * re-expressed in link frames whose x axis is the joint axis (q-independent;
+ * qdd does not depend on the choice of link frames) and stored in double and
+ * float copies on `device`. Ownership of *out passes to the caller; free it
+ * with fd_destroy_chain.
+ */
+fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets,
+                          const double *joint_axes, const double *link_frames,
+                          const double *spatial_inertias, const double gravity[3],
+                          int32_t device, fd_chain_t *out);
+
+fd_status fd_destroy_chain(fd_chain_t chain);
+
+/* Number of chains, total links and the longest chain's link count. */
+fd_status fd_chain_info(fd_chain_t chain, int32_t *n_chains, int64_t *n_links,
+                        int32_t *max_links);
+
+/*
+ * fd_batch_create -- plan a batch of n_problems forward-dynamics problems.
+ *
+ * Problem p uses chain chain_index[p] of `chain` (host array, may be NULL: then
+ * n_problems must equal the number of chains and problem p uses chain p). The
+ * problems' joint states are packed in problem order: problem p occupies
+ * entries state_offset(p) .. state_offset(p) + n_p - 1 of every state array,
+ * where state_offset is the prefix sum of the problems' link counts. The plan
+ * holds device copies of this map and is reusable for any number of solves.
+ */
+fd_status fd_batch_create(fd_chain_t chain, int32_t n_problems, const int32_t *chain_index,
+                          fd_batch_t *out);
+
+fd_status fd_batch_destroy(fd_batch_t batch);
+
+/* Total state entries (sum of the problems' link counts) of a batch. */
+fd_status fd_batch_info(fd_batch_t batch, int32_t *n_problems, int64_t *n_state_links,
+                        int32_t *max_links);
+
+/*
+ * Threads that cooperate on one problem ("team"): 0 lets the library choose;
+ * otherwise a power of two from 1 (one thread per chain: serial recursions) to
+ * 32 (one warp per chain: warp-shuffle scans and OEE levels across lanes).
+ * FD_ABIA runs its articulated-inertia recursion serially (the paper notes it
+ * cannot be parallelised beyond a constant factor, Section III) and accepts only
+ * team 1 (or 0).
+ */
+
+/* Bytes of device workspace fd_solve_batch / fd_inverse_dynamics need for
+ * (algo, prec, team). For fd_inverse_dynamics pass algo = -1. */
+size_t fd_workspace_size(fd_batch_t batch, int32_t algo, fd_prec prec, int32_t team);
+
+/*
+ * fd_solve_batch -- qdd = FD(q, qdot, tau) for every problem of the batch.
+ *
+ * q, qdot, tau (inputs) and qddot (output) are device arrays of n_state_links
+ * elements, double for FD_FP64 and float for FD_FP32 / FD_MIXED, packed as
+ * fd_batch_create describes. workspace: device memory of at least
+ * fd_workspace_size(batch, algo, prec, team) bytes, 256-byte aligned, owned by
+ * the caller, contents need not be initialised and are garbage afterwards; it
+ * must not be shared by solves that overlap on the GPU. status: optional device
+ * int32 array [n_problems] receiving FD_OK, FD_ERR_NOT_SPD or FD_ERR_NUMERIC per
+ * problem (valid once the stream reaches that point). Enqueues work on `stream`
+ * (a cudaStream_t) and returns without synchronising. No device memory is
+ * allocated by this call.
+ */
+fd_status fd_solve_batch(fd_batch_t batch, const void *q, const void *qdot, const void *tau,
+                         void *qddot, fd_algo algo, fd_prec prec, int32_t team,
+                         void *workspace, size_t workspace_bytes, int32_t *status,
+                         void *stream);
+
+/*
+ * fd_inverse_dynamics -- tau = ID(q, qdot, qddot) with gravity (Eq. 2a-2d): the
+ * twist and acceleration recursions (forward, block bi-diagonal) and the force
+ * recursion (backward, transposed), each solved as a segmented prefix scan over
+ * composed SE(3)-affine operators (Section II-B). Arrays and workspace as for
+ * fd_solve_batch (workspace size: fd_workspace_size(batch, -1, prec, team));
+ * prec FD_MIXED is treated as FD_FP32.
+ */
+fd_status fd_inverse_dynamics(fd_batch_t batch, const void *q, const void *qdot,
+                              const void *qddot, void *tau, fd_prec prec, int32_t team,
+                              void *workspace, size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FD_GB300_H */

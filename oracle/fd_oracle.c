@@ -649,7 +649,9 @@ int orc_fd_batch(int algo, int n_problems, const int32_t *chain_of,
     int64_t m0 = model_offsets[c], s0 = state_offsets[p];
     int n = (int)(model_offsets[c + 1] - m0);
     int st;
-    if (algo == ORC_ALGO_CHOLESKY)
+    if (n == 0)
+      st = ORC_OK; /* an empty chain has nothing to solve */
+    else if (algo == ORC_ALGO_CHOLESKY)
       st = fd_cholesky_chain(n, axes + 3 * m0, frames + 12 * m0, J + 36 * m0, grav, q + s0,
                              qd + s0, tau + s0, qdd + s0);
     else if (algo == ORC_ALGO_ABA)
@@ -679,6 +681,7 @@ int orc_rnea_batch(int n_problems, const int32_t *chain_of, const int64_t *model
     int c = chain_of ? chain_of[p] : p;
     int64_t m0 = model_offsets[c], s0 = state_offsets[p];
     int n = (int)(model_offsets[c + 1] - m0);
+    if (n == 0) continue;
     rnea_chain(n, axes + 3 * m0, frames + 12 * m0, J + 36 * m0, grav, q + s0, qd + s0,
                qdd ? qdd + s0 : NULL, tau + s0);
   }

@@ -1,0 +1,515 @@
+// fd_abi.cu -- the C ABI declared in include/fd_gb300.h: model packing (chain
+// sets in canonical link frames), batch plans, argument validation and kernel
+// dispatch. Host code only; the arithmetic of the method runs in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/fd_gb300.h"
+#include "fd_launch.h"
+#include "fd_layout.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+fd_status fail(fd_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+fd_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? FD_ERR_OOM : FD_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+// packed symmetric 6x6 index (upper triangle row by row), as in the kernels
+constexpr int s6(int i, int j) {
+  return i <= j ? i * 6 - (i * (i - 1)) / 2 + (j - i) : j * 6 - (j * (j - 1)) / 2 + (i - j);
+}
+
+// Cholesky of a dense 6x6 (row-major); false if not positive definite.
+bool chol6(const double *A, double *L) {
+  std::memset(L, 0, 36 * sizeof(double));
+  for (int j = 0; j < 6; ++j) {
+    double d = A[6 * j + j];
+    for (int k = 0; k < j; ++k) d -= L[6 * j + k] * L[6 * j + k];
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    L[6 * j + j] = std::sqrt(d);
+    for (int i = j + 1; i < 6; ++i) {
+      double s = A[6 * i + j];
+      for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
+      L[6 * i + j] = s / L[6 * j + j];
+    }
+  }
+  return true;
+}
+
+void inv_from_chol6(const double *L, double *Ai) {
+  for (int c = 0; c < 6; ++c) {
+    double x[6] = {0, 0, 0, 0, 0, 0};
+    x[c] = 1.0;
+    for (int i = 0; i < 6; ++i) {
+      double s = x[i];
+      for (int k = 0; k < i; ++k) s -= L[6 * i + k] * x[k];
+      x[i] = s / L[6 * i + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+      double s = x[i];
+      for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
+      x[i] = s / L[6 * i + i];
+    }
+    for (int i = 0; i < 6; ++i) Ai[6 * i + c] = x[i];
+  }
+}
+
+// Q with first column a (unit): a right-handed frame whose x axis is the joint axis.
+void axis_frame(const double *a, double *Q) {
+  int m = 0;
+  if (std::fabs(a[1]) < std::fabs(a[m])) m = 1;
+  if (std::fabs(a[2]) < std::fabs(a[m])) m = 2;
+  double e[3] = {0, 0, 0};
+  e[m] = 1.0;
+  const double d = e[0] * a[0] + e[1] * a[1] + e[2] * a[2];
+  double b[3] = {e[0] - d * a[0], e[1] - d * a[1], e[2] - d * a[2]};
+  const double nb = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+  for (double &v : b) v /= nb;
+  const double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2],
+                       a[0] * b[1] - a[1] * b[0]};
+  for (int r = 0; r < 3; ++r) {
+    Q[3 * r + 0] = a[r];
+    Q[3 * r + 1] = b[r];
+    Q[3 * r + 2] = c[r];
+  }
+}
+
+void m3_mul(const double *A, const double *B, double *C) {
+  double T[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      T[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+  std::memcpy(C, T, sizeof T);
+}
+
+void m3_tmul(const double *A, const double *B, double *C) {  // A^T B
+  double T[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      T[3 * i + j] = A[i] * B[j] + A[3 + i] * B[3 + j] + A[6 + i] * B[6 + j];
+  std::memcpy(C, T, sizeof T);
+}
+
+int pow2_floor(long long v) {
+  int p = 1;
+  while (2LL * p <= v) p *= 2;
+  return p;
+}
+
+}  // namespace
+
+struct fd_chain_s {
+  int device = 0;
+  int32_t n_chains = 0;
+  int64_t n_links = 0;
+  int32_t max_links = 0;
+  double grav[3] = {0, 0, 0};
+  std::vector<int64_t> h_off;
+  void *d_model64 = nullptr;
+  void *d_model32 = nullptr;
+  int64_t *d_off = nullptr;
+};
+
+struct fd_batch_s {
+  fd_chain_t chain = nullptr;
+  int32_t n_problems = 0;
+  int64_t n_state_links = 0;
+  int64_t sum_sq = 0;
+  int32_t max_links = 0;
+  int32_t *d_prob_chain = nullptr;
+  int64_t *d_state_off = nullptr;
+  int64_t *d_sq_off = nullptr;
+  int32_t *d_order = nullptr;
+};
+
+extern "C" {
+
+const char *fd_last_error(void) { return g_err.c_str(); }
+
+int32_t fd_abi_version(void) { return FD_ABI_VERSION; }
+
+fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const double *joint_axes,
+                          const double *link_frames, const double *spatial_inertias,
+                          const double gravity[3], int32_t device, fd_chain_t *out) {
+  if (!out) return fail(FD_ERR_INVALID_ARG, "fd_create_chain: out is NULL");
+  *out = nullptr;
+  if (n_chains < 0) return fail(FD_ERR_INVALID_ARG, "fd_create_chain: n_chains < 0");
+  if (!link_offsets || !gravity)
+    return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link_offsets or gravity is NULL");
+  if (link_offsets[0] != 0)
+    return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link_offsets[0] must be 0");
+  int32_t max_links = 0;
+  for (int32_t k = 0; k < n_chains; ++k) {
+    const int64_t len = link_offsets[k + 1] - link_offsets[k];
+    if (len < 0 || len > (1 << 20))
+      return fail(FD_ERR_INVALID_ARG, "fd_create_chain: chain %d has %lld links", k,
+                  static_cast<long long>(len));
+    max_links = std::max<int32_t>(max_links, static_cast<int32_t>(len));
+  }
+  const int64_t L = link_offsets[n_chains];
+  if (L > 0 && (!joint_axes || !link_frames || !spatial_inertias))
+    return fail(FD_ERR_INVALID_ARG, "fd_create_chain: model array is NULL");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(gravity[k])) return fail(FD_ERR_INVALID_ARG, "fd_create_chain: gravity");
+
+  // Canonical link frames (joint axis = x axis of the child frame), model records.
+  std::vector<double> rec64(static_cast<size_t>(std::max<int64_t>(L, 1)) * fdk::REC, 0.0);
+  for (int32_t k = 0; k < n_chains; ++k) {
+    double Qprev[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    for (int64_t i = link_offsets[k]; i < link_offsets[k + 1]; ++i) {
+      const double *ax = joint_axes + 3 * i;
+      const double *fr = link_frames + 12 * i;
+      const double *J = spatial_inertias + 36 * i;
+      const double na = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+      if (!(na > 1e-12) || !std::isfinite(na))
+        return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld has a zero joint axis",
+                    static_cast<long long>(i));
+      const double a[3] = {ax[0] / na, ax[1] / na, ax[2] / na};
+      double RtR[9];
+      m3_tmul(fr, fr, RtR);
+      for (int r = 0; r < 9; ++r)
+        if (!(std::fabs(RtR[r] - (r % 4 == 0 ? 1.0 : 0.0)) < 1e-9))
+          return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld frame is not a rotation",
+                      static_cast<long long>(i));
+      const double det = fr[0] * (fr[4] * fr[8] - fr[5] * fr[7]) -
+                         fr[1] * (fr[3] * fr[8] - fr[5] * fr[6]) +
+                         fr[2] * (fr[3] * fr[7] - fr[4] * fr[6]);
+      if (!(det > 0.0))
+        return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld frame has det <= 0",
+                    static_cast<long long>(i));
+      double scale = 0.0;
+      for (int r = 0; r < 36; ++r) scale = std::max(scale, std::fabs(J[r]));
+      for (int r = 0; r < 6; ++r)
+        for (int c = r + 1; c < 6; ++c)
+          if (!(std::fabs(J[6 * r + c] - J[6 * c + r]) <= 1e-9 * scale))
+            return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld inertia not symmetric",
+                        static_cast<long long>(i));
+      double Q[9];
+      axis_frame(a, Q);
+      // R0' = Qprev^T R0 Q, p0' = Qprev^T p0
+      double t[9], R0c[9], p0c[3];
+      m3_mul(fr, Q, t);
+      m3_tmul(Qprev, t, R0c);
+      for (int r = 0; r < 3; ++r)
+        p0c[r] = Qprev[r] * fr[9] + Qprev[3 + r] * fr[10] + Qprev[6 + r] * fr[11];
+      // J' = diag(Q, Q)^T J diag(Q, Q)
+      double B[36] = {0};
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) B[6 * r + c] = B[6 * (r + 3) + c + 3] = Q[3 * r + c];
+      double JB[36], Jc[36];
+      for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c) {
+          double s = 0;
+          for (int k2 = 0; k2 < 6; ++k2) s += 0.5 * (J[6 * r + k2] + J[6 * k2 + r]) * B[6 * k2 + c];
+          JB[6 * r + c] = s;
+        }
+      for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c) {
+          double s = 0;
+          for (int k2 = 0; k2 < 6; ++k2) s += B[6 * k2 + r] * JB[6 * k2 + c];
+          Jc[6 * r + c] = s;
+        }
+      double Lc[36], Ji[36];
+      if (!chol6(Jc, Lc))
+        return fail(FD_ERR_INVALID_ARG,
+                    "fd_create_chain: link %lld inertia is not positive definite",
+                    static_cast<long long>(i));
+      inv_from_chol6(Lc, Ji);
+      double *rc = rec64.data() + static_cast<size_t>(i) * fdk::REC;
+      std::memcpy(rc + fdk::REC_R0, R0c, 9 * sizeof(double));
+      std::memcpy(rc + fdk::REC_P0, p0c, 3 * sizeof(double));
+      for (int r = 0; r < 6; ++r)
+        for (int c = r; c < 6; ++c) {
+          rc[fdk::REC_J + s6(r, c)] = Jc[6 * r + c];
+          rc[fdk::REC_JI + s6(r, c)] = 0.5 * (Ji[6 * r + c] + Ji[6 * c + r]);
+        }
+      std::memcpy(Qprev, Q, sizeof Qprev);
+    }
+  }
+  std::vector<float> rec32(rec64.size());
+  for (size_t k = 0; k < rec64.size(); ++k) rec32[k] = static_cast<float>(rec64[k]);
+
+  int n_dev = 0;
+  cudaError_t e = cudaGetDeviceCount(&n_dev);
+  if (e != cudaSuccess || n_dev == 0)
+    return fail(FD_ERR_CUDA, "fd_create_chain: no CUDA device (%s)", cudaGetErrorString(e));
+  if (device < 0 || device >= n_dev)
+    return fail(FD_ERR_INVALID_ARG, "fd_create_chain: device %d of %d", device, n_dev);
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+
+  auto *c = new fd_chain_s();
+  c->device = device;
+  c->n_chains = n_chains;
+  c->n_links = L;
+  c->max_links = max_links;
+  std::memcpy(c->grav, gravity, sizeof c->grav);
+  c->h_off.assign(link_offsets, link_offsets + n_chains + 1);
+  const size_t b64 = rec64.size() * sizeof(double), b32 = rec32.size() * sizeof(float);
+  const size_t boff = (n_chains + 1) * sizeof(int64_t);
+  if ((e = cudaMalloc(&c->d_model64, b64)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_model32, b32)) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void **>(&c->d_off), boff)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_model64, rec64.data(), b64, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_model32, rec32.data(), b32, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_off, link_offsets, boff, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(c->d_model64);
+    cudaFree(c->d_model32);
+    cudaFree(c->d_off);
+    delete c;
+    cudaSetDevice(prev);
+    return cuda_fail(e, "fd_create_chain: device copy");
+  }
+  cudaSetDevice(prev);
+  *out = c;
+  return FD_OK;
+}
+
+fd_status fd_destroy_chain(fd_chain_t c) {
+  if (!c) return fail(FD_ERR_INVALID_ARG, "fd_destroy_chain: NULL");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaFree(c->d_model64);
+  cudaFree(c->d_model32);
+  cudaFree(c->d_off);
+  cudaSetDevice(prev);
+  delete c;
+  return FD_OK;
+}
+
+fd_status fd_chain_info(fd_chain_t c, int32_t *n_chains, int64_t *n_links, int32_t *max_links) {
+  if (!c) return fail(FD_ERR_INVALID_ARG, "fd_chain_info: NULL chain");
+  if (n_chains) *n_chains = c->n_chains;
+  if (n_links) *n_links = c->n_links;
+  if (max_links) *max_links = c->max_links;
+  return FD_OK;
+}
+
+fd_status fd_batch_create(fd_chain_t c, int32_t n_problems, const int32_t *chain_index,
+                          fd_batch_t *out) {
+  if (!out) return fail(FD_ERR_INVALID_ARG, "fd_batch_create: out is NULL");
+  *out = nullptr;
+  if (!c) return fail(FD_ERR_INVALID_ARG, "fd_batch_create: NULL chain");
+  if (n_problems < 0) return fail(FD_ERR_INVALID_ARG, "fd_batch_create: n_problems < 0");
+  if (!chain_index && n_problems != c->n_chains)
+    return fail(FD_ERR_INVALID_ARG,
+                "fd_batch_create: without chain_index n_problems (%d) must equal the number "
+                "of chains (%d)", n_problems, c->n_chains);
+  std::vector<int32_t> pc(static_cast<size_t>(n_problems));
+  std::vector<int64_t> so(static_cast<size_t>(n_problems) + 1, 0), sq(so.size(), 0);
+  std::vector<int32_t> len(pc.size());
+  int32_t max_links = 0;
+  for (int32_t p = 0; p < n_problems; ++p) {
+    const int32_t k = chain_index ? chain_index[p] : p;
+    if (k < 0 || k >= c->n_chains)
+      return fail(FD_ERR_INVALID_ARG, "fd_batch_create: chain_index[%d] = %d out of range", p, k);
+    pc[p] = k;
+    const int64_t n = c->h_off[k + 1] - c->h_off[k];
+    len[p] = static_cast<int32_t>(n);
+    max_links = std::max<int32_t>(max_links, static_cast<int32_t>(n));
+    so[p + 1] = so[p] + n;
+    sq[p + 1] = sq[p] + n * n;
+  }
+  // longest problems first (a ragged batch then finishes together)
+  std::vector<int32_t> order(pc.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t x, int32_t y) { return len[x] > len[y]; });
+
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  auto *b = new fd_batch_s();
+  b->chain = c;
+  b->n_problems = n_problems;
+  b->n_state_links = so.back();
+  b->sum_sq = sq.back();
+  b->max_links = max_links;
+  const size_t np = std::max<size_t>(pc.size(), 1);
+  if ((e = cudaMalloc(reinterpret_cast<void **>(&b->d_prob_chain), np * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void **>(&b->d_order), np * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void **>(&b->d_state_off), so.size() * sizeof(int64_t))) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void **>(&b->d_sq_off), sq.size() * sizeof(int64_t))) != cudaSuccess ||
+      (n_problems > 0 &&
+       ((e = cudaMemcpy(b->d_prob_chain, pc.data(), pc.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)) ||
+      (e = cudaMemcpy(b->d_state_off, so.data(), so.size() * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_sq_off, sq.data(), sq.size() * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(b->d_prob_chain);
+    cudaFree(b->d_order);
+    cudaFree(b->d_state_off);
+    cudaFree(b->d_sq_off);
+    delete b;
+    cudaSetDevice(prev);
+    return cuda_fail(e, "fd_batch_create: device copy");
+  }
+  cudaSetDevice(prev);
+  *out = b;
+  return FD_OK;
+}
+
+fd_status fd_batch_destroy(fd_batch_t b) {
+  if (!b) return fail(FD_ERR_INVALID_ARG, "fd_batch_destroy: NULL");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->chain->device);
+  cudaFree(b->d_prob_chain);
+  cudaFree(b->d_order);
+  cudaFree(b->d_state_off);
+  cudaFree(b->d_sq_off);
+  cudaSetDevice(prev);
+  delete b;
+  return FD_OK;
+}
+
+fd_status fd_batch_info(fd_batch_t b, int32_t *n_problems, int64_t *n_state_links,
+                        int32_t *max_links) {
+  if (!b) return fail(FD_ERR_INVALID_ARG, "fd_batch_info: NULL batch");
+  if (n_problems) *n_problems = b->n_problems;
+  if (n_state_links) *n_state_links = b->n_state_links;
+  if (max_links) *max_links = b->max_links;
+  return FD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int resolve_team(const fd_batch_s *b, int32_t algo, int32_t team) {
+  if (algo == FD_ABIA) return 1;
+  if (team > 0) return team;
+  // enough threads to fill the GPU (about 78k resident threads is a full GB300),
+  // but no more lanes than links
+  const long long want = 152LL * 512;
+  long long per = b->n_problems > 0 ? want / b->n_problems : 1;
+  int p = pow2_floor(std::max<long long>(per, 1));
+  int cap = 1;
+  while (cap < b->max_links && cap < 32) cap *= 2;
+  return std::min(p, cap);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+struct WsPlan {
+  size_t t_bytes, a_bytes;
+};
+
+WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int team) {
+  const size_t ts = prec == FD_FP64 ? 8 : 4;
+  const size_t as = prec == FD_FP32 ? 4 : 8;
+  const size_t L = static_cast<size_t>(b->n_state_links);
+  WsPlan w{align256(L * fdk::NT * ts), 0};
+  if (algo == FD_CFA) w.a_bytes = L * fdk::NA_CFA * as;
+  if (algo == FD_JSIIA)
+    w.a_bytes = (L * (fdk::NA_JSIIA + fdk::NP_JSIIA * team) +
+                 static_cast<size_t>(b->sum_sq) * fdk::NSQ_JSIIA) * as;
+  if (algo == FD_ABIA) w.a_bytes = L * fdk::NA_ABIA * as;
+  w.a_bytes = align256(w.a_bytes);
+  return w;
+}
+
+bool valid_team(int t) { return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32; }
+
+}  // namespace
+
+extern "C" {
+
+size_t fd_workspace_size(fd_batch_t b, int32_t algo, fd_prec prec, int32_t team) {
+  if (!b) return 0;
+  const int t = resolve_team(b, algo, team);
+  const WsPlan w = ws_plan(b, algo, prec, t);
+  return w.t_bytes + w.a_bytes;
+}
+
+static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, const void *in3,
+                               void *out, int32_t algo, fd_prec prec, int32_t team, void *ws,
+                               size_t ws_bytes, int32_t *status, void *stream, const char *who) {
+  if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
+  if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
+    return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
+  if (algo != -1 && algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA)
+    return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, algo);
+  if (team < 0 || (team > 0 && !valid_team(team)))
+    return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 32", who, team);
+  if (algo == FD_ABIA && team > 1)
+    return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs one thread per problem (team 1)", who);
+  if (b->n_problems == 0 || b->n_state_links == 0) return FD_OK;
+  if (!q || !qd || !in3 || !out) return fail(FD_ERR_INVALID_ARG, "%s: NULL state array", who);
+  const int t = resolve_team(b, algo, team);
+  const WsPlan w = ws_plan(b, algo, prec, t);
+  if (!ws || ws_bytes < w.t_bytes + w.a_bytes)
+    return fail(FD_ERR_INVALID_ARG, "%s: workspace of %zu bytes, %zu needed", who, ws_bytes,
+                w.t_bytes + w.a_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+    return fail(FD_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", who);
+  const int prec_k = prec == FD_FP64 ? 0 : (prec == FD_FP32 || algo == -1 ? 1 : 2);
+  fdk::KArgs a{};
+  a.model = prec == FD_FP64 ? b->chain->d_model64 : b->chain->d_model32;
+  a.model_off = b->chain->d_off;
+  a.prob_chain = b->d_prob_chain;
+  a.state_off = b->d_state_off;
+  a.sq_off = b->d_sq_off;
+  a.order = b->d_order;
+  a.n_problems = b->n_problems;
+  a.team = t;
+  a.q = q;
+  a.qd = qd;
+  a.in3 = in3;
+  a.out = out;
+  a.ws_t = ws;
+  a.ws_a = static_cast<char *>(ws) + w.t_bytes;
+  a.status = status;
+  std::memcpy(a.grav, b->chain->grav, sizeof a.grav);
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(b->chain->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  auto s = static_cast<cudaStream_t>(stream);
+  if (algo == -1) e = fdk::launch_id(a, prec_k, t, s);
+  else if (algo == FD_CFA) e = fdk::launch_cfa(a, prec_k, t, s);
+  else if (algo == FD_JSIIA) e = fdk::launch_jsiia(a, prec_k, t, s);
+  else e = fdk::launch_abia(a, prec_k, s);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  return FD_OK;
+}
+
+fd_status fd_solve_batch(fd_batch_t b, const void *q, const void *qdot, const void *tau,
+                         void *qddot, fd_algo algo, fd_prec prec, int32_t team, void *workspace,
+                         size_t workspace_bytes, int32_t *status, void *stream) {
+  return launch_common(b, q, qdot, tau, qddot, static_cast<int32_t>(algo), prec, team, workspace,
+                       workspace_bytes, status, stream, "fd_solve_batch");
+}
+
+fd_status fd_inverse_dynamics(fd_batch_t b, const void *q, const void *qdot, const void *qddot,
+                              void *tau, fd_prec prec, int32_t team, void *workspace,
+                              size_t workspace_bytes, void *stream) {
+  return launch_common(b, q, qdot, qddot, tau, -1, prec == FD_MIXED ? FD_FP32 : prec, team,
+                       workspace, workspace_bytes, nullptr, stream, "fd_inverse_dynamics");
+}
+
+}  // extern "C"

@@ -1,0 +1,635 @@
+// fd_kernels.cuh -- the forward-dynamics kernels (ABIA, JSIIA, CFA) and the
+// inverse-dynamics kernel, generic in the arithmetic type T, the accumulation
+// type TA (OEE, articulated inertia, JSIIA Cholesky) and the team size P.
+//
+// One team of P lanes solves one problem (chain + state). Link i of an n-link
+// chain belongs to lane floor(i / S), S = ceil(n / P): each lane runs the
+// recursions serially over its segment and the lanes combine their segments'
+// operators by a Kogge-Stone scan (Section II-B); P = 1 is the serial recursion.
+#pragma once
+
+#include "fd_device.cuh"
+
+namespace fdk {
+
+template <class T>
+struct Prob {
+  int p;          // problem index
+  int n;          // links
+  int a, b;       // this lane's segment [a, b)
+  const T *rec;   // model records of the chain
+  const T *q, *qd, *in3;
+  T *out;
+  T *wt;          // T workspace of the problem [n][NT]
+};
+
+template <class T, int P>
+__device__ __forceinline__ bool load_problem(const KArgs &A, const Team<P> &tm, Prob<T> &pb,
+                                             int nt_stride) {
+  const long long team = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) / P;
+  if (team >= A.n_problems) return false;
+  const int p = A.order ? A.order[team] : static_cast<int>(team);
+  const int c = A.prob_chain[p];
+  const int64_t m0 = A.model_off[c];
+  const int n = static_cast<int>(A.model_off[c + 1] - m0);
+  const int64_t s0 = A.state_off[p];
+  const int S = (n + P - 1) / P;
+  pb.p = p;
+  pb.n = n;
+  pb.a = min(tm.r * S, n);
+  pb.b = min(pb.a + S, n);
+  pb.rec = static_cast<const T *>(A.model) + m0 * REC;
+  pb.q = static_cast<const T *>(A.q) + s0;
+  pb.qd = static_cast<const T *>(A.qd) + s0;
+  pb.in3 = static_cast<const T *>(A.in3) + s0;
+  pb.out = static_cast<T *>(A.out) + s0;
+  pb.wt = static_cast<T *>(A.ws_t) + s0 * nt_stride;
+  return true;
+}
+
+// -------------------------------------------------------- inverse dynamics
+
+// Eq. 2a-2d for one problem: the twist and acceleration recursions (forward,
+// block lower bi-diagonal) and the force recursion (backward, block upper
+// bi-diagonal), each as a segmented scan over SE(3)-affine operators.
+//   mode_fd = true:  qdd = 0 and gravity; writes tau_delta_i = tau_i - tau_bias_i
+//   mode_fd = false: qdd = in3;           writes tau_i
+// Leaves g_i, V_i, f_i in the workspace.
+template <class T, int P>
+__device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, const double *grav,
+                                        bool mode_fd) {
+  const int a = pb.a, b = pb.b;
+  SegOp<T> op;
+  se3_identity(op.h);
+  // joint transforms and this segment's product h = g_a ... g_{b-1}
+  for (int i = a; i < b; ++i) {
+    SE3<T> g;
+    joint_transform(pb.rec + static_cast<int64_t>(i) * REC, pb.q[i], g);
+    st_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+    if (P > 1) se3_mul(op.h, g, op.h);
+  }
+  const T zero6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  T x[6];
+
+  // ---- twist: V_i = Ad_{g_i^{-1}} V_{i-1} + e_1 qd_i, V_{-1} = 0 (Eq. 2a)
+  if (P > 1) {
+    for (int k = 0; k < 6; ++k) x[k] = T(0);
+    for (int i = a; i < b; ++i) {
+      SE3<T> g;
+      ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+      adinv(g, x, x);
+      x[0] += pb.qd[i];
+    }
+    for (int k = 0; k < 6; ++k) op.psi[k] = x[k];
+    team_scan_fwd(tm, op, zero6, x);
+  } else {
+    for (int k = 0; k < 6; ++k) x[k] = T(0);
+  }
+  for (int i = a; i < b; ++i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    SE3<T> g;
+    ld_se3(w + W_G, g);
+    adinv(g, x, x);
+    x[0] += pb.qd[i];
+    stv<T, 6>(w + W_V, x);
+  }
+
+  // ---- acceleration: Vd_i = Ad_{g_i^{-1}} Vd_{i-1} + e_1 qdd_i + ad_{V_i} e_1 qd_i,
+  //      Vd_{-1} = (0; -g) (Eq. 2b, gravity as base acceleration)
+  const T base[6] = {T(0), T(0), T(0), T(-grav[0]), T(-grav[1]), T(-grav[2])};
+  auto accel_step = [&](int i, T *xx) {
+    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    SE3<T> g;
+    ld_se3(w + W_G, g);
+    adinv(g, xx, xx);
+    const T *V = w + W_V;
+    const T qdi = pb.qd[i];
+    // ad_V e_1 = (0, w_z, -w_y; 0, v_z, -v_y)
+    xx[1] += V[2] * qdi;
+    xx[2] -= V[1] * qdi;
+    xx[4] += V[5] * qdi;
+    xx[5] -= V[4] * qdi;
+    if (!mode_fd) xx[0] += pb.in3[i];
+  };
+  if (P > 1) {
+    for (int k = 0; k < 6; ++k) x[k] = T(0);
+    for (int i = a; i < b; ++i) accel_step(i, x);
+    for (int k = 0; k < 6; ++k) op.psi[k] = x[k];
+    team_scan_fwd(tm, op, base, x);
+  } else {
+    for (int k = 0; k < 6; ++k) x[k] = base[k];
+  }
+  for (int i = a; i < b; ++i) {
+    accel_step(i, x);
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+    T V[6], JV[6], JA[6], c[6];
+    ldv<T, 6>(w + W_V, V);
+    sym6_apply(rec + REC_J, x, JA);
+    sym6_apply(rec + REC_J, V, JV);
+    adT_apply(V, JV, c);
+    for (int k = 0; k < 6; ++k) JA[k] -= c[k];
+    stv<T, 6>(w + W_F, JA);
+  }
+
+  // ---- force: F_i = Ad_{g_{i+1}^{-1}}^T F_{i+1} + f_i, F_n = 0 (Eq. 2c), tau = S^T F (2d)
+  T y[6];
+  if (P > 1) {
+    for (int k = 0; k < 6; ++k) y[k] = T(0);
+    for (int i = b - 1; i >= a; --i) {
+      const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+      SE3<T> g;
+      ld_se3(w + W_G, g);
+      for (int k = 0; k < 6; ++k) y[k] += w[W_F + k];
+      adinvT(g, y, y);
+    }
+    for (int k = 0; k < 6; ++k) op.psi[k] = y[k];
+    team_scan_bwd(tm, op, y);
+  } else {
+    for (int k = 0; k < 6; ++k) y[k] = T(0);
+  }
+  for (int i = b - 1; i >= a; --i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    SE3<T> g;
+    ld_se3(w + W_G, g);
+    for (int k = 0; k < 6; ++k) y[k] += w[W_F + k];
+    w[W_TD] = mode_fd ? pb.in3[i] - y[0] : y[0];
+    adinvT(g, y, y);
+  }
+}
+
+template <class T, int P>
+__global__ void __launch_bounds__(128) id_kernel(KArgs A) {
+  Team<P> tm;
+  Prob<T> pb;
+  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  id_team<T, P>(tm, pb, A.grav, false);
+  for (int i = pb.a; i < pb.b; ++i) pb.out[i] = pb.wt[static_cast<int64_t>(i) * NT + W_TD];
+}
+
+// -------------------------------------------------------------------- CFA
+
+// (X K X^T)[1..5][1..5] + Kd[1..5][1..5] into packed lower 5x5, X = Ad_{g^{-1}},
+// K, Kd packed symmetric 6x6 (T_ii of Algorithm 1's CalcA, W_i^T T_ii W_i).
+template <class T, class TA>
+__device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, const T *Kself,
+                                            TA *D) {
+  TA acc[15];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c) acc[l5(r, c)] = TA(Kself[s6(r + 1, c + 1)]);
+  if (g) {
+    // M1 = X K: X applied to each column of K
+    T M1[6][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      T col[6], o[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) col[k] = Kprev[s6(k, j)];
+      adinv(*g, col, o);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) M1[k][j] = o[k];
+    }
+    // (X K X^T) column c = X (row c of M1)
+#pragma unroll
+    for (int c = 1; c < 6; ++c) {
+      T row[6], o[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) row[k] = M1[c][k];
+      adinv(*g, row, o);
+#pragma unroll
+      for (int r = c; r < 6; ++r) acc[l5(r - 1, c - 1)] += TA(o[r]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 15; ++k) D[k] = acc[k];
+}
+
+// U_i = W_i^T T_{i,i+1} W_{i+1} = -(J_i^{-1} Ad_{g_{i+1}^{-1}}^T)[1..5][1..5]
+template <class T, class TA>
+__device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, TA *U) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    T e[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    e[c + 1] = T(1);
+    T col[6], o[6];
+    adinvT(gn, e, col);
+    sym6_apply(Ki, col, o);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) U[5 * r + c] = TA(-o[r + 1]);
+  }
+}
+
+// One OEE update of row i at distance d (Section IV, update rule and Algorithm 2,
+// right-hand sides all at level j-1).
+template <class TA>
+__device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int srcD, int srcU,
+                                        int srcR, TA *Dn, TA *Un, TA *Rn) {
+  const TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+#pragma unroll
+  for (int k = 0; k < 15; ++k) Dn[k] = row[srcD + k];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Rn[k] = row[srcR + k];
+#pragma unroll
+  for (int k = 0; k < 25; ++k) Un[k] = TA(0);
+  if (i + d < n) {
+    const TA *nb = wa + static_cast<int64_t>(i + d) * NA_CFA;
+    TA L[15], inv[5];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) L[k] = nb[A_L + k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) inv[k] = nb[A_LI + k];
+    TA Z[5][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Z[k][c] = row[srcU + 5 * k + c];
+      fwd5(L, inv, Z[k]);  // z_k^T = L^{-1} u_k^T  (Z = U_i L^{-T})
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) {
+        TA s = TA(0);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) s += Z[r][k] * Z[c][k];
+        Dn[l5(r, c)] -= s;  // E_i U_i^T = Z Z^T
+      }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) bwd5(L, inv, Z[k]);  // now Z = E_i = U_i D_{i+d}^{-1}
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      TA s = TA(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s += Z[r][k] * nb[srcR + k];
+      Rn[r] -= s;  // E_i R_{i+d}
+    }
+    if (i + 2 * d < n) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          TA s = TA(0);
+#pragma unroll
+          for (int k = 0; k < 5; ++k) s += Z[r][k] * nb[srcU + 5 * k + c];
+          Un[5 * r + c] = -s;  // U_i <- -E_i U_{i+d}
+        }
+    }
+  }
+  if (i - d >= 0) {
+    const TA *pr = wa + static_cast<int64_t>(i - d) * NA_CFA;
+    TA L[15], inv[5];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) L[k] = pr[A_L + k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) inv[k] = pr[A_LI + k];
+    TA Zt[5][5];  // Zt[l] = column l of L^{-1} U_{i-d}
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Zt[l][k] = pr[srcU + 5 * k + l];
+      fwd5(L, inv, Zt[l]);
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) {
+        TA s = TA(0);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) s += Zt[r][k] * Zt[c][k];
+        Dn[l5(r, c)] -= s;  // K_i U_{i-d} = (L^{-1}U)^T (L^{-1}U)
+      }
+    TA w[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w[k] = pr[srcR + k];
+    fwd5(L, inv, w);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      TA s = TA(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s += Zt[r][k] * w[k];
+      Rn[r] -= s;  // K_i R_{i-d}
+    }
+  }
+}
+
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(128) cfa_kernel(KArgs A) {
+  Team<P> tm;
+  Prob<T> pb;
+  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  const int n = pb.n, a = pb.a, b = pb.b;
+  TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_CFA;
+  bool bad = false;
+
+  // bias torque and tau_delta (Algorithm 1: CalcInvDyn, CalcDiffTorques)
+  id_team<T, P>(tm, pb, A.grav, true);
+  tm.sync();
+
+  // CalcA: D_i, U_i; R = -B tau_delta applied as -W^T (I-Gamma) J^{-1} (I-Gamma)^T S tau_delta
+  for (int i = a; i < b; ++i) {
+    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+    TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    SE3<T> g;
+    ld_se3(w + W_G, g);
+    calc_dblock<T, TA>(i > 0 ? &g : nullptr, i > 0 ? rec - REC + REC_JI : nullptr,
+                       rec + REC_JI, row + A_D0);
+    T yv[6] = {w[W_TD], T(0), T(0), T(0), T(0), T(0)};
+    if (i + 1 < n) {
+      SE3<T> gn;
+      ld_se3(w + NT + W_G, gn);
+      calc_ublock<T, TA>(gn, rec + REC_JI, row + A_U0);
+      const T tn = w[NT + W_TD];
+      // Ad_{g_{i+1}^{-1}}^T (e_1 t) = (t R e_1; 0)
+      yv[0] -= gn.R[0] * tn;
+      yv[1] -= gn.R[3] * tn;
+      yv[2] -= gn.R[6] * tn;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 25; ++k) row[A_U0 + k] = TA(0);
+    }
+    T z[6];
+    sym6_apply(rec + REC_JI, yv, z);
+    stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
+  }
+  tm.sync();
+  for (int i = a; i < b; ++i) {
+    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    T z[6];
+    ldv<T, 6>(w + W_Z, z);
+    if (i > 0) {
+      SE3<T> g;
+      ld_se3(w + W_G, g);
+      T t[6];
+      adinv(g, w - NT + W_Z, t);
+      for (int k = 0; k < 6; ++k) z[k] -= t[k];
+    }
+    TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    for (int k = 0; k < 5; ++k) row[A_R0 + k] = TA(-z[k + 1]);
+  }
+  tm.sync();
+
+  // SolvBTDSys: odd-even elimination, ceil(log2 n) levels (Algorithm 2)
+  int levels = 0;
+  while ((1 << levels) < n) ++levels;
+  int src = 0;
+  for (int j = 1; j <= levels; ++j) {
+    const int d = 1 << (j - 1);
+    const int sD = src ? A_D1 : A_D0, sU = src ? A_U1 : A_U0, sR = src ? A_R1 : A_R0;
+    const int tD = src ? A_D0 : A_D1, tU = src ? A_U0 : A_U1, tR = src ? A_R0 : A_R1;
+    for (int m = a; m < b; ++m) {
+      TA *row = wa + static_cast<int64_t>(m) * NA_CFA;
+      TA Dm[15];
+      for (int k = 0; k < 15; ++k) Dm[k] = row[sD + k];
+      bad |= !chol5(Dm, row + A_L, row + A_LI);
+    }
+    tm.sync();
+    for (int i = a; i < b; ++i) {
+      TA Dn[15], Un[25], Rn[5];
+      oee_row<TA>(i, d, n, wa, sD, sU, sR, Dn, Un, Rn);
+      TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+      for (int k = 0; k < 15; ++k) row[tD + k] = Dn[k];
+      for (int k = 0; k < 25; ++k) row[tU + k] = Un[k];
+      for (int k = 0; k < 5; ++k) row[tR + k] = Rn[k];
+    }
+    tm.sync();
+    src ^= 1;
+  }
+  // F_c,i = D_i^{-1} R_i
+  for (int i = a; i < b; ++i) {
+    TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    TA Dm[15], L[15], inv[5], r[5];
+    for (int k = 0; k < 15; ++k) Dm[k] = row[(src ? A_D1 : A_D0) + k];
+    for (int k = 0; k < 5; ++k) r[k] = row[(src ? A_R1 : A_R0) + k];
+    bad |= !chol5(Dm, L, inv);
+    fwd5(L, inv, r);
+    bwd5(L, inv, r);
+    for (int k = 0; k < 5; ++k) row[A_FC + k] = r[k];
+  }
+  tm.sync();
+
+  // CalcAcc: qdd = C tau_delta + B^T F_c = S^T (I-Gamma) J^{-1} (I-Gamma)^T F,
+  // F_i = S tau_delta_i + W F_c,i (Eq. force-decomposition-global)
+  for (int i = a; i < b; ++i) {
+    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+    const TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    T yv[6] = {w[W_TD], T(row[A_FC]), T(row[A_FC + 1]), T(row[A_FC + 2]), T(row[A_FC + 3]),
+               T(row[A_FC + 4])};
+    if (i + 1 < n) {
+      SE3<T> gn;
+      ld_se3(w + NT + W_G, gn);
+      const TA *rn = row + NA_CFA;
+      T Fn[6] = {w[NT + W_TD], T(rn[A_FC]), T(rn[A_FC + 1]), T(rn[A_FC + 2]), T(rn[A_FC + 3]),
+                 T(rn[A_FC + 4])};
+      T t[6];
+      adinvT(gn, Fn, t);
+      for (int k = 0; k < 6; ++k) yv[k] -= t[k];
+    }
+    T z[6];
+    sym6_apply(rec + REC_JI, yv, z);
+    stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
+  }
+  tm.sync();
+  for (int i = a; i < b; ++i) {
+    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    T qdd = w[W_Z];
+    if (i > 0) {
+      // (Ad_{g_i^{-1}} z_{i-1})_0 = (R^T omega)_0
+      const T *zp = w - NT + W_Z;
+      qdd -= w[W_G + 0] * zp[0] + w[W_G + 3] * zp[1] + w[W_G + 6] * zp[2];
+    }
+    pb.out[i] = qdd;
+    if (!finite_t(qdd)) bad = true;
+  }
+  const bool any_bad = P > 1 ? __any_sync(tm.mask, bad) : bad;
+  if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
+}
+
+// ------------------------------------------------------------------ JSIIA
+
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(128) jsiia_kernel(KArgs A) {
+  Team<P> tm;
+  Prob<T> pb;
+  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  const int n = pb.n, a = pb.a, b = pb.b;
+  const int64_t s0 = A.state_off[pb.p];
+  TA *vec = static_cast<TA *>(A.ws_a) + s0 * (NA_JSIIA + NP_JSIIA * P) + A.sq_off[pb.p] * NSQ_JSIIA;
+  TA *M = vec + static_cast<int64_t>(n) * NA_JSIIA;               // n x n, row-major
+  TA *acc = M + static_cast<int64_t>(n) * n;                      // [P][n][6]
+  TA *myacc = acc + static_cast<int64_t>(tm.r) * n * 6;
+  bool bad = false;
+
+  id_team<T, P>(tm, pb, A.grav, true);
+  for (int i = a; i < b; ++i) vec[i] = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]);
+  tm.sync();
+
+  // columns of M: ID with qdd = e_k, qdot = 0, no gravity (Section II-C); the
+  // lower triangle i >= k of column k needs links k..n-1 only.
+  for (int k = tm.r; k < n; k += P) {
+    TA x[6] = {TA(1), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    for (int c = 0; c < 6; ++c) myacc[static_cast<int64_t>(k) * 6 + c] = x[c];
+    for (int i = k + 1; i < n; ++i) {
+      SE3<T> g;
+      ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+      SE3<TA> ga;
+      for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
+      for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
+      adinv(ga, x, x);
+      for (int c = 0; c < 6; ++c) myacc[static_cast<int64_t>(i) * 6 + c] = x[c];
+    }
+    TA y[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    for (int i = n - 1; i >= k; --i) {
+      TA f[6], va[6];
+      for (int c = 0; c < 6; ++c) va[c] = myacc[static_cast<int64_t>(i) * 6 + c];
+      sym6_apply(pb.rec + static_cast<int64_t>(i) * REC + REC_J, va, f);
+      for (int c = 0; c < 6; ++c) y[c] += f[c];
+      M[static_cast<int64_t>(i) * n + k] = y[0];
+      SE3<T> g;
+      ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+      SE3<TA> ga;
+      for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
+      for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
+      adinvT(ga, y, y);
+    }
+  }
+  tm.sync();
+
+  // Cholesky M = L L^T (right-looking, rows shared by the team), then the two
+  // triangular solves (the "inversion" of Section II-C read as a factorisation).
+  for (int j = 0; j < n; ++j) {
+    const TA djj = M[static_cast<int64_t>(j) * n + j];
+    bad |= !(djj > TA(0));
+    const TA r = djj > TA(0) ? rsqrt_t(djj) : TA(0);
+    for (int i = j + 1 + tm.r; i < n; i += P) M[static_cast<int64_t>(i) * n + j] *= r;
+    tm.sync();
+    if (tm.r == 0) M[static_cast<int64_t>(j) * n + j] = djj * r;
+    for (int i = j + 1 + tm.r; i < n; i += P) {
+      const TA lij = M[static_cast<int64_t>(i) * n + j];
+      for (int l = j + 1; l <= i; ++l) M[static_cast<int64_t>(i) * n + l] -= lij * M[static_cast<int64_t>(l) * n + j];
+    }
+    tm.sync();
+  }
+  for (int j = 0; j < n; ++j) {  // L y = b
+    const TA yj = vec[j] / M[static_cast<int64_t>(j) * n + j];
+    for (int i = j + 1 + tm.r; i < n; i += P) vec[i] -= M[static_cast<int64_t>(i) * n + j] * yj;
+    tm.sync();
+    if (tm.r == 0) vec[j] = yj;
+    tm.sync();
+  }
+  for (int j = n - 1; j >= 0; --j) {  // L^T x = y
+    const TA xj = vec[j] / M[static_cast<int64_t>(j) * n + j];
+    for (int i = tm.r; i < j; i += P) vec[i] -= M[static_cast<int64_t>(j) * n + i] * xj;
+    tm.sync();
+    if (tm.r == 0) vec[j] = xj;
+    tm.sync();
+  }
+  for (int i = a; i < b; ++i) {
+    const T v = T(vec[i]);
+    pb.out[i] = v;
+    if (!finite_t(v)) bad = true;
+  }
+  const bool any_bad = P > 1 ? __any_sync(tm.mask, bad) : bad;
+  if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
+}
+
+// ------------------------------------------------------------------- ABIA
+
+// Ad_{g^{-1}}^T P Ad_{g^{-1}} of a packed symmetric 6x6 P, added to Out.
+template <class TA>
+__device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, TA *Out) {
+  TA N[6][6];  // N = X^T P (X^T applied to each column of P)
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    TA col[6], o[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) col[k] = P6[s6(k, j)];
+    adinvT(g, col, o);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) N[k][j] = o[k];
+  }
+  // (N X) row i = (X^T N_i^T)^T
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    TA row[6], o[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) row[k] = N[i][k];
+    adinvT(g, row, o);
+#pragma unroll
+    for (int k = i; k < 6; ++k) Out[s6(i, k)] += o[k];
+  }
+}
+
+// ABIA (Section II-C): tau_delta by inverse dynamics, the articulated-body
+// inertia recursion P_{i-1} = J_{i-1} + X_i^T (P_i - P_i S D_i^{-1} S^T P_i) X_i
+// (serial in i, Section III), the bias-force recursion (backward) and the
+// acceleration recursion (forward) of M^{-1} = [I - S^T Y Pi]^T (S^T J^ S)^{-1}
+// [I - S^T Y Pi]. One thread per problem.
+template <class T, class TA>
+__global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
+  Team<1> tm;
+  Prob<T> pb;
+  if (!load_problem<T, 1>(A, tm, pb, NT)) return;
+  const int n = pb.n;
+  TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_ABIA;
+  bool bad = false;
+  id_team<T, 1>(tm, pb, A.grav, true);
+
+  TA Pm[21], pbias[6];
+  if (n > 0) {
+    const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
+    for (int k = 0; k < 21; ++k) Pm[k] = TA(J[k]);
+  }
+  for (int k = 0; k < 6; ++k) pbias[k] = TA(0);
+  for (int i = n - 1; i >= 0; --i) {
+    TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
+    TA h[6];
+    for (int k = 0; k < 6; ++k) h[k] = Pm[s6(0, k)];
+    const TA D = h[0];
+    const TA u = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]) - pbias[0];
+    bad |= !(D > TA(0));
+    const TA Dinv = TA(1) / D;
+    for (int k = 0; k < 6; ++k) ra[A_H + k] = h[k];
+    ra[A_DD] = Dinv;
+    ra[A_UU] = u;
+    if (i == 0) break;
+    // Pa = P - h h^T / D, pa = p + h u / D
+    TA Pa[21], pa[6];
+    for (int r = 0; r < 6; ++r)
+      for (int c = r; c < 6; ++c) Pa[s6(r, c)] = Pm[s6(r, c)] - h[r] * h[c] * Dinv;
+    for (int k = 0; k < 6; ++k) pa[k] = pbias[k] + h[k] * u * Dinv;
+    SE3<T> g;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+    SE3<TA> ga;
+    for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
+    for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
+    const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
+    for (int k = 0; k < 21; ++k) Pm[k] = TA(J[k]);
+    congruence_add(ga, Pa, Pm);
+    adinvT(ga, pa, pbias);
+  }
+  // forward: a' = X_i a_{i-1}, qdd_i = (u_i - h_i . a') / D_i, a_i = a' + e_1 qdd_i
+  TA acc[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+  for (int i = 0; i < n; ++i) {
+    const TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
+    SE3<T> g;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+    SE3<TA> ga;
+    for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
+    for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
+    adinv(ga, acc, acc);
+    TA s = TA(0);
+    for (int k = 0; k < 6; ++k) s += ra[A_H + k] * acc[k];
+    const TA qdd = (ra[A_UU] - s) * ra[A_DD];
+    acc[0] += qdd;
+    const T v = T(qdd);
+    pb.out[i] = v;
+    if (!finite_t(v)) bad = true;
+  }
+  set_status(A.status, pb.p, bad ? 2 : 0);
+}
+
+}  // namespace fdk

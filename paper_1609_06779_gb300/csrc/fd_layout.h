@@ -1,0 +1,79 @@
+// fd_layout.h -- data layout shared by the host side and the kernels.
+//
+// Model arena (one record per link, canonical link frames with the joint axis
+// along x, so S_i = e_1): REC entries of the arena's type per link,
+//   [0, 9)   R0   home rotation parent -> child (row-major)
+//   [9, 12)  p0   home translation parent -> child
+//   [12, 33) J    spatial inertia at the link origin, packed symmetric 6x6
+//   [33, 54) Jinv its inverse, packed symmetric 6x6
+//   [54, 56) padding (keeps a record a multiple of 16 bytes in float and double)
+// Records of one chain are contiguous; chain k starts at record model_off[k].
+#pragma once
+
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#endif
+
+namespace fdk {
+
+constexpr int REC = 56;
+constexpr int REC_R0 = 0;
+constexpr int REC_P0 = 9;
+constexpr int REC_J = 12;
+constexpr int REC_JI = 33;
+
+// Per-link workspace fields of the arithmetic type T (inverse-dynamics part).
+constexpr int W_G = 0;    // joint transform g_{i-1,i}(q_i): R (9), p (3)
+constexpr int W_V = 12;   // twist V_i
+constexpr int W_F = 18;   // f_i = J_i Vd_i - ad_{V_i}^T J_i V_i
+constexpr int W_TD = 24;  // tau_delta_i (or tau_i for inverse dynamics)
+constexpr int W_Z = 25;   // CFA: J^{-1} (I - Gamma)^T F products
+constexpr int NT = 32;    // T entries per link
+
+// Per-row workspace of the accumulation type TA for CFA's odd-even elimination.
+constexpr int A_D0 = 0;    // D (packed symmetric 5x5), two buffers
+constexpr int A_D1 = 15;
+constexpr int A_U0 = 30;   // U (row-major 5x5), two buffers
+constexpr int A_U1 = 55;
+constexpr int A_R0 = 80;   // R (5), two buffers
+constexpr int A_R1 = 85;
+constexpr int A_L = 90;    // Cholesky factor of D (15) and reciprocal diagonal (5)
+constexpr int A_LI = 105;
+constexpr int A_FC = 110;  // F_c (5)
+constexpr int NA_CFA = 116;
+
+// JSIIA: per-link TA entries (right-hand side), n*n TA entries (M), and per team
+// lane 6 TA entries per link (the column's accelerations).
+constexpr int A_B = 0;
+constexpr int NA_JSIIA = 2;
+constexpr int NSQ_JSIIA = 1;
+constexpr int NP_JSIIA = 6;
+
+// ABIA: per-link TA entries: h_i = P_i S_i (6), D_i (1), u_i (1).
+constexpr int A_H = 0;
+constexpr int A_DD = 6;
+constexpr int A_UU = 7;
+constexpr int NA_ABIA = 8;
+
+struct KArgs {
+  const void *model;         // [L][REC] of T
+  const int64_t *model_off;  // [K + 1]
+  const int32_t *prob_chain; // [N]
+  const int64_t *state_off;  // [N + 1]
+  const int64_t *sq_off;     // [N + 1] prefix sums of n_p^2
+  const int32_t *order;      // [N] processing order (longest first)
+  int32_t n_problems;
+  int32_t team;
+  const void *q;
+  const void *qd;
+  const void *in3;  // tau (forward dynamics) or qdd (inverse dynamics)
+  void *out;        // qdd (forward dynamics) or tau (inverse dynamics)
+  void *ws_t;       // per-link T workspace
+  void *ws_a;       // TA workspace
+  int32_t *status;  // [N] or null
+  double grav[3];
+};
+
+}  // namespace fdk

@@ -1,0 +1,225 @@
+"""Python binding of the C ABI in include/fd_gb300.h (argument marshalling only).
+
+Every step of forward and inverse dynamics runs in the CUDA library
+``libfd_gb300.so``; this module passes torch device pointers and the current
+CUDA stream through ctypes. There is no CPU fallback: a missing library or a CPU
+tensor raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ALGOS = {"abia": 0, "jsiia": 1, "cfa": 2}
+PRECS = {"fp64": 0, "fp32": 1, "mixed": 2}
+STATUS = {0: "FD_OK", 1: "FD_ERR_INVALID_ARG", 2: "FD_ERR_NOT_SPD", 3: "FD_ERR_OOM",
+          4: "FD_ERR_CUDA", 5: "FD_ERR_TIMEOUT", 6: "FD_ERR_NUMERIC", 7: "FD_ERR_BUSY",
+          8: "FD_ERR_UNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libfd_gb300.so (building it with nvcc if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise FDError(4, f"CUDA library not built: {path}")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        i32, i64 = ctypes.c_int32, ctypes.c_int64
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.fd_last_error.restype = ctypes.c_char_p
+        lib.fd_abi_version.restype = i32
+        lib.fd_create_chain.argtypes = [i32, i64p, dp, dp, dp, dp, i32, ctypes.POINTER(vp)]
+        lib.fd_destroy_chain.argtypes = [vp]
+        lib.fd_chain_info.argtypes = [vp, i32p, i64p, i32p]
+        lib.fd_batch_create.argtypes = [vp, i32, i32p, ctypes.POINTER(vp)]
+        lib.fd_batch_destroy.argtypes = [vp]
+        lib.fd_batch_info.argtypes = [vp, i32p, i64p, i32p]
+        lib.fd_workspace_size.argtypes = [vp, i32, i32, i32]
+        lib.fd_workspace_size.restype = sz
+        lib.fd_solve_batch.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp, vp]
+        lib.fd_inverse_dynamics.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
+        for f in ("fd_create_chain", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
+                  "fd_batch_destroy", "fd_batch_info", "fd_solve_batch", "fd_inverse_dynamics"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise FDError(st, load().fd_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class ChainSet:
+    """A set of serial chains resident on one GPU (fd_create_chain)."""
+
+    def __init__(self, model, device: int = 0):
+        lib = load()
+        self._lib = lib
+        off = np.ascontiguousarray(model.offsets, dtype=np.int64)
+        ax = np.ascontiguousarray(model.axes, dtype=np.float64)
+        fr = np.ascontiguousarray(model.frames, dtype=np.float64)
+        J = np.ascontiguousarray(model.inertias, dtype=np.float64)
+        g = np.ascontiguousarray(model.gravity, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib.fd_create_chain(int(off.shape[0] - 1),
+                                   off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   _dptr(ax), _dptr(fr), _dptr(J), _dptr(g), int(device),
+                                   ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+        self.offsets = off.copy()
+
+    def info(self):
+        n = ctypes.c_int32(); L = ctypes.c_int64(); m = ctypes.c_int32()
+        _check(self._lib.fd_chain_info(self.handle, ctypes.byref(n), ctypes.byref(L),
+                                       ctypes.byref(m)))
+        return n.value, L.value, m.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.fd_destroy_chain(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A batch plan (fd_batch_create): problem p uses chain chain_index[p]."""
+
+    def __init__(self, chains: ChainSet, chain_index=None):
+        lib = load()
+        self._lib = lib
+        self.chains = chains
+        h = ctypes.c_void_p()
+        if chain_index is None:
+            n_problems = chains.info()[0]
+            _check(lib.fd_batch_create(chains.handle, n_problems, None, ctypes.byref(h)))
+        else:
+            ci = np.ascontiguousarray(chain_index, dtype=np.int32)
+            n_problems = int(ci.shape[0])
+            _check(lib.fd_batch_create(chains.handle, n_problems,
+                                       ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       ctypes.byref(h)))
+        self.handle = h
+        n = ctypes.c_int32(); L = ctypes.c_int64(); m = ctypes.c_int32()
+        _check(lib.fd_batch_info(h, ctypes.byref(n), ctypes.byref(L), ctypes.byref(m)))
+        self.n_problems, self.n_state_links, self.max_links = n.value, L.value, m.value
+
+    def workspace_size(self, algo, prec="fp64", team=0) -> int:
+        a = -1 if algo in (None, "id") else ALGOS[algo]
+        return int(self._lib.fd_workspace_size(self.handle, a, PRECS[prec], int(team)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.fd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _state_dtype(prec):
+    torch = _torch()
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+def _check_state(t, batch, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise FDError(1, f"{name} must be a CUDA tensor (there is no CPU path)")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != batch.n_state_links:
+        raise FDError(1, f"{name}: need contiguous {dtype} of {batch.n_state_links} elements, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+
+
+def workspace(batch: Batch, algo, prec="fp64", team=0, device=None):
+    torch = _torch()
+    n = batch.workspace_size(algo, prec, team)
+    # the caching allocator returns blocks aligned to at least 512 bytes
+    return torch.empty(max(n, 1), dtype=torch.uint8,
+                       device=device if device is not None else f"cuda:{batch.chains.device}")
+
+
+def solve(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", team=0, out=None, ws=None,
+          status=None, stream=None):
+    """qdd = FD(q, qd, tau) for every problem of ``batch`` (fd_solve_batch)."""
+    torch = _torch()
+    dt = _state_dtype(prec)
+    for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau")):
+        _check_state(t, batch, dt, nm)
+    if out is None:
+        out = torch.empty_like(q)
+    _check_state(out, batch, dt, "qddot")
+    if ws is None:
+        ws = workspace(batch, algo, prec, team, q.device)
+    if status is not None and (status.dtype != torch.int32 or not status.is_cuda
+                               or status.numel() < batch.n_problems):
+        raise FDError(1, "status must be a CUDA int32 tensor of n_problems elements")
+    s = stream if stream is not None else torch.cuda.current_stream(q.device)
+    _check(load().fd_solve_batch(batch.handle, q.data_ptr(), qd.data_ptr(), tau.data_ptr(),
+                                 out.data_ptr(), ALGOS[algo], PRECS[prec], int(team),
+                                 ws.data_ptr(), ws.numel(),
+                                 None if status is None else status.data_ptr(),
+                                 ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+def inverse_dynamics(batch: Batch, q, qd, qdd, prec="fp64", team=0, out=None, ws=None,
+                     stream=None):
+    """tau = ID(q, qd, qdd) with gravity (fd_inverse_dynamics)."""
+    torch = _torch()
+    dt = _state_dtype(prec)
+    for t, nm in ((q, "q"), (qd, "qdot"), (qdd, "qddot")):
+        _check_state(t, batch, dt, nm)
+    if out is None:
+        out = torch.empty_like(q)
+    if ws is None:
+        ws = workspace(batch, None, prec, team, q.device)
+    s = stream if stream is not None else torch.cuda.current_stream(q.device)
+    _check(load().fd_inverse_dynamics(batch.handle, q.data_ptr(), qd.data_ptr(), qdd.data_ptr(),
+                                      out.data_ptr(), PRECS[prec], int(team), ws.data_ptr(),
+                                      ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+    return out

@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, exports
+every entry point that include/fd_gb300.h declares, validates its arguments
+before touching the device, and fails loudly (no CPU fallback) without one."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1609_06779_gb300 import build as fdbuild
+from paper_1609_06779_gb300 import fd, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(fd_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fdbuild.build()
+    return fd.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert "fd_solve_batch" in declared and "fd_create_chain" in declared
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert lib.fd_abi_version() == 1
+
+
+def _create(model, lib):
+    h = ctypes.c_void_p()
+    off = np.ascontiguousarray(model.offsets, dtype=np.int64)
+    dp = lambda a: np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(
+        ctypes.POINTER(ctypes.c_double))
+    st = lib.fd_create_chain(int(off.shape[0] - 1),
+                             off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                             dp(model.axes), dp(model.frames), dp(model.inertias),
+                             dp(model.gravity), 0, ctypes.byref(h))
+    return st, h
+
+
+def test_invalid_models_rejected_before_any_device_call(lib):
+    base = synth.random_chains([3, 2], seed=0)
+
+    def variant(fn):
+        m = synth.random_chains([3, 2], seed=0)
+        fn(m)
+        return m
+
+    cases = {
+        "zero axis": variant(lambda m: m.axes.__setitem__(1, 0.0)),
+        "not a rotation": variant(lambda m: m.frames.__setitem__((0, 0), 2.0)),
+        "reflection": variant(lambda m: m.frames.__setitem__((0, slice(0, 9)),
+                                                             np.diag([1, 1, -1.0]).reshape(9))),
+        "non-symmetric inertia": variant(lambda m: m.inertias.__setitem__((2, 1), 5.0)),
+        "indefinite inertia": variant(lambda m: m.inertias.__setitem__(
+            (4, slice(None)), (-np.eye(6)).reshape(36))),
+        "nan gravity": variant(lambda m: m.gravity.__setitem__(0, np.nan)),
+    }
+    for name, m in cases.items():
+        st, h = _create(m, lib)
+        assert st == 1, name
+        assert h.value is None
+        assert len(lib.fd_last_error()) > 0
+    bad_off = synth.random_chains([3, 2], seed=0)
+    bad_off.offsets = np.array([0, 4, 3], dtype=np.int64)
+    assert _create(bad_off, lib)[0] == 1
+    # a valid model gets past validation; without a GPU the call must fail loudly
+    st, h = _create(base, lib)
+    if st != 0:
+        assert st == 4, fd.STATUS.get(st)
+        assert b"CUDA" in lib.fd_last_error() or b"device" in lib.fd_last_error()
+    else:
+        lib.fd_destroy_chain(h)
+
+
+def test_null_handles_are_invalid(lib):
+    assert lib.fd_destroy_chain(None) == 1
+    assert lib.fd_batch_destroy(None) == 1
+    assert lib.fd_solve_batch(None, None, None, None, None, 2, 0, 0, None, 0, None, None) == 1
+    assert lib.fd_inverse_dynamics(None, None, None, None, None, 0, 0, None, 0, None) == 1
+    assert lib.fd_workspace_size(None, 2, 0, 0) == 0
+
+
+def test_python_binding_refuses_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-GPU path")
+    with pytest.raises(fd.FDError):
+        fd.ChainSet(synth.random_chains([2], seed=0))
