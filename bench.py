@@ -1,0 +1,351 @@
+"""Benchmark: batched forward dynamics of 65 536 independent 32-link chains.
+
+One step = ABIA, JSIIA and CFA each solving the whole batch in FP64 (3 x 65 536
+FD solves) through the C ABI, inputs resident on the device. Prints one JSON
+line (rank 0). ``--impl reference`` times the FP64 CPU oracle instead.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1609_06779_gb300 import roofline, synth  # noqa: E402
+
+N_CHAINS = 65536
+N_LINKS = 32
+ALGOS = ("abia", "jsiia", "cfa")
+METRIC = "FD solves/s (32-link, batch 64K) ABIA/JSIIA/CFA"
+WORKLOAD = "65536 independent 32-link revolute chains (random models, seed 0), FP64"
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--chains", type=int, default=N_CHAINS)
+    ap.add_argument("--links", type=int, default=N_LINKS)
+    ap.add_argument("--team", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, path, index):
+        self.path, self.proc = path, None
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per link of `kernel` from the committed ncu summary, if the
+    kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except Exception:
+        return None
+    if rec.get("csrc_sha") != csrc_sha():
+        return None
+    return rec
+
+
+def csrc_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1609_06779_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_oracle(model, st, n_problems, budget_s=10.0, threads=None):
+    """Time the FP64 CPU oracle (the three algorithms) on a bounded sample."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    n = int(model.offsets[1] - model.offsets[0])
+    sample = min(n_problems, 4096)
+    # the first `sample` chains as their own model
+    L = sample * n
+    sub = synth.ChainModel(model.axes[:L], model.frames[:L], model.inertias[:L],
+                           model.offsets[:sample + 1].copy(), model.gravity)
+    q, qd, tau = st.q[:L], st.qdot[:L], st.tau[:L]
+    algos = {"abia": "aba", "jsiia": "cholesky", "cfa": "cfa"}
+    t0 = time.perf_counter()
+    solved = 0
+    while True:
+        for a in ALGOS:
+            oracle.fd(sub, q, qd, tau, algo=algos[a], n_threads=threads)
+            solved += sample
+        el = time.perf_counter() - t0
+        if el > budget_s:
+            break
+    return {"value": solved / el, "unit": "FD solves/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {sample} of {n_problems} chains x {{ABA, Cholesky (JSIIA), CFA+OEE}},"
+                      f" {solved} solves in {el:.1f} s, FP64, OpenMP across chains"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    model = synth.random_chains([args.links] * args.chains, seed=0)
+    st = synth.random_states(model.n_links_total, seed=1)
+    import oracle
+    threads = os.cpu_count() or 1
+    sample = 512
+    L = sample * args.links
+    sub = synth.ChainModel(model.axes[:L], model.frames[:L], model.inertias[:L],
+                           model.offsets[:sample + 1].copy(), model.gravity)
+    algos = {"abia": "aba", "jsiia": "cholesky", "cfa": "cfa"}
+    for _ in range(args.warmup):
+        oracle.fd(sub, st.q[:L], st.qdot[:L], st.tau[:L], algo="cfa", n_threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for a in ALGOS:
+            oracle.fd(sub, st.q[:L], st.qdot[:L], st.tau[:L], algo=algos[a], n_threads=threads)
+    el = time.perf_counter() - t0
+    val = 3 * sample * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "FD solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "chains": args.chains, "links": args.links,
+                       "step": f"ABIA+JSIIA+CFA on a bounded sample of {sample} chains"},
+            "cpu_baseline": {"value": val, "unit": "FD solves/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"{sample} of {args.chains} chains per step"},
+            "e2e": {"value": val, "unit": "FD solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1609_06779_gb300 import fd
+
+    # weak scaling: every rank solves its own 65 536-chain batch (no data exchange)
+    model = synth.random_chains([args.links] * args.chains, seed=rank)
+    st = synth.random_states(model.n_links_total, seed=1000 + rank)
+    cs = fd.ChainSet(model, device=local)
+    batch = fd.Batch(cs)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=dev)
+    q, qd, tau = (t(x, torch.float64) for x in (st.q, st.qdot, st.tau))
+    out = {a: torch.empty_like(q) for a in ALGOS}
+    ws = {a: fd.workspace(batch, a, "fp64", args.team, dev) for a in ALGOS}
+    stream = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        for k, a in enumerate(ALGOS):
+            if evs is not None:
+                evs[k].record(stream)
+            fd.solve(batch, q, qd, tau, algo=a, prec="fp64", team=args.team, out=out[a],
+                     ws=ws[a], stream=stream)
+        if evs is not None:
+            evs[3].record(stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clk = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                              else ".", f".clocks_rank{rank}.csv"), local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with clk:
+        time.sleep(0.3)
+        t_begin = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_begin.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t_begin.elapsed_time(t_end)
+    per_algo_ms = {a: float(np.mean([evs[s][k].elapsed_time(evs[s][k + 1])
+                                     for s in range(args.steps)])) for k, a in enumerate(ALGOS)}
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    solves = 3 * args.chains * world * args.steps
+    value = solves / (total_ms / 1e3)
+
+    # per-algorithm roofline (FP64 pipe: the kernels are ALU bound)
+    lengths = [args.links] * args.chains
+    rl = {}
+    for a in ALGOS:
+        fl = roofline.flops(a, lengths)
+        ach = fl / (per_algo_ms[a] / 1e3) / 1e12
+        rl[a] = {"ms": per_algo_ms[a], "tflops": ach, "frac": ach / FP64_PEAK_TFLOPS,
+                 "solves_per_s": args.chains / (per_algo_ms[a] / 1e3)}
+    dom = max(ALGOS, key=lambda a: per_algo_ms[a])
+    tr = traffic_record(f"{dom}_kernel")
+    traffic = None
+    if tr is not None:
+        traffic = tr["bytes_per_link"] * args.chains * args.links
+    roof = {"bound": "alu", "achieved": rl[dom]["tflops"], "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": rl[dom]["frac"], "traffic": traffic,
+            "kernel": f"{dom}_kernel<double,double,team>",
+            "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s), not measured",
+            "algorithmic_flops_per_launch": roofline.flops(dom, lengths),
+            "algorithmic_bytes_per_launch": roofline.bytes_per_link("fp64") * args.chains * args.links}
+
+    # FP32 and mixed variants of each algorithm (context; not part of the step)
+    variants = {}
+    if rank == 0:
+        q32, qd32, tau32 = (x.float() for x in (q, qd, tau))
+        for prec in ("fp32", "mixed"):
+            for a in ALGOS:
+                w = fd.workspace(batch, a, prec, args.team, dev)
+                o = torch.empty_like(q32)
+                for _ in range(2):
+                    fd.solve(batch, q32, qd32, tau32, algo=a, prec=prec, team=args.team,
+                             out=o, ws=w)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(3):
+                    fd.solve(batch, q32, qd32, tau32, algo=a, prec=prec, team=args.team,
+                             out=o, ws=w)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 3
+                variants[f"{a}_{prec}"] = {"ms": ms, "solves_per_s": args.chains / (ms / 1e3)}
+                del w
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        hq, hqd, htau = (x.cpu().pin_memory() for x in (q, qd, tau))
+        hout = {a: torch.empty(q.shape, dtype=torch.float64).pin_memory() for a in ALGOS}
+        dq, dqd, dtau = torch.empty_like(q), torch.empty_like(q), torch.empty_like(q)
+
+        def e2e_step():
+            dq.copy_(hq, non_blocking=True)
+            dqd.copy_(hqd, non_blocking=True)
+            dtau.copy_(htau, non_blocking=True)
+            for a in ALGOS:
+                fd.solve(batch, dq, dqd, dtau, algo=a, prec="fp64", team=args.team, out=out[a],
+                         ws=ws[a], stream=stream)
+                hout[a].copy_(out[a], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ksteps = max(1, min(args.steps, 5))
+        for _ in range(ksteps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        nb = q.numel() * 8
+        e2e = {"value": 3 * args.chains * world * ksteps / (ms / 1e3), "unit": "FD solves/s",
+               "h2d_bytes_per_step": 3 * nb, "d2h_bytes_per_step": 3 * nb,
+               "steps": ksteps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle(model, st, args.chains)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "FD solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "chains_per_gpu": args.chains,
+                           "links": args.links, "step": "ABIA + JSIIA + CFA, FP64, one launch each",
+                           "team": args.team or "auto",
+                           "l2": "inputs larger than L2 (FP64 model arena 940 MB), no flush",
+                           "parallelism": f"replicas x{world}, chains partitioned, no exchange"},
+                "per_algo": rl, "variants_fp32": variants,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,76 @@
+"""Algorithmic work per problem, for the roofline of each kernel.
+
+Counts are the floating-point operations of the method as the kernels carry it
+out in canonical link frames (S_i = e_1), with a fused multiply-add counted as 2
+and every other add, multiply, divide or reciprocal square root as 1; sin/cos of
+the joint angles are not counted. The serial (team = 1) schedule is the
+reference: the scan's extra compositions for team > 1 are overhead, not work.
+
+Primitive costs (flops): Ad_{g^-1} x or Ad_{g^-1}^T x = 42, symmetric 6x6 times
+a vector = 66, ad_V^T x = 33, joint transform = 18; 5x5 Cholesky = 60, one 5x5
+triangular solve = 25.
+
+Bytes: the model record (56 entries of the arithmetic type per link) and the
+four state vectors (q, qdot, tau in, qdd out) per link; the workspace is
+intermediate traffic, not algorithmic.
+"""
+from __future__ import annotations
+
+import math
+
+ADJ, SYM6, ADT, JT = 42, 66, 33, 18
+CHOL5, TRI5 = 60, 25
+
+
+def id_flops(n: int) -> int:
+    """Eq. 2a-2d: transform 18, twist 43, acceleration 50, f_i 171, force 49."""
+    return n * (JT + (ADJ + 1) + (ADJ + 8) + (2 * SYM6 + ADT + 6) + (ADJ + 7))
+
+
+def abia_flops(n: int) -> int:
+    """ID + articulated-inertia recursion (Pa 63 + 1, pa 18, congruence 12 adjoint
+    applications, + J 21, bias transport 42) for n-1 links + forward pass 56."""
+    per_abi = 64 + 18 + 12 * ADJ + 21 + ADJ
+    return id_flops(n) + max(n - 1, 0) * per_abi + n * (ADJ + 14)
+
+
+def jsiia_flops(n: int) -> int:
+    """ID + lower-triangle columns of M by ID (forward transports, then J Vd,
+    accumulation and transport per link of the column) + Cholesky n^3/3 + two
+    triangular solves 2 n^2."""
+    cols = ADJ * n * (n - 1) // 2 + (SYM6 + 6 + ADJ) * n * (n + 1) // 2
+    return id_flops(n) + cols + (n ** 3) // 3 + 2 * n * n
+
+
+def oee_flops(n: int) -> int:
+    """Odd-even elimination (Algorithm 2): ceil(log2 n) levels of per-row
+    Cholesky, the E part (Z, Z Z^T, E, E R: 470, plus E U: 250 while row i+2d
+    exists) and the K part (370), then the final block solves (110 per row)."""
+    levels = math.ceil(math.log2(n)) if n > 1 else 0
+    f = 0
+    for j in range(1, levels + 1):
+        d = 1 << (j - 1)
+        f += n * CHOL5
+        e_rows = max(n - d, 0)
+        f += e_rows * (5 * TRI5 + 165 + 5 * TRI5 + 55)
+        f += max(n - 2 * d, 0) * 250
+        f += e_rows * (5 * TRI5 + 165 + TRI5 + 55)
+    return f + n * (CHOL5 + 2 * TRI5)
+
+
+def cfa_flops(n: int) -> int:
+    """ID + A blocks (D 477, U 540) + R = -B tau (120) + OEE + CalcAcc (120)."""
+    return id_flops(n) + n * (477 + 540 + 120) + oee_flops(n) + n * 120
+
+
+FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops}
+
+
+def flops(algo: str, lengths) -> int:
+    f = FLOPS[algo]
+    return int(sum(f(int(n)) for n in lengths))
+
+
+def bytes_per_link(prec: str) -> int:
+    es = 8 if prec == "fp64" else 4
+    return 56 * es + 4 * es
