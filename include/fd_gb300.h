@@ -168,6 +168,36 @@ fd_status fd_inverse_dynamics(fd_batch_t batch, const void *q, const void *qdot,
                               const void *qddot, void *tau, fd_prec prec, int32_t team,
                               void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * fd_solve_cfa_static -- CFA forward dynamics that allocates nothing.
+ *
+ * The paper has no counterpart: this is a deployment variant of fd_solve_batch
+ * with algo = FD_CFA. It is for callers that cannot call cudaMalloc (or any
+ * allocating routine) when they solve: a control loop with a hard deadline, a
+ * host callback or a framework that owns all device memory and forbids raw
+ * allocations. Instead of a caller workspace it uses a scratch array of 32 MiB
+ * compiled into the library as a file-scope device variable; every GPU that
+ * loads the library holds that array until the process exits.
+ *
+ * Problem p is chain p of `chain` (no batch plan); q, qdot, tau (inputs) and
+ * qddot (output) are device arrays of the chain set's total link count, packed
+ * in chain order, double for FD_FP64 and float for FD_FP32 / FD_MIXED. team and
+ * status as for fd_solve_batch. Limits: at most 65 536 chains, and the CFA
+ * workspace of all links must fit in 32 MiB - 256 KiB (FD_FP64: 1 184 bytes per
+ * link, about 28 000 links; FD_FP32 / FD_MIXED: about 31 000 links); larger sets
+ * return FD_ERR_INVALID_ARG with the sizes in fd_last_error().
+ *
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress and copies a constant problem map into it (synchronous);
+ * make that first call before any stream capture. Every call shares the one
+ * array and leaves its contents behind; nothing in it has to start at zero, but
+ * calls whose kernels overlap on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller.
+ */
+fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const void *qdot,
+                              const void *tau, void *qddot, fd_prec prec, int32_t team,
+                              int32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/fd_gb300.h"
+#include "fd_internal.h"
 #include "fd_launch.h"
 #include "fd_layout.h"
 
@@ -119,29 +120,9 @@ int pow2_floor(long long v) {
 
 }  // namespace
 
-struct fd_chain_s {
-  int device = 0;
-  int32_t n_chains = 0;
-  int64_t n_links = 0;
-  int32_t max_links = 0;
-  double grav[3] = {0, 0, 0};
-  std::vector<int64_t> h_off;
-  void *d_model64 = nullptr;
-  void *d_model32 = nullptr;
-  int64_t *d_off = nullptr;
-};
-
-struct fd_batch_s {
-  fd_chain_t chain = nullptr;
-  int32_t n_problems = 0;
-  int64_t n_state_links = 0;
-  int64_t sum_sq = 0;
-  int32_t max_links = 0;
-  int32_t *d_prob_chain = nullptr;
-  int64_t *d_state_off = nullptr;
-  int64_t *d_sq_off = nullptr;
-  int32_t *d_order = nullptr;
-};
+// Records an error message for fd_last_error from the library's other
+// translation units.
+fd_status fdk_fail(fd_status st, const char *msg) { return fail(st, "%s", msg); }
 
 extern "C" {
 

@@ -64,8 +64,10 @@ def load(build_if_missing: bool = True):
         lib.fd_workspace_size.restype = sz
         lib.fd_solve_batch.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp, vp]
         lib.fd_inverse_dynamics.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
+        lib.fd_solve_cfa_static.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, vp]
         for f in ("fd_create_chain", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
-                  "fd_batch_destroy", "fd_batch_info", "fd_solve_batch", "fd_inverse_dynamics"):
+                  "fd_batch_destroy", "fd_batch_info", "fd_solve_batch", "fd_inverse_dynamics",
+                  "fd_solve_cfa_static"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -222,4 +224,26 @@ def inverse_dynamics(batch: Batch, q, qd, qdd, prec="fp64", team=0, out=None, ws
     _check(load().fd_inverse_dynamics(batch.handle, q.data_ptr(), qd.data_ptr(), qdd.data_ptr(),
                                       out.data_ptr(), PRECS[prec], int(team), ws.data_ptr(),
                                       ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+def solve_cfa_static(chains: ChainSet, q, qd, tau, prec="fp64", team=0, out=None, status=None,
+                     stream=None):
+    """CFA for problem p = chain p with the library's static scratch
+    (fd_solve_cfa_static): no allocation by the library; ``out`` may be given to
+    avoid torch's allocation as well."""
+    torch = _torch()
+    dt = _state_dtype(prec)
+    n_links = chains.info()[1]
+    for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau")):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt \
+                or not t.is_contiguous() or t.numel() != n_links:
+            raise FDError(1, f"{nm}: need a contiguous CUDA {dt} tensor of {n_links} elements")
+    if out is None:
+        out = torch.empty_like(q)
+    s = stream if stream is not None else torch.cuda.current_stream(q.device)
+    _check(load().fd_solve_cfa_static(chains.handle, q.data_ptr(), qd.data_ptr(), tau.data_ptr(),
+                                      out.data_ptr(), PRECS[prec], int(team),
+                                      None if status is None else status.data_ptr(),
+                                      ctypes.c_void_p(s.cuda_stream)))
     return out
