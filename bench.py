@@ -203,6 +203,10 @@ def main():
     t = lambda a, dt: torch.tensor(a, dtype=dt, device=dev)
     q, qd, tau = (t(x, torch.float64) for x in (st.q, st.qdot, st.tau))
     out = {a: torch.empty_like(q) for a in ALGOS}
+    teams = {}
+    for a in ALGOS:  # schedule per algorithm, chosen by timing (untimed here)
+        teams[a] = args.team if args.team else fd.autotune(batch, q, qd, tau, algo=a, prec="fp64")
+    torch.cuda.empty_cache()
     ws = {a: fd.workspace(batch, a, "fp64", args.team, dev) for a in ALGOS}
     stream = torch.cuda.current_stream(dev)
 
@@ -271,6 +275,8 @@ def main():
         q32, qd32, tau32 = (x.float() for x in (q, qd, tau))
         for prec in ("fp32", "mixed"):
             for a in ALGOS:
+                if not args.team:
+                    fd.autotune(batch, q32, qd32, tau32, algo=a, prec=prec)
                 w = fd.workspace(batch, a, prec, args.team, dev)
                 o = torch.empty_like(q32)
                 for _ in range(2):
@@ -335,7 +341,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "chains_per_gpu": args.chains,
                            "links": args.links, "step": "ABIA + JSIIA + CFA, FP64, one launch each",
-                           "team": args.team or "auto",
+                           "team": teams,
                            "l2": "inputs larger than L2 (FP64 model arena 940 MB), no flush",
                            "parallelism": f"replicas x{world}, chains partitioned, no exchange"},
                 "per_algo": rl, "variants_fp32": variants,

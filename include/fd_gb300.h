@@ -118,6 +118,9 @@ fd_status fd_chain_info(fd_chain_t chain, int32_t *n_chains, int64_t *n_links,
 fd_status fd_batch_create(fd_chain_t chain, int32_t n_problems, const int32_t *chain_index,
                           fd_batch_t *out);
 
+/* Frees a batch plan. Allowed before or after fd_destroy_chain of its chain set;
+ * solving with a plan whose chain set was destroyed is an error the library
+ * cannot detect. */
 fd_status fd_batch_destroy(fd_batch_t batch);
 
 /* Total state entries (sum of the problems' link counts) of a batch. */
@@ -125,12 +128,14 @@ fd_status fd_batch_info(fd_batch_t batch, int32_t *n_problems, int64_t *n_state_
                         int32_t *max_links);
 
 /*
- * Threads that cooperate on one problem ("team"): 0 lets the library choose;
- * otherwise a power of two from 1 (one thread per chain: serial recursions) to
- * 32 (one warp per chain: warp-shuffle scans and OEE levels across lanes).
- * FD_ABIA runs its articulated-inertia recursion serially (the paper notes it
- * cannot be parallelised beyond a constant factor, Section III) and accepts only
- * team 1 (or 0).
+ * Threads that cooperate on one problem ("team"): 0 lets the library choose
+ * (the autotuned size if fd_autotune ran for this batch, algorithm and
+ * precision, else a size that fills the GPU); otherwise a power of two from 1
+ * (one thread per chain: serial recursions) through 32 (one warp per chain:
+ * warp-shuffle scans and OEE levels across lanes) to 256 (one block per chain:
+ * scans across warps through shared memory). FD_ABIA runs its articulated-
+ * inertia recursion serially (the paper notes it cannot be parallelised beyond
+ * a constant factor, Section III) and accepts only team 1 (or 0).
  */
 
 /* Bytes of device workspace fd_solve_batch / fd_inverse_dynamics need for
@@ -167,6 +172,48 @@ fd_status fd_solve_batch(fd_batch_t batch, const void *q, const void *qdot, cons
 fd_status fd_inverse_dynamics(fd_batch_t batch, const void *q, const void *qdot,
                               const void *qddot, void *tau, fd_prec prec, int32_t team,
                               void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * fd_autotune -- pick the team size for (batch, algo, prec) by timing.
+ *
+ * The paper leaves the parallel schedule to the implementation; this times
+ * every team size (1 .. 256, at most the longest chain rounded up to a power of
+ * two; ABIA: 1) whose workspace fits in workspace_bytes, one warm-up and two
+ * timed solves each with CUDA events on `stream`, and records the fastest in the
+ * batch plan: later calls with team 0 use it. Synchronises the stream. Inputs as
+ * fd_solve_batch (qddot is overwritten). *best_team (may be NULL) receives the
+ * choice.
+ */
+fd_status fd_autotune(fd_batch_t batch, fd_algo algo, fd_prec prec, const void *q,
+                      const void *qdot, const void *tau, void *qddot, void *workspace,
+                      size_t workspace_bytes, void *stream, int32_t *best_team);
+
+/*
+ * fd_solve_adjoint -- reverse-mode derivatives of qdd = FD(q, qdot, tau).
+ *
+ * Not in the paper; it follows from ID(q, qdot, FD(q, qdot, tau)) = tau
+ * (Eq. 2a-2d, Eq. 4): with lambda = M^{-1} qddot_bar, solved by the algorithm's
+ * own factorisation of M^{-1} (ABIA, JSIIA or CFA),
+ *   tau_bar  = lambda,
+ *   q_bar    = -(d ID/d q)^T lambda,   qdot_bar = -(d ID/d qdot)^T lambda,
+ *   mass_bar = -(d ID/d m)^T lambda    (link masses, centre of mass and
+ *                                       rotational inertia about it held fixed),
+ * with (d ID/d x)^T lambda computed by a reverse sweep of the inverse-dynamics
+ * recursions (three forward and three backward segmented scans).
+ * Inputs (device, n_state_links elements, dtype as fd_solve_batch): q, qdot,
+ * tau, qddot (the forward result; may be NULL, then it is recomputed) and
+ * qddot_bar. Outputs: q_bar, qdot_bar, tau_bar and mass_bar (may be NULL; needs
+ * rigid-body inertias, else FD_ERR_UNSUPPORTED). workspace: at least
+ * fd_adjoint_workspace_size(batch, algo, prec, team) bytes, 256-byte aligned.
+ * status as for fd_solve_batch (for the solve with M). Asynchronous on stream.
+ */
+size_t fd_adjoint_workspace_size(fd_batch_t batch, fd_algo algo, fd_prec prec, int32_t team);
+
+fd_status fd_solve_adjoint(fd_batch_t batch, const void *q, const void *qdot, const void *tau,
+                           const void *qddot, const void *qddot_bar, void *q_bar,
+                           void *qdot_bar, void *tau_bar, void *mass_bar, fd_algo algo,
+                           fd_prec prec, int32_t team, void *workspace, size_t workspace_bytes,
+                           int32_t *status, void *stream);
 
 /*
  * fd_solve_cfa_static -- CFA forward dynamics that allocates nothing.

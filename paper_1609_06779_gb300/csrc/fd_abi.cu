@@ -32,6 +32,7 @@ fd_status fail(fd_status st, const char *fmt, ...) {
 }
 
 fd_status cuda_fail(cudaError_t e, const char *what) {
+  cudaGetLastError();  // the status carries the error; do not leave it for the caller's runtime
   return fail(e == cudaErrorMemoryAllocation ? FD_ERR_OOM : FD_ERR_CUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
@@ -155,6 +156,7 @@ fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const d
     if (!std::isfinite(gravity[k])) return fail(FD_ERR_INVALID_ARG, "fd_create_chain: gravity");
 
   // Canonical link frames (joint axis = x axis of the child frame), model records.
+  bool rigid = true;
   std::vector<double> rec64(static_cast<size_t>(std::max<int64_t>(L, 1)) * fdk::REC, 0.0);
   for (int32_t k = 0; k < n_chains; ++k) {
     double Qprev[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
@@ -211,6 +213,16 @@ fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const d
           for (int k2 = 0; k2 < 6; ++k2) s += B[6 * k2 + r] * JB[6 * k2 + c];
           Jc[6 * r + c] = s;
         }
+      {  // rigid-body form: lower-right block m 1, off-diagonal block m c^ (skew)
+        const double m = Jc[6 * 3 + 3];
+        for (int r = 0; r < 3 && rigid; ++r)
+          for (int cc = 0; cc < 3; ++cc) {
+            if (std::fabs(Jc[6 * (3 + r) + 3 + cc] - (r == cc ? m : 0.0)) > 1e-9 * scale)
+              rigid = false;
+            if (std::fabs(Jc[6 * r + 3 + cc] + Jc[6 * cc + 3 + r]) > 1e-9 * scale) rigid = false;
+          }
+        if (!(m > 0.0)) rigid = false;
+      }
       double Lc[36], Ji[36];
       if (!chol6(Jc, Lc))
         return fail(FD_ERR_INVALID_ARG,
@@ -246,6 +258,7 @@ fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const d
   c->n_chains = n_chains;
   c->n_links = L;
   c->max_links = max_links;
+  c->rigid = rigid;
   std::memcpy(c->grav, gravity, sizeof c->grav);
   c->h_off.assign(link_offsets, link_offsets + n_chains + 1);
   const size_t b64 = rec64.size() * sizeof(double), b32 = rec32.size() * sizeof(float);
@@ -277,6 +290,7 @@ fd_status fd_destroy_chain(fd_chain_t c) {
   cudaFree(c->d_model32);
   cudaFree(c->d_off);
   cudaSetDevice(prev);
+  cudaGetLastError();  // leave no error state behind for other users of the runtime
   delete c;
   return FD_OK;
 }
@@ -326,6 +340,7 @@ fd_status fd_batch_create(fd_chain_t c, int32_t n_problems, const int32_t *chain
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto *b = new fd_batch_s();
   b->chain = c;
+  b->device = c->device;
   b->n_problems = n_problems;
   b->n_state_links = so.back();
   b->sum_sq = sq.back();
@@ -357,12 +372,13 @@ fd_status fd_batch_destroy(fd_batch_t b) {
   if (!b) return fail(FD_ERR_INVALID_ARG, "fd_batch_destroy: NULL");
   int prev = 0;
   cudaGetDevice(&prev);
-  cudaSetDevice(b->chain->device);
+  cudaSetDevice(b->device);
   cudaFree(b->d_prob_chain);
   cudaFree(b->d_order);
   cudaFree(b->d_state_off);
   cudaFree(b->d_sq_off);
   cudaSetDevice(prev);
+  cudaGetLastError();  // leave no error state behind for other users of the runtime
   delete b;
   return FD_OK;
 }
@@ -380,16 +396,18 @@ fd_status fd_batch_info(fd_batch_t b, int32_t *n_problems, int64_t *n_state_link
 
 namespace {
 
-int resolve_team(const fd_batch_s *b, int32_t algo, int32_t team) {
+int resolve_team(const fd_batch_s *b, int32_t algo, fd_prec prec, int32_t team) {
   if (algo == FD_ABIA) return 1;
   if (team > 0) return team;
-  // enough threads to fill the GPU (about 78k resident threads is a full GB300),
-  // but no more lanes than links
-  const long long want = 152LL * 512;
+  const int tuned = (algo >= 0 && algo < 3 && prec >= 0 && prec < 3) ? b->tuned[algo][prec] : 0;
+  if (tuned > 0) return tuned;
+  // about four resident warps' worth of lanes per FP64 unit of the GPU
+  // (152 SMs x 2048 threads), but no more lanes than links and at most 256
+  const long long want = 152LL * 2048;
   long long per = b->n_problems > 0 ? want / b->n_problems : 1;
   int p = pow2_floor(std::max<long long>(per, 1));
   int cap = 1;
-  while (cap < b->max_links && cap < 32) cap *= 2;
+  while (cap < b->max_links && cap < 256) cap *= 2;
   return std::min(p, cap);
 }
 
@@ -413,7 +431,10 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int team) {
   return w;
 }
 
-bool valid_team(int t) { return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32; }
+bool valid_team(int t) {
+  return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32 || t == 64 || t == 128 ||
+         t == 256;
+}
 
 }  // namespace
 
@@ -421,7 +442,7 @@ extern "C" {
 
 size_t fd_workspace_size(fd_batch_t b, int32_t algo, fd_prec prec, int32_t team) {
   if (!b) return 0;
-  const int t = resolve_team(b, algo, team);
+  const int t = resolve_team(b, algo, prec, team);
   const WsPlan w = ws_plan(b, algo, prec, t);
   return w.t_bytes + w.a_bytes;
 }
@@ -435,12 +456,12 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   if (algo != -1 && algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, algo);
   if (team < 0 || (team > 0 && !valid_team(team)))
-    return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 32", who, team);
+    return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 256", who, team);
   if (algo == FD_ABIA && team > 1)
     return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs one thread per problem (team 1)", who);
   if (b->n_problems == 0 || b->n_state_links == 0) return FD_OK;
   if (!q || !qd || !in3 || !out) return fail(FD_ERR_INVALID_ARG, "%s: NULL state array", who);
-  const int t = resolve_team(b, algo, team);
+  const int t = resolve_team(b, algo, prec, team);
   const WsPlan w = ws_plan(b, algo, prec, t);
   if (!ws || ws_bytes < w.t_bytes + w.a_bytes)
     return fail(FD_ERR_INVALID_ARG, "%s: workspace of %zu bytes, %zu needed", who, ws_bytes,
@@ -494,3 +515,178 @@ fd_status fd_inverse_dynamics(fd_batch_t b, const void *q, const void *qdot, con
 }
 
 }  // extern "C"
+
+extern "C" {
+
+size_t fd_adjoint_workspace_size(fd_batch_t b, fd_algo algo, fd_prec prec, int32_t team) {
+  if (!b) return 0;
+  const int t = resolve_team(b, algo, prec, team);
+  const WsPlan w = ws_plan(b, algo, prec, t);
+  const size_t ts = prec == FD_FP64 ? 8 : 4;
+  const size_t L = static_cast<size_t>(b->n_state_links);
+  return align256(L * ts) + std::max(w.t_bytes + w.a_bytes, align256(L * fdk::NT_ADJ * ts));
+}
+
+fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const void *tau,
+                           const void *qddot, const void *qddot_bar, void *q_bar,
+                           void *qdot_bar, void *tau_bar, void *mass_bar, fd_algo algo,
+                           fd_prec prec, int32_t team, void *workspace, size_t workspace_bytes,
+                           int32_t *status, void *stream) {
+  const char *who = "fd_solve_adjoint";
+  if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
+  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA)
+    return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, static_cast<int>(algo));
+  if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
+    return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
+  if (team < 0 || (team > 0 && !valid_team(team)))
+    return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 256", who, team);
+  if (algo == FD_ABIA && team > 1)
+    return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs one thread per problem (team 1)", who);
+  if (mass_bar && !b->chain->rigid)
+    return fail(FD_ERR_UNSUPPORTED,
+                "%s: mass gradients need rigid-body inertias (J = [[I - m c^c^, m c^], "
+                "[-m c^, m 1]])", who);
+  if (b->n_problems == 0 || b->n_state_links == 0) return FD_OK;
+  if (!q || !qdot || !tau || !qddot_bar || !q_bar || !qdot_bar || !tau_bar)
+    return fail(FD_ERR_INVALID_ARG, "%s: NULL array", who);
+  const size_t need = fd_adjoint_workspace_size(b, algo, prec, team);
+  if (!workspace || workspace_bytes < need)
+    return fail(FD_ERR_INVALID_ARG, "%s: workspace of %zu bytes, %zu needed", who,
+                workspace_bytes, need);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(FD_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", who);
+  const int t = resolve_team(b, algo, prec, team);
+  const WsPlan w = ws_plan(b, algo, prec, t);
+  const size_t ts = prec == FD_FP64 ? 8 : 4;
+  const size_t L = static_cast<size_t>(b->n_state_links);
+  char *qdd_scratch = static_cast<char *>(workspace);
+  char *region = qdd_scratch + align256(L * ts);
+  const int prec_k = prec == FD_FP64 ? 0 : (prec == FD_FP32 ? 1 : 2);
+
+  fdk::KArgs a{};
+  a.model = prec == FD_FP64 ? b->chain->d_model64 : b->chain->d_model32;
+  a.model_off = b->chain->d_off;
+  a.prob_chain = b->d_prob_chain;
+  a.state_off = b->d_state_off;
+  a.sq_off = b->d_sq_off;
+  a.order = b->d_order;
+  a.n_problems = b->n_problems;
+  a.team = t;
+  a.q = q;
+  a.qd = qdot;
+  a.status = status;
+  std::memcpy(a.grav, b->chain->grav, sizeof a.grav);
+  a.ws_t = region;
+  a.ws_a = region + w.t_bytes;
+
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(b->chain->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  auto s = static_cast<cudaStream_t>(stream);
+  auto run_fd = [&](fdk::KArgs &k) {
+    if (algo == FD_CFA) return fdk::launch_cfa(k, prec_k, t, s);
+    if (algo == FD_JSIIA) return fdk::launch_jsiia(k, prec_k, t, s);
+    return fdk::launch_abia(k, prec_k, s);
+  };
+  // 1. qdd (unless given)
+  const void *qdd = qddot;
+  if (!qdd) {
+    a.mode = fdk::MODE_FD;
+    a.in3 = tau;
+    a.out = qdd_scratch;
+    e = run_fd(a);
+    qdd = qdd_scratch;
+  }
+  // 2. lambda = M^{-1} qdd_bar with the algorithm's own factorisation: tau_bar
+  if (e == cudaSuccess) {
+    a.mode = fdk::MODE_LINEAR;
+    a.in3 = qddot_bar;
+    a.out = tau_bar;
+    e = run_fd(a);
+  }
+  // 3. q_bar, qdot_bar, mass_bar = -(d ID / d x)^T lambda
+  if (e == cudaSuccess) {
+    fdk::KArgs r = a;
+    r.mode = fdk::MODE_ID;
+    r.in3 = qdd;
+    r.lam = tau_bar;
+    r.out = q_bar;
+    r.out2 = qdot_bar;
+    r.out3 = mass_bar;
+    r.ws_t = region;
+    r.status = nullptr;
+    const int tr = algo == FD_ABIA ? resolve_team(b, FD_CFA, prec, 0) : t;
+    r.team = tr;
+    e = fdk::launch_adjoint_rnea(r, prec == FD_FP64 ? 0 : 1, tr, s);
+  }
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  return FD_OK;
+}
+
+}  // extern "C"
+
+extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const void *q,
+                                 const void *qdot, const void *tau, void *qddot,
+                                 void *workspace, size_t workspace_bytes, void *stream,
+                                 int32_t *best_team) {
+  const char *who = "fd_autotune";
+  if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
+  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA)
+    return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm", who);
+  if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
+    return fail(FD_ERR_INVALID_ARG, "%s: bad precision", who);
+  int cap = 1;
+  while (cap < b->max_links && cap < 256) cap *= 2;
+  std::vector<int> cand;
+  if (algo == FD_ABIA) cand.push_back(1);
+  else
+    for (int t = 1; t <= cap; t *= 2) cand.push_back(t);
+  if (b->n_problems == 0 || b->n_state_links == 0) {
+    if (best_team) *best_team = 1;
+    return FD_OK;
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto s = static_cast<cudaStream_t>(stream);
+  int best = 0;
+  float best_ms = 0.f;
+  fd_status st = FD_OK;
+  for (int t : cand) {
+    const WsPlan w = ws_plan(b, algo, prec, t);
+    if (w.t_bytes + w.a_bytes > workspace_bytes) continue;
+    st = launch_common(b, q, qdot, tau, qddot, algo, prec, t, workspace, workspace_bytes,
+                       nullptr, stream, who);
+    if (st != FD_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && st == FD_OK; ++r)
+      st = launch_common(b, q, qdot, tau, qddot, algo, prec, t, workspace, workspace_bytes,
+                         nullptr, stream, who);
+    cudaEventRecord(e1, s);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+      st = cuda_fail(e, who);
+      break;
+    }
+    if (st != FD_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best == 0 || ms < best_ms) {
+      best = t;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaSetDevice(prev);
+  if (st != FD_OK) return st;
+  if (best == 0) return fail(FD_ERR_INVALID_ARG, "%s: workspace too small for any team", who);
+  b->tuned[algo][prec] = best;
+  if (best_team) *best_team = best;
+  return FD_OK;
+}

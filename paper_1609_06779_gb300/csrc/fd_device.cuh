@@ -187,30 +187,67 @@ __device__ __forceinline__ void stv(T *dst, const T *x) {
 
 // --------------------------------------------------------------------- teams
 
-// P consecutive lanes of a warp cooperate on one problem (P a power of two, <= 32).
+// Threads per block for a team of P lanes: teams of up to 128 lanes share
+// 128-thread blocks; larger teams are one block each.
+template <int P>
+__host__ __device__ constexpr int block_for() {
+  return P > 128 ? P : 128;
+}
+
+// P lanes cooperate on one problem (P a power of two, 1..256). P <= 32: a
+// sub-warp, synchronised with __syncwarp and combined with shuffles. P > 32:
+// whole warps of one block, synchronised with a named barrier per team and
+// combined through shared memory.
 template <int P>
 struct Team {
   unsigned mask;
-  int r;
+  int r;    // lane within the team
+  int bar;  // named barrier of the team (P > 32)
   __device__ __forceinline__ Team() {
     const int lane = threadIdx.x & 31;
-    r = lane & (P - 1);
-    mask = (P == 32) ? 0xffffffffu : (((1u << P) - 1u) << (lane & ~(P - 1)));
+    if constexpr (P < 32) {
+      r = lane & (P - 1);
+      mask = ((1u << P) - 1u) << (lane & ~(P - 1));
+    } else if constexpr (P == 32) {
+      r = lane;
+      mask = 0xffffffffu;
+    } else {
+      r = threadIdx.x & (P - 1);
+      mask = 0xffffffffu;
+    }
+    bar = 1 + static_cast<int>(threadIdx.x) / (P > 32 ? P : 32);
   }
   __device__ __forceinline__ void sync() const {
-    if (P > 1) __syncwarp(mask);
+    if (P > 32) {
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(P) : "memory");
+    } else if (P > 1) {
+      __syncwarp(mask);
+    }
   }
+  // true on every lane if `b` is true on any lane of the team
+  __device__ __forceinline__ bool any(bool b) const {
+    if (P > 32) {
+      unsigned out;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+          "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+          : "=r"(out)
+          : "r"(static_cast<unsigned>(b)), "r"(bar), "r"(P)
+          : "memory");
+      return out != 0;
+    } else if (P > 1) {
+      return __any_sync(mask, b);
+    }
+    return b;
+  }
+  // shuffles within the warp part of the team (width min(P, 32))
   template <class V>
   __device__ __forceinline__ V up(V v, int d) const {
-    return __shfl_up_sync(mask, v, d, P);
+    return __shfl_up_sync(mask, v, d, P < 32 ? P : 32);
   }
   template <class V>
   __device__ __forceinline__ V down(V v, int d) const {
-    return __shfl_down_sync(mask, v, d, P);
-  }
-  template <class V>
-  __device__ __forceinline__ V bcast(V v, int src) const {
-    return __shfl_sync(mask, v, src, P);
+    return __shfl_down_sync(mask, v, d, P < 32 ? P : 32);
   }
 };
 
@@ -223,6 +260,37 @@ struct SegOp {
   T psi[6];
 };
 
+template <class T>
+__device__ __forceinline__ void segop_identity(SegOp<T> &o) {
+  se3_identity(o.h);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o.psi[k] = T(0);
+}
+
+// forward composition: earlier `e`, then later `l`  ->  l (+) e  (into out)
+template <class T>
+__device__ __forceinline__ void compose_fwd(const SegOp<T> &e, const SegOp<T> &l, SegOp<T> &out) {
+  T t[6];
+  adinv(l.h, e.psi, t);
+  SegOp<T> o;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o.psi[k] = t[k] + l.psi[k];
+  se3_mul(e.h, l.h, o.h);
+  out = o;
+}
+
+// backward composition (applied right to left): `m` then the later `l`
+template <class T>
+__device__ __forceinline__ void compose_bwd(const SegOp<T> &m, const SegOp<T> &l, SegOp<T> &out) {
+  T t[6];
+  adinvT(m.h, l.psi, t);
+  SegOp<T> o;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o.psi[k] = t[k] + m.psi[k];
+  se3_mul(m.h, l.h, o.h);
+  out = o;
+}
+
 template <int P, class T>
 __device__ __forceinline__ void shfl_op(const Team<P> &tm, const SegOp<T> &a, SegOp<T> &b, int d,
                                         bool up) {
@@ -234,9 +302,17 @@ __device__ __forceinline__ void shfl_op(const Team<P> &tm, const SegOp<T> &a, Se
   for (int k = 0; k < 6; ++k) b.psi[k] = up ? tm.up(a.psi[k], d) : tm.down(a.psi[k], d);
 }
 
+// shared-memory slots for the warp aggregates of multi-warp teams
+template <class T>
+__device__ __forceinline__ SegOp<T> *warp_slots() {
+  __shared__ __align__(16) unsigned char raw[32 * sizeof(SegOp<double>)];
+  return reinterpret_cast<SegOp<T> *>(raw);
+}
+
 // Exclusive forward scan over the team's segments (Section II-B: the operator
-// a_{i-1} (+) a_i = a_i a_{i-1}, Kogge-Stone schedule across lanes). Returns the
-// value entering this lane's segment, given x_base entering lane 0.
+// a_{i-1} (+) a_i = a_i a_{i-1}; Kogge-Stone across the lanes of a warp, then
+// across the warps of a team). Returns the value entering this lane's segment,
+// given x_base entering lane 0.
 template <int P, class T>
 __device__ __forceinline__ void team_scan_fwd(const Team<P> &tm, SegOp<T> op, const T *x_base,
                                               T *x_in) {
@@ -245,28 +321,32 @@ __device__ __forceinline__ void team_scan_fwd(const Team<P> &tm, SegOp<T> op, co
     for (int k = 0; k < 6; ++k) x_in[k] = x_base[k];
     return;
   } else {
+    constexpr int WP = P < 32 ? P : 32;
+    const int wl = tm.r & (WP - 1);  // lane within the warp part
 #pragma unroll
-  for (int d = 1; d < P; d <<= 1) {
-    SegOp<T> o;
-    shfl_op(tm, op, o, d, true);
-    if (tm.r >= d) {  // earlier (o) then mine (op)
-      T t[6];
-      adinv(op.h, o.psi, t);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) op.psi[k] += t[k];
-      se3_mul(o.h, op.h, op.h);
+    for (int d = 1; d < WP; d <<= 1) {
+      SegOp<T> o;
+      shfl_op(tm, op, o, d, true);
+      if (wl >= d) compose_fwd(o, op, op);
     }
-  }
-  SegOp<T> ex;
-  shfl_op(tm, op, ex, 1, true);
-  if (tm.r == 0) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) x_in[k] = x_base[k];
-  } else {
+    SegOp<T> ex;
+    shfl_op(tm, op, ex, 1, true);
+    if (wl == 0) segop_identity(ex);
+    if constexpr (P > 32) {
+      SegOp<T> *slot = warp_slots<T>();
+      const int w = static_cast<int>(threadIdx.x) >> 5;  // warp in block
+      const int w0 = w - (tm.r >> 5);                      // first warp of the team
+      if (wl == 31) slot[w] = op;
+      tm.sync();
+      SegOp<T> pre;
+      segop_identity(pre);
+      for (int k = w0; k < w; ++k) compose_fwd(pre, slot[k], pre);
+      tm.sync();
+      compose_fwd(pre, ex, ex);
+    }
     adinv(ex.h, x_base, x_in);
 #pragma unroll
     for (int k = 0; k < 6; ++k) x_in[k] += ex.psi[k];
-  }
   }
 }
 
@@ -277,24 +357,31 @@ __device__ __forceinline__ void team_scan_bwd(const Team<P> &tm, SegOp<T> op, T 
 #pragma unroll
   for (int k = 0; k < 6; ++k) y_in[k] = T(0);
   if constexpr (P > 1) {
+    constexpr int WP = P < 32 ? P : 32;
+    const int wl = tm.r & (WP - 1);
 #pragma unroll
-  for (int d = 1; d < P; d <<= 1) {
-    SegOp<T> o;
-    shfl_op(tm, op, o, d, false);
-    if (tm.r + d < P) {  // mine (op) then later (o), applied right to left
-      T t[6];
-      adinvT(op.h, o.psi, t);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) op.psi[k] += t[k];
-      se3_mul(op.h, o.h, op.h);
+    for (int d = 1; d < WP; d <<= 1) {
+      SegOp<T> o;
+      shfl_op(tm, op, o, d, false);
+      if (wl + d < WP) compose_bwd(op, o, op);
     }
-  }
-  SegOp<T> ex;
-  shfl_op(tm, op, ex, 1, false);
-  if (tm.r + 1 < P) {
+    SegOp<T> ex;
+    shfl_op(tm, op, ex, 1, false);
+    if (wl == WP - 1) segop_identity(ex);
+    if constexpr (P > 32) {
+      SegOp<T> *slot = warp_slots<T>();
+      const int w = static_cast<int>(threadIdx.x) >> 5;
+      const int wend = w - (tm.r >> 5) + P / 32;  // one past the team's last warp
+      if (wl == 0) slot[w] = op;
+      tm.sync();
+      SegOp<T> post;
+      segop_identity(post);
+      for (int k = wend - 1; k > w; --k) compose_bwd(slot[k], post, post);
+      tm.sync();
+      compose_bwd(ex, post, ex);
+    }
 #pragma unroll
     for (int k = 0; k < 6; ++k) y_in[k] = ex.psi[k];
-  }
   }
 }
 

@@ -17,10 +17,12 @@ struct fd_chain_s {
   void *d_model64 = nullptr;
   void *d_model32 = nullptr;
   int64_t *d_off = nullptr;
+  bool rigid = true;  // every inertia has the rigid-body form (mass gradients)
 };
 
 struct fd_batch_s {
   fd_chain_t chain = nullptr;
+  int device = 0;  // the chain set's device, kept so the plan can be freed on its own
   int32_t n_problems = 0;
   int64_t n_state_links = 0;
   int64_t sum_sq = 0;
@@ -29,6 +31,7 @@ struct fd_batch_s {
   int64_t *d_state_off = nullptr;
   int64_t *d_sq_off = nullptr;
   int32_t *d_order = nullptr;
+  int tuned[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // autotuned team per [algo][prec]
 };
 
 // Sets the calling thread's fd_last_error message and returns st.

@@ -57,8 +57,9 @@ __device__ __forceinline__ bool load_problem(const KArgs &A, const Team<P> &tm, 
 // Leaves g_i, V_i, f_i in the workspace.
 template <class T, int P>
 __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, const double *grav,
-                                        bool mode_fd) {
+                                        int mode) {
   const int a = pb.a, b = pb.b;
+  const bool mode_fd = mode == MODE_FD;
   SegOp<T> op;
   se3_identity(op.h);
   // joint transforms and this segment's product h = g_a ... g_{b-1}
@@ -67,7 +68,9 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
     joint_transform(pb.rec + static_cast<int64_t>(i) * REC, pb.q[i], g);
     st_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
     if (P > 1) se3_mul(op.h, g, op.h);
+    if (mode == MODE_LINEAR) pb.wt[static_cast<int64_t>(i) * NT + W_TD] = pb.in3[i];
   }
+  if (mode == MODE_LINEAR) return;
   const T zero6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   T x[6];
 
@@ -159,11 +162,11 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
 }
 
 template <class T, int P>
-__global__ void __launch_bounds__(128) id_kernel(KArgs A) {
+__global__ void __launch_bounds__(block_for<P>()) id_kernel(KArgs A) {
   Team<P> tm;
   Prob<T> pb;
   if (!load_problem<T, P>(A, tm, pb, NT)) return;
-  id_team<T, P>(tm, pb, A.grav, false);
+  id_team<T, P>(tm, pb, A.grav, MODE_ID);
   for (int i = pb.a; i < pb.b; ++i) pb.out[i] = pb.wt[static_cast<int64_t>(i) * NT + W_TD];
 }
 
@@ -315,7 +318,7 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
 }
 
 template <class T, class TA, int P>
-__global__ void __launch_bounds__(128) cfa_kernel(KArgs A) {
+__global__ void __launch_bounds__(block_for<P>()) cfa_kernel(KArgs A) {
   Team<P> tm;
   Prob<T> pb;
   if (!load_problem<T, P>(A, tm, pb, NT)) return;
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(128) cfa_kernel(KArgs A) {
   bool bad = false;
 
   // bias torque and tau_delta (Algorithm 1: CalcInvDyn, CalcDiffTorques)
-  id_team<T, P>(tm, pb, A.grav, true);
+  id_team<T, P>(tm, pb, A.grav, A.mode);
   tm.sync();
 
   // CalcA: D_i, U_i; R = -B tau_delta applied as -W^T (I-Gamma) J^{-1} (I-Gamma)^T S tau_delta
@@ -444,14 +447,14 @@ __global__ void __launch_bounds__(128) cfa_kernel(KArgs A) {
     pb.out[i] = qdd;
     if (!finite_t(qdd)) bad = true;
   }
-  const bool any_bad = P > 1 ? __any_sync(tm.mask, bad) : bad;
+  const bool any_bad = tm.any(bad);
   if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
 }
 
 // ------------------------------------------------------------------ JSIIA
 
 template <class T, class TA, int P>
-__global__ void __launch_bounds__(128) jsiia_kernel(KArgs A) {
+__global__ void __launch_bounds__(block_for<P>()) jsiia_kernel(KArgs A) {
   Team<P> tm;
   Prob<T> pb;
   if (!load_problem<T, P>(A, tm, pb, NT)) return;
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(128) jsiia_kernel(KArgs A) {
   TA *myacc = acc + static_cast<int64_t>(tm.r) * n * 6;
   bool bad = false;
 
-  id_team<T, P>(tm, pb, A.grav, true);
+  id_team<T, P>(tm, pb, A.grav, A.mode);
   for (int i = a; i < b; ++i) vec[i] = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]);
   tm.sync();
 
@@ -532,7 +535,7 @@ __global__ void __launch_bounds__(128) jsiia_kernel(KArgs A) {
     pb.out[i] = v;
     if (!finite_t(v)) bad = true;
   }
-  const bool any_bad = P > 1 ? __any_sync(tm.mask, bad) : bad;
+  const bool any_bad = tm.any(bad);
   if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
 }
 
@@ -576,7 +579,7 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
   const int n = pb.n;
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_ABIA;
   bool bad = false;
-  id_team<T, 1>(tm, pb, A.grav, true);
+  id_team<T, 1>(tm, pb, A.grav, A.mode);
 
   TA Pm[21], pbias[6];
   if (n > 0) {

@@ -14,10 +14,24 @@ cudaError_t launch_id(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_cfa(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_jsiia(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_abia(const KArgs &a, int prec, cudaStream_t s);
+cudaError_t launch_adjoint_rnea(const KArgs &a, int prec, int team, cudaStream_t s);
 
 inline unsigned grid_for(int n_problems, int team) {
+  const int block = team > BLOCK ? team : BLOCK;
   const long long threads = static_cast<long long>(n_problems) * team;
-  return static_cast<unsigned>((threads + BLOCK - 1) / BLOCK);
+  return static_cast<unsigned>((threads + block - 1) / block);
 }
+
+// Team sizes the kernels are built for: one thread up to a 256-thread block.
+#define FDK_TEAM_CASES(KERNEL, ...)                                               \
+  case 1: KERNEL<__VA_ARGS__, 1><<<g, block_for<1>(), 0, s>>>(a); break;          \
+  case 2: KERNEL<__VA_ARGS__, 2><<<g, block_for<2>(), 0, s>>>(a); break;          \
+  case 4: KERNEL<__VA_ARGS__, 4><<<g, block_for<4>(), 0, s>>>(a); break;          \
+  case 8: KERNEL<__VA_ARGS__, 8><<<g, block_for<8>(), 0, s>>>(a); break;          \
+  case 16: KERNEL<__VA_ARGS__, 16><<<g, block_for<16>(), 0, s>>>(a); break;       \
+  case 32: KERNEL<__VA_ARGS__, 32><<<g, block_for<32>(), 0, s>>>(a); break;       \
+  case 64: KERNEL<__VA_ARGS__, 64><<<g, block_for<64>(), 0, s>>>(a); break;       \
+  case 128: KERNEL<__VA_ARGS__, 128><<<g, block_for<128>(), 0, s>>>(a); break;    \
+  case 256: KERNEL<__VA_ARGS__, 256><<<g, block_for<256>(), 0, s>>>(a); break;
 
 }  // namespace fdk

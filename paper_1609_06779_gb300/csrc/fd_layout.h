@@ -57,6 +57,21 @@ constexpr int A_DD = 6;
 constexpr int A_UU = 7;
 constexpr int NA_ABIA = 8;
 
+// Adjoint (reverse inverse dynamics) per-link workspace of T.
+constexpr int J_G = 0;    // g_i (12)
+constexpr int J_V = 12;   // V_i
+constexpr int J_A = 18;   // Vd_i
+constexpr int J_F = 24;   // F_i
+constexpr int J_FB = 30;  // Fbar_i (f_i before the force pass)
+constexpr int J_AB = 36;  // Abar_i
+constexpr int J_VB = 42;  // Vbar_i
+constexpr int NT_ADJ = 48;
+
+// id_team modes (a zero-initialised KArgs means forward dynamics)
+constexpr int MODE_FD = 0;      // tau_delta = tau - ID(q, qd, 0)
+constexpr int MODE_ID = 1;      // tau = ID(q, qd, qdd)
+constexpr int MODE_LINEAR = 2;  // tau_delta = in3 (solve M x = in3: joint transforms only)
+
 struct KArgs {
   const void *model;         // [L][REC] of T
   const int64_t *model_off;  // [K + 1]
@@ -74,6 +89,10 @@ struct KArgs {
   void *ws_a;       // TA workspace
   int32_t *status;  // [N] or null
   double grav[3];
+  int32_t mode;     // MODE_FD (default) or MODE_LINEAR for the forward-dynamics kernels
+  const void *lam;  // adjoint: lambda = M^{-1} qdd_bar
+  void *out2;       // adjoint: qdot_bar
+  void *out3;       // adjoint: mass_bar (or null)
 };
 
 }  // namespace fdk

@@ -8,12 +8,7 @@ template <class T, class TA>
 static cudaError_t go(const KArgs &a, int team, cudaStream_t s) {
   const unsigned g = grid_for(a.n_problems, team);
   switch (team) {
-    case 1: jsiia_kernel<T, TA, 1><<<g, BLOCK, 0, s>>>(a); break;
-    case 2: jsiia_kernel<T, TA, 2><<<g, BLOCK, 0, s>>>(a); break;
-    case 4: jsiia_kernel<T, TA, 4><<<g, BLOCK, 0, s>>>(a); break;
-    case 8: jsiia_kernel<T, TA, 8><<<g, BLOCK, 0, s>>>(a); break;
-    case 16: jsiia_kernel<T, TA, 16><<<g, BLOCK, 0, s>>>(a); break;
-    case 32: jsiia_kernel<T, TA, 32><<<g, BLOCK, 0, s>>>(a); break;
+    FDK_TEAM_CASES(jsiia_kernel, T, TA)
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

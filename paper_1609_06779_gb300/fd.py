@@ -65,6 +65,14 @@ def load(build_if_missing: bool = True):
         lib.fd_solve_batch.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp, vp]
         lib.fd_inverse_dynamics.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
         lib.fd_solve_cfa_static.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, vp]
+        lib.fd_adjoint_workspace_size.argtypes = [vp, i32, i32, i32]
+        lib.fd_adjoint_workspace_size.restype = sz
+        lib.fd_solve_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32,
+                                         vp, sz, vp, vp]
+        lib.fd_solve_adjoint.restype = ctypes.c_int
+        lib.fd_autotune.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, sz, vp,
+                                    ctypes.POINTER(i32)]
+        lib.fd_autotune.restype = ctypes.c_int
         for f in ("fd_create_chain", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
                   "fd_batch_destroy", "fd_batch_info", "fd_solve_batch", "fd_inverse_dynamics",
                   "fd_solve_cfa_static"):
@@ -247,3 +255,91 @@ def solve_cfa_static(chains: ChainSet, q, qd, tau, prec="fp64", team=0, out=None
                                       None if status is None else status.data_ptr(),
                                       ctypes.c_void_p(s.cuda_stream)))
     return out
+
+
+def adjoint(batch: Batch, q, qd, tau, qdd_bar, qdd=None, algo="cfa", prec="fp64", team=0,
+            masses=True, ws=None, status=None, stream=None):
+    """Reverse-mode derivatives of qdd = FD(q, qd, tau) for the cotangent
+    ``qdd_bar`` (fd_solve_adjoint). Returns (q_bar, qd_bar, tau_bar, mass_bar);
+    mass_bar is None unless ``masses``."""
+    torch = _torch()
+    dt = _state_dtype(prec)
+    for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau"), (qdd_bar, "qddot_bar")):
+        _check_state(t, batch, dt, nm)
+    if qdd is not None:
+        _check_state(qdd, batch, dt, "qddot")
+    outs = [torch.empty_like(q) for _ in range(4 if masses else 3)]
+    if ws is None:
+        n = int(load().fd_adjoint_workspace_size(batch.handle, ALGOS[algo], PRECS[prec],
+                                                 int(team)))
+        ws = torch.empty(max(n, 1), dtype=torch.uint8, device=q.device)
+    s = stream if stream is not None else torch.cuda.current_stream(q.device)
+    _check(load().fd_solve_adjoint(batch.handle, q.data_ptr(), qd.data_ptr(), tau.data_ptr(),
+                                   None if qdd is None else qdd.data_ptr(), qdd_bar.data_ptr(),
+                                   outs[0].data_ptr(), outs[1].data_ptr(), outs[2].data_ptr(),
+                                   outs[3].data_ptr() if masses else None, ALGOS[algo],
+                                   PRECS[prec], int(team), ws.data_ptr(), ws.numel(),
+                                   None if status is None else status.data_ptr(),
+                                   ctypes.c_void_p(s.cuda_stream)))
+    return outs[0], outs[1], outs[2], (outs[3] if masses else None)
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class ForwardDynamics(torch.autograd.Function):
+        """qdd = FD(q, qd, tau) with the adjoint kernels as its backward."""
+
+        @staticmethod
+        def forward(ctx, q, qd, tau, batch, algo, prec, team):
+            qdd = solve(batch, q.contiguous(), qd.contiguous(), tau.contiguous(), algo=algo,
+                        prec=prec, team=team)
+            ctx.save_for_backward(q, qd, tau, qdd)
+            ctx.cfg = (batch, algo, prec, team)
+            return qdd
+
+        @staticmethod
+        def backward(ctx, g):
+            q, qd, tau, qdd = ctx.saved_tensors
+            batch, algo, prec, team = ctx.cfg
+            qb, qdb, tb, _ = adjoint(batch, q, qd, tau, g.contiguous(), qdd=qdd, algo=algo,
+                                     prec=prec, team=team, masses=False)
+            return qb, qdb, tb, None, None, None, None
+
+    return ForwardDynamics
+
+
+_FD_FN = None
+
+
+def forward_dynamics(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", team=0):
+    """Differentiable qdd = FD(q, qd, tau) (torch.autograd.Function)."""
+    global _FD_FN
+    if _FD_FN is None:
+        _FD_FN = _make_autograd()
+    return _FD_FN.apply(q, qd, tau, batch, algo, prec, team)
+
+
+def autotune(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", max_workspace_bytes=8 << 30,
+             stream=None) -> int:
+    """Time the team sizes (fd_autotune) and record the fastest in the batch plan;
+    returns it. Uses a workspace of at most ``max_workspace_bytes``."""
+    torch = _torch()
+    dt = _state_dtype(prec)
+    for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau")):
+        _check_state(t, batch, dt, nm)
+    need = 0
+    t = 1
+    while t <= 256:
+        n = batch.workspace_size(algo, prec, t)
+        if n <= max_workspace_bytes:
+            need = max(need, n)
+        t *= 2
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=q.device)
+    out = torch.empty_like(q)
+    best = ctypes.c_int32(0)
+    s = stream if stream is not None else torch.cuda.current_stream(q.device)
+    _check(load().fd_autotune(batch.handle, ALGOS[algo], PRECS[prec], q.data_ptr(), qd.data_ptr(),
+                              tau.data_ptr(), out.data_ptr(), ws.data_ptr(), ws.numel(),
+                              ctypes.c_void_p(s.cuda_stream), ctypes.byref(best)))
+    return best.value

@@ -56,7 +56,7 @@ RAGGED = [1, 2, 3, 5, 7, 8, 13, 31, 32, 33, 47, 64, 100]
 
 
 @pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa"])
-@pytest.mark.parametrize("team", [1, 2, 4, 8, 32])
+@pytest.mark.parametrize("team", [1, 2, 4, 8, 32, 64, 128, 256])
 def test_fd_fp64_ragged_parity(algo, team):
     if algo == "abia" and team != 1:
         pytest.skip("ABIA runs one thread per problem")
@@ -88,7 +88,7 @@ def test_fd_fp32_parity_short_chains(prec, algo):
         assert np.median(err) < 1e-5 and err.max() < bar, (team, err.max())
 
 
-@pytest.mark.parametrize("team", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("team", [1, 2, 4, 8, 16, 32, 64, 128, 256])
 def test_inverse_dynamics_fp64_parity(team):
     fd = _fd()
     model = synth.random_chains(RAGGED, seed=3)
@@ -198,3 +198,23 @@ def test_full_size_uniform_batch_sampled(prec):
         else:
             # measured and reported; the 1e-4 bar applies to well-conditioned chains
             assert np.median(err) < 1e-3, (algo, np.median(err))
+
+
+def test_autotune_records_a_team_and_matches():
+    fd = _fd()
+    model = synth.random_chains([32] * 2048 + [7] * 100, seed=71)
+    st = synth.random_states(model.n_links_total, seed=72)
+    cs = fd.ChainSet(model)
+    b = fd.Batch(cs)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    q, qd, tau = t(st.q), t(st.qdot), t(st.tau)
+    ref = oracle.fd(model, st.q, st.qdot, st.tau, n_threads=8)
+    for algo in ("abia", "jsiia", "cfa"):
+        best = fd.autotune(b, q, qd, tau, algo=algo)
+        assert best in (1, 2, 4, 8, 16, 32), (algo, best)
+        if algo == "abia":
+            assert best == 1
+        # team 0 now uses the tuned size: same workspace size as asking for it
+        assert b.workspace_size(algo, "fp64", 0) == b.workspace_size(algo, "fp64", best)
+        got = fd.solve(b, q, qd, tau, algo=algo).cpu().numpy()
+        assert _rel_err(got, ref, model.offsets).max() < 1e-10, algo

@@ -34,13 +34,15 @@ def test_static_scratch_cfa_matches_workspace_cfa(prec, tol):
     b = fd.Batch(cs)
     dt = torch.float64 if prec == "fp64" else torch.float32
     q, qd, tau = (torch.tensor(x, dtype=dt, device="cuda") for x in (st.q, st.qdot, st.tau))
-    ref = fd.solve(b, q, qd, tau, algo="cfa", prec=prec).double().cpu().numpy()
+    # the same team on both sides, so the two entry points run the same arithmetic
+    team = 32
+    ref = fd.solve(b, q, qd, tau, algo="cfa", prec=prec, team=team).double().cpu().numpy()
     stream = torch.cuda.current_stream()
     for call in range(2):
         out = torch.full_like(q, float("nan"))
         status = torch.full((cs.info()[0],), -1, dtype=torch.int32, device="cuda")
         rc = lib.fd_solve_cfa_static(cs.handle, q.data_ptr(), qd.data_ptr(), tau.data_ptr(),
-                                     out.data_ptr(), fd.PRECS[prec], 0, status.data_ptr(),
+                                     out.data_ptr(), fd.PRECS[prec], team, status.data_ptr(),
                                      ctypes.c_void_p(stream.cuda_stream))
         assert rc == 0, lib.fd_last_error()
         torch.cuda.synchronize()
