@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--team", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
     return ap.parse_args()
 
 
@@ -143,6 +146,82 @@ def cpu_oracle(model, st, n_problems, budget_s=10.0, threads=None):
     return {"value": solved / el, "unit": "FD solves/s", "cores": threads, "kind": "oracle",
             "sample": f"first {sample} of {n_problems} chains x {{ABA, Cholesky (JSIIA), CFA+OEE}},"
                       f" {solved} solves in {el:.1f} s, FP64, OpenMP across chains"}
+
+
+def serve_bench(seconds=10.0, rate=20000.0, per_size=False, budget=40 << 30, seed=0,
+                device=0):
+    """Open-loop Poisson stream of FD+gradient queries and 50-step rollouts
+    (dt = 1e-3) on chains of 6..256 links (log-uniform), 50/50; latency =
+    completion - scheduled arrival."""
+    from paper_1609_06779_gb300 import fd
+    rng = np.random.default_rng(seed)
+    n_models, n_templates, steps = 1024, 2048, 50
+    lengths = synth.log_uniform_lengths(n_models, 6, 256, seed=seed)
+    models = synth.random_chains(lengths, seed=seed + 1)
+    srv = fd.Server(device=device, budget_bytes=budget, per_size=per_size)
+    ids = [srv.add_model(models.chain(k)) for k in range(n_models)]
+    temps = []
+    for j in range(n_templates):
+        k = int(rng.integers(n_models))
+        n = int(lengths[k])
+        q = rng.uniform(-np.pi, np.pi, n)
+        qd = rng.standard_normal(n)
+        if j % 2 == 0:
+            temps.append((0, ids[k], n, q, qd, rng.standard_normal(n) * 10, rng.standard_normal(n)))
+        else:
+            temps.append((1, ids[k], n, q, qd, rng.standard_normal((steps, n)) * 10, None))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds * 1.2) + 16))
+    arrivals = arrivals[arrivals < seconds]
+    sched, kinds, links = {}, {}, {}
+    lat = {0: [], 1: []}
+    t0 = fd.serve_clock() + 0.05
+    k = 0
+    n_total = len(arrivals)
+    busy_refused = 0
+
+    def collect():
+        tk, _, done, st = srv.drain()
+        for t, d in zip(tk.tolist(), done.tolist()):
+            lat[kinds.pop(t)].append(d - sched.pop(t))
+
+    while k < n_total:
+        now = fd.serve_clock() - t0
+        while k < n_total and arrivals[k] <= now:
+            kind, mid, n, q, qd, tau, w = temps[k % n_templates]
+            try:
+                if kind == 0:
+                    t = srv.submit_grad(mid, q, qd, tau, w, algo="cfa")
+                else:
+                    t = srv.submit_rollout(mid, q, qd, tau, 1e-3, algo="abia")
+            except fd.FDError:
+                busy_refused += 1
+                k += 1
+                continue
+            sched[t] = t0 + arrivals[k]
+            kinds[t] = kind
+            k += 1
+        collect()
+        if k < n_total:
+            time.sleep(max(0.0, min(0.0005, arrivals[k] - (fd.serve_clock() - t0))))
+    t_end_arrivals = fd.serve_clock()
+    while sched and fd.serve_clock() - t_end_arrivals < 120:
+        collect()
+        time.sleep(0.001)
+    st = srv.stats()
+    srv.close()
+    span = max(fd.serve_clock() - t0, 1e-9)
+    out = {"rate_offered": rate, "seconds": seconds, "requests": n_total,
+           "refused": busy_refused, "unfinished": len(sched),
+           "per_size_launches": per_size, "ticks": st["ticks"], "launches": st["launches"],
+           "fd_solves_per_s": (len(lat[0]) + steps * len(lat[1])) / span,
+           "link_solves_per_s": st["link_solves"] / span,
+           "gpu_busy_frac": st["busy_seconds"] / span}
+    for kind, name in ((0, "fd_grad"), (1, "rollout50")):
+        v = np.array(lat[kind]) * 1e3
+        if len(v):
+            out[name] = {"n": int(len(v)), "p50_ms": float(np.percentile(v, 50)),
+                         "p99_ms": float(np.percentile(v, 99)), "max_ms": float(v.max())}
+    return out
 
 
 def reference_arm(args):
@@ -330,6 +409,15 @@ def main():
                "h2d_bytes_per_step": 3 * nb, "d2h_bytes_per_step": 3 * nb,
                "steps": ksteps}
 
+    serving = None
+    if rank == 0 and not args.no_serve:
+        del ws, out
+        torch.cuda.empty_cache()
+        serving = {"continuous": serve_bench(args.serve_seconds, args.serve_rate, False,
+                                             device=local),
+                   "per_size_baseline": serve_bench(args.serve_seconds, args.serve_rate, True,
+                                                    device=local)}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle(model, st, args.chains)
@@ -345,7 +433,7 @@ def main():
                            "l2": "inputs larger than L2 (FP64 model arena 940 MB), no flush",
                            "parallelism": f"replicas x{world}, chains partitioned, no exchange"},
                 "per_algo": rl, "variants_fp32": variants,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
                 "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -245,6 +245,104 @@ fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const void *qdot,
                               const void *tau, void *qddot, fd_prec prec, int32_t team,
                               int32_t *status, void *stream);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * A server owns one device allocation of mem_budget_bytes (its memory budget)
+ * and a worker thread. Chain models are registered once and stay resident.
+ * Requests name a model and carry their state; they are admitted in arrival
+ * order as link slots and memory free up, and every tick the worker runs one
+ * forward-dynamics launch per algorithm over all admitted requests ("continuous
+ * batching": requests arriving while others are on the GPU join the next tick),
+ * the adjoint over new FD+gradient requests and one integration step over the
+ * rollouts. Not in the paper (its experiments solve fixed groups); built on the
+ * same kernels as fd_solve_batch and fd_solve_adjoint, FP64 only, with a fixed
+ * team per algorithm so a request's arithmetic does not depend on the mix.
+ */
+typedef struct fd_server_s *fd_server_t;
+
+typedef enum fd_request_kind {
+  FD_REQ_FD_GRAD = 0, /* qdd = FD(q, qdot, tau) and its adjoint for qddot_bar */
+  FD_REQ_ROLLOUT = 1  /* `steps` semi-implicit Euler steps:
+                         qdot += dt FD(q, qdot, tau_k); q += dt qdot */
+} fd_request_kind;
+
+#define FD_SERVE_PER_SIZE 1 /* flag: one launch per distinct chain length (the
+                               static per-size batching baseline) */
+
+typedef struct fd_request {
+  int32_t kind;     /* fd_request_kind */
+  int32_t algo;     /* FD_ABIA or FD_CFA */
+  int32_t model_id; /* from fd_serve_add_model */
+  int32_t steps;    /* FD_REQ_ROLLOUT: >= 1 */
+  double dt;        /* FD_REQ_ROLLOUT: > 0 */
+  const double *q;         /* host [n] initial joint positions */
+  const double *qdot;      /* host [n] initial joint velocities */
+  const double *tau;       /* host: [n] (FD_GRAD) or [steps][n] torques per step */
+  const double *qddot_bar; /* host [n], FD_GRAD: cotangent of qdd */
+} fd_request;
+
+typedef struct fd_result {
+  int32_t status;      /* FD_OK, FD_ERR_NOT_SPD or FD_ERR_NUMERIC */
+  int32_t n_links;
+  int32_t steps_done;
+  int32_t pad;
+  double submit_time;  /* fd_serve_clock() seconds */
+  double done_time;    /* when the result reached host memory */
+  /* caller buffers of n_links doubles, each may be NULL */
+  double *q, *qdot;    /* ROLLOUT: final state */
+  double *qddot;       /* FD_GRAD: qdd; ROLLOUT: qdd of the last step */
+  double *q_bar, *qdot_bar, *tau_bar; /* FD_GRAD: the adjoint */
+} fd_result;
+
+typedef struct fd_serve_stats_t {
+  uint64_t ticks, launches, completed, queued, active;
+  int64_t link_slots_used, link_slots;
+  double link_solves;  /* sum over ticks of the links of the requests solved */
+  double busy_seconds; /* worker time spent in ticks */
+} fd_serve_stats_t;
+
+/* Monotonic clock (seconds) of the server's timestamps (CLOCK_MONOTONIC). */
+double fd_serve_clock(void);
+
+/* Creates a server on `device`: allocates mem_budget_bytes (>= 16 MiB) once and
+ * starts the worker. gravity in the base frame. flags: 0 or FD_SERVE_PER_SIZE. */
+fd_status fd_serve_create(int32_t device, size_t mem_budget_bytes, const double gravity[3],
+                          int32_t flags, fd_server_t *out);
+
+/* Registers a chain model (host arrays as fd_create_chain, one chain of
+ * n_links links); it stays resident until fd_serve_remove_model. FD_ERR_OOM if
+ * the model region of the budget is full. */
+fd_status fd_serve_add_model(fd_server_t server, int32_t n_links, const double *joint_axes,
+                             const double *link_frames, const double *spatial_inertias,
+                             int32_t *model_id);
+
+/* FD_ERR_BUSY while requests that use the model are pending. */
+fd_status fd_serve_remove_model(fd_server_t server, int32_t model_id);
+
+/* Queues a request (its host arrays are copied); *ticket identifies it.
+ * FD_ERR_INVALID_ARG if it can never fit the budget, FD_ERR_BUSY if the queue
+ * is full (retry later). */
+fd_status fd_serve_submit(fd_server_t server, const fd_request *request, uint64_t *ticket);
+
+/* FD_OK and the result (ticket released) if done; FD_ERR_BUSY if not yet. */
+fd_status fd_serve_poll(fd_server_t server, uint64_t ticket, fd_result *out);
+
+/* As fd_serve_poll, but waits at most timeout_ms; FD_ERR_TIMEOUT if not done. */
+fd_status fd_serve_wait(fd_server_t server, uint64_t ticket, int32_t timeout_ms,
+                        fd_result *out);
+
+/* Releases up to `max` finished requests without copying their states:
+ * tickets, submit and completion times and statuses (submit_times, statuses may
+ * be NULL); *count receives how many. For load generators. */
+fd_status fd_serve_drain(fd_server_t server, int32_t max, uint64_t *tickets,
+                         double *submit_times, double *done_times, int32_t *statuses,
+                         int32_t *count);
+
+fd_status fd_serve_stats(fd_server_t server, fd_serve_stats_t *out);
+
+/* Stops the worker (pending requests are dropped) and frees everything. */
+fd_status fd_serve_destroy(fd_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -121,6 +121,95 @@ int pow2_floor(long long v) {
 
 }  // namespace
 
+// Re-expresses one chain (links first .. first+n-1 of the packed user arrays) in
+// canonical link frames (x axis = joint axis) and writes its model records to
+// rec[0 .. n*REC). Clears *rigid if an inertia is not of the rigid-body form.
+fd_status fdk_pack_chain(int64_t first, int64_t n, const double *joint_axes,
+                         const double *link_frames, const double *spatial_inertias, double *rec,
+                         bool *rigid) {
+  double Qprev[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  for (int64_t i = first; i < first + n; ++i) {
+    const double *ax = joint_axes + 3 * i;
+    const double *fr = link_frames + 12 * i;
+    const double *J = spatial_inertias + 36 * i;
+    const double na = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+    if (!(na > 1e-12) || !std::isfinite(na))
+      return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld has a zero joint axis",
+                  static_cast<long long>(i));
+    const double a[3] = {ax[0] / na, ax[1] / na, ax[2] / na};
+    double RtR[9];
+    m3_tmul(fr, fr, RtR);
+    for (int r = 0; r < 9; ++r)
+      if (!(std::fabs(RtR[r] - (r % 4 == 0 ? 1.0 : 0.0)) < 1e-9))
+        return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld frame is not a rotation",
+                    static_cast<long long>(i));
+    const double det = fr[0] * (fr[4] * fr[8] - fr[5] * fr[7]) -
+                       fr[1] * (fr[3] * fr[8] - fr[5] * fr[6]) +
+                       fr[2] * (fr[3] * fr[7] - fr[4] * fr[6]);
+    if (!(det > 0.0))
+      return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld frame has det <= 0",
+                  static_cast<long long>(i));
+    double scale = 0.0;
+    for (int r = 0; r < 36; ++r) scale = std::max(scale, std::fabs(J[r]));
+    for (int r = 0; r < 6; ++r)
+      for (int c = r + 1; c < 6; ++c)
+        if (!(std::fabs(J[6 * r + c] - J[6 * c + r]) <= 1e-9 * scale))
+          return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld inertia not symmetric",
+                      static_cast<long long>(i));
+    double Q[9];
+    axis_frame(a, Q);
+    // R0' = Qprev^T R0 Q, p0' = Qprev^T p0
+    double t[9], R0c[9], p0c[3];
+    m3_mul(fr, Q, t);
+    m3_tmul(Qprev, t, R0c);
+    for (int r = 0; r < 3; ++r)
+      p0c[r] = Qprev[r] * fr[9] + Qprev[3 + r] * fr[10] + Qprev[6 + r] * fr[11];
+    // J' = diag(Q, Q)^T J diag(Q, Q)
+    double B[36] = {0};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) B[6 * r + c] = B[6 * (r + 3) + c + 3] = Q[3 * r + c];
+    double JB[36], Jc[36];
+    for (int r = 0; r < 6; ++r)
+      for (int c = 0; c < 6; ++c) {
+        double s = 0;
+        for (int k2 = 0; k2 < 6; ++k2) s += 0.5 * (J[6 * r + k2] + J[6 * k2 + r]) * B[6 * k2 + c];
+        JB[6 * r + c] = s;
+      }
+    for (int r = 0; r < 6; ++r)
+      for (int c = 0; c < 6; ++c) {
+        double s = 0;
+        for (int k2 = 0; k2 < 6; ++k2) s += B[6 * k2 + r] * JB[6 * k2 + c];
+        Jc[6 * r + c] = s;
+      }
+    {  // rigid-body form: lower-right block m 1, off-diagonal block m c^ (skew)
+      const double m = Jc[6 * 3 + 3];
+      for (int r = 0; r < 3 && *rigid; ++r)
+        for (int cc = 0; cc < 3; ++cc) {
+          if (std::fabs(Jc[6 * (3 + r) + 3 + cc] - (r == cc ? m : 0.0)) > 1e-9 * scale)
+            *rigid = false;
+          if (std::fabs(Jc[6 * r + 3 + cc] + Jc[6 * cc + 3 + r]) > 1e-9 * scale) *rigid = false;
+        }
+      if (!(m > 0.0)) *rigid = false;
+    }
+    double Lc[36], Ji[36];
+    if (!chol6(Jc, Lc))
+      return fail(FD_ERR_INVALID_ARG,
+                  "fd_create_chain: link %lld inertia is not positive definite",
+                  static_cast<long long>(i));
+    inv_from_chol6(Lc, Ji);
+    double *rc = rec + static_cast<size_t>(i - first) * fdk::REC;
+    std::memcpy(rc + fdk::REC_R0, R0c, 9 * sizeof(double));
+    std::memcpy(rc + fdk::REC_P0, p0c, 3 * sizeof(double));
+    for (int r = 0; r < 6; ++r)
+      for (int c = r; c < 6; ++c) {
+        rc[fdk::REC_J + s6(r, c)] = Jc[6 * r + c];
+        rc[fdk::REC_JI + s6(r, c)] = 0.5 * (Ji[6 * r + c] + Ji[6 * c + r]);
+      }
+    std::memcpy(Qprev, Q, sizeof Qprev);
+  }
+  return FD_OK;
+}
+
 // Records an error message for fd_last_error from the library's other
 // translation units.
 fd_status fdk_fail(fd_status st, const char *msg) { return fail(st, "%s", msg); }
@@ -159,86 +248,11 @@ fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const d
   bool rigid = true;
   std::vector<double> rec64(static_cast<size_t>(std::max<int64_t>(L, 1)) * fdk::REC, 0.0);
   for (int32_t k = 0; k < n_chains; ++k) {
-    double Qprev[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-    for (int64_t i = link_offsets[k]; i < link_offsets[k + 1]; ++i) {
-      const double *ax = joint_axes + 3 * i;
-      const double *fr = link_frames + 12 * i;
-      const double *J = spatial_inertias + 36 * i;
-      const double na = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
-      if (!(na > 1e-12) || !std::isfinite(na))
-        return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld has a zero joint axis",
-                    static_cast<long long>(i));
-      const double a[3] = {ax[0] / na, ax[1] / na, ax[2] / na};
-      double RtR[9];
-      m3_tmul(fr, fr, RtR);
-      for (int r = 0; r < 9; ++r)
-        if (!(std::fabs(RtR[r] - (r % 4 == 0 ? 1.0 : 0.0)) < 1e-9))
-          return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld frame is not a rotation",
-                      static_cast<long long>(i));
-      const double det = fr[0] * (fr[4] * fr[8] - fr[5] * fr[7]) -
-                         fr[1] * (fr[3] * fr[8] - fr[5] * fr[6]) +
-                         fr[2] * (fr[3] * fr[7] - fr[4] * fr[6]);
-      if (!(det > 0.0))
-        return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld frame has det <= 0",
-                    static_cast<long long>(i));
-      double scale = 0.0;
-      for (int r = 0; r < 36; ++r) scale = std::max(scale, std::fabs(J[r]));
-      for (int r = 0; r < 6; ++r)
-        for (int c = r + 1; c < 6; ++c)
-          if (!(std::fabs(J[6 * r + c] - J[6 * c + r]) <= 1e-9 * scale))
-            return fail(FD_ERR_INVALID_ARG, "fd_create_chain: link %lld inertia not symmetric",
-                        static_cast<long long>(i));
-      double Q[9];
-      axis_frame(a, Q);
-      // R0' = Qprev^T R0 Q, p0' = Qprev^T p0
-      double t[9], R0c[9], p0c[3];
-      m3_mul(fr, Q, t);
-      m3_tmul(Qprev, t, R0c);
-      for (int r = 0; r < 3; ++r)
-        p0c[r] = Qprev[r] * fr[9] + Qprev[3 + r] * fr[10] + Qprev[6 + r] * fr[11];
-      // J' = diag(Q, Q)^T J diag(Q, Q)
-      double B[36] = {0};
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) B[6 * r + c] = B[6 * (r + 3) + c + 3] = Q[3 * r + c];
-      double JB[36], Jc[36];
-      for (int r = 0; r < 6; ++r)
-        for (int c = 0; c < 6; ++c) {
-          double s = 0;
-          for (int k2 = 0; k2 < 6; ++k2) s += 0.5 * (J[6 * r + k2] + J[6 * k2 + r]) * B[6 * k2 + c];
-          JB[6 * r + c] = s;
-        }
-      for (int r = 0; r < 6; ++r)
-        for (int c = 0; c < 6; ++c) {
-          double s = 0;
-          for (int k2 = 0; k2 < 6; ++k2) s += B[6 * k2 + r] * JB[6 * k2 + c];
-          Jc[6 * r + c] = s;
-        }
-      {  // rigid-body form: lower-right block m 1, off-diagonal block m c^ (skew)
-        const double m = Jc[6 * 3 + 3];
-        for (int r = 0; r < 3 && rigid; ++r)
-          for (int cc = 0; cc < 3; ++cc) {
-            if (std::fabs(Jc[6 * (3 + r) + 3 + cc] - (r == cc ? m : 0.0)) > 1e-9 * scale)
-              rigid = false;
-            if (std::fabs(Jc[6 * r + 3 + cc] + Jc[6 * cc + 3 + r]) > 1e-9 * scale) rigid = false;
-          }
-        if (!(m > 0.0)) rigid = false;
-      }
-      double Lc[36], Ji[36];
-      if (!chol6(Jc, Lc))
-        return fail(FD_ERR_INVALID_ARG,
-                    "fd_create_chain: link %lld inertia is not positive definite",
-                    static_cast<long long>(i));
-      inv_from_chol6(Lc, Ji);
-      double *rc = rec64.data() + static_cast<size_t>(i) * fdk::REC;
-      std::memcpy(rc + fdk::REC_R0, R0c, 9 * sizeof(double));
-      std::memcpy(rc + fdk::REC_P0, p0c, 3 * sizeof(double));
-      for (int r = 0; r < 6; ++r)
-        for (int c = r; c < 6; ++c) {
-          rc[fdk::REC_J + s6(r, c)] = Jc[6 * r + c];
-          rc[fdk::REC_JI + s6(r, c)] = 0.5 * (Ji[6 * r + c] + Ji[6 * c + r]);
-        }
-      std::memcpy(Qprev, Q, sizeof Qprev);
-    }
+    const fd_status st = fdk_pack_chain(link_offsets[k], link_offsets[k + 1] - link_offsets[k],
+                                        joint_axes, link_frames, spatial_inertias,
+                                        rec64.data() + static_cast<size_t>(link_offsets[k]) * fdk::REC,
+                                        &rigid);
+    if (st != FD_OK) return st;
   }
   std::vector<float> rec32(rec64.size());
   for (size_t k = 0; k < rec64.size(); ++k) rec32[k] = static_cast<float>(rec64[k]);

@@ -36,3 +36,8 @@ struct fd_batch_s {
 
 // Sets the calling thread's fd_last_error message and returns st.
 fd_status fdk_fail(fd_status st, const char *msg);
+
+// Packs one chain's model records in canonical link frames (see fd_abi.cu).
+fd_status fdk_pack_chain(int64_t first, int64_t n, const double *joint_axes,
+                         const double *link_frames, const double *spatial_inertias, double *rec,
+                         bool *rigid);

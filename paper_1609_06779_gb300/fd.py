@@ -343,3 +343,153 @@ def autotune(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", max_workspace_by
                               tau.data_ptr(), out.data_ptr(), ws.data_ptr(), ws.numel(),
                               ctypes.c_void_p(s.cuda_stream), ctypes.byref(best)))
     return best.value
+
+
+# ------------------------------------------------------------------- serving
+
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("algo", ctypes.c_int32), ("model_id", ctypes.c_int32),
+                ("steps", ctypes.c_int32), ("dt", ctypes.c_double),
+                ("q", ctypes.c_void_p), ("qdot", ctypes.c_void_p), ("tau", ctypes.c_void_p),
+                ("qddot_bar", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_links", ctypes.c_int32),
+                ("steps_done", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("submit_time", ctypes.c_double), ("done_time", ctypes.c_double),
+                ("q", ctypes.c_void_p), ("qdot", ctypes.c_void_p), ("qddot", ctypes.c_void_p),
+                ("q_bar", ctypes.c_void_p), ("qdot_bar", ctypes.c_void_p),
+                ("tau_bar", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("active", ctypes.c_uint64), ("link_slots_used", ctypes.c_int64),
+                ("link_slots", ctypes.c_int64), ("link_solves", ctypes.c_double),
+                ("busy_seconds", ctypes.c_double)]
+
+
+REQ_FD_GRAD, REQ_ROLLOUT = 0, 1
+SERVE_PER_SIZE = 1
+
+
+def _serve_lib():
+    lib = load()
+    if not getattr(lib, "_serve_ready", False):
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        i32, u64 = ctypes.c_int32, ctypes.c_uint64
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.fd_serve_clock.restype = ctypes.c_double
+        lib.fd_serve_create.argtypes = [i32, sz, dp, i32, ctypes.POINTER(vp)]
+        lib.fd_serve_add_model.argtypes = [vp, i32, dp, dp, dp, ctypes.POINTER(i32)]
+        lib.fd_serve_remove_model.argtypes = [vp, i32]
+        lib.fd_serve_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(u64)]
+        lib.fd_serve_poll.argtypes = [vp, u64, ctypes.POINTER(_Result)]
+        lib.fd_serve_wait.argtypes = [vp, u64, i32, ctypes.POINTER(_Result)]
+        lib.fd_serve_drain.argtypes = [vp, i32, ctypes.POINTER(u64), dp, dp,
+                                       ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.fd_serve_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+        lib.fd_serve_destroy.argtypes = [vp]
+        for f in ("fd_serve_create", "fd_serve_add_model", "fd_serve_remove_model",
+                  "fd_serve_submit", "fd_serve_poll", "fd_serve_wait", "fd_serve_drain",
+                  "fd_serve_stats", "fd_serve_destroy"):
+            getattr(lib, f).restype = ctypes.c_int
+        lib._serve_ready = True
+    return lib
+
+
+def serve_clock() -> float:
+    return float(_serve_lib().fd_serve_clock())
+
+
+class Server:
+    """Continuous-batching forward-dynamics server (fd_serve_*)."""
+
+    def __init__(self, device=0, budget_bytes=1 << 30, gravity=(0.0, 0.0, -9.81),
+                 per_size=False):
+        lib = _serve_lib()
+        self._lib = lib
+        g = np.ascontiguousarray(gravity, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib.fd_serve_create(int(device), int(budget_bytes), _dptr(g),
+                                   SERVE_PER_SIZE if per_size else 0, ctypes.byref(h)))
+        self.handle = h
+        self.n_of = {}
+
+    def add_model(self, model) -> int:
+        """Register one chain (a ChainModel with a single chain)."""
+        ax = np.ascontiguousarray(model.axes, dtype=np.float64)
+        fr = np.ascontiguousarray(model.frames, dtype=np.float64)
+        J = np.ascontiguousarray(model.inertias, dtype=np.float64)
+        mid = ctypes.c_int32()
+        _check(self._lib.fd_serve_add_model(self.handle, ax.shape[0], _dptr(ax), _dptr(fr),
+                                            _dptr(J), ctypes.byref(mid)))
+        self.n_of[mid.value] = ax.shape[0]
+        return mid.value
+
+    def remove_model(self, model_id):
+        _check(self._lib.fd_serve_remove_model(self.handle, int(model_id)))
+
+    def _submit(self, kind, algo, model_id, q, qd, tau, w=None, steps=1, dt=0.0):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (q, qd, tau)]
+        wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        rq = _Request(kind, ALGOS[algo], int(model_id), int(steps), float(dt),
+                      arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                      None if wv is None else wv.ctypes.data)
+        t = ctypes.c_uint64()
+        _check(self._lib.fd_serve_submit(self.handle, ctypes.byref(rq), ctypes.byref(t)))
+        return t.value
+
+    def submit_grad(self, model_id, q, qd, tau, qdd_bar, algo="cfa") -> int:
+        return self._submit(REQ_FD_GRAD, algo, model_id, q, qd, tau, qdd_bar)
+
+    def submit_rollout(self, model_id, q, qd, taus, dt, algo="abia") -> int:
+        taus = np.ascontiguousarray(taus, dtype=np.float64)
+        return self._submit(REQ_ROLLOUT, algo, model_id, q, qd, taus.reshape(-1),
+                            steps=taus.shape[0], dt=dt)
+
+    def wait(self, ticket, timeout_ms=60000, n=4096):
+        """Blocks up to timeout_ms; returns a dict of results (raises FDError on
+        FD_ERR_TIMEOUT and other failures). ``n``: at least the chain's links."""
+        bufs = {k: np.full(n, np.nan) for k in ("q", "qdot", "qddot", "q_bar", "qdot_bar",
+                                                  "tau_bar")}
+        res = _Result()
+        for k, v in bufs.items():
+            setattr(res, k, v.ctypes.data)
+        _check(self._lib.fd_serve_wait(self.handle, int(ticket), int(timeout_ms),
+                                       ctypes.byref(res)))
+        m = res.n_links
+        out = {k: v[:m].copy() for k, v in bufs.items()}
+        out.update(status=res.status, steps_done=res.steps_done, submit_time=res.submit_time,
+                   done_time=res.done_time)
+        return out
+
+    def drain(self, max_n=65536):
+        """Finished requests: (tickets, submit times, done times, statuses)."""
+        if getattr(self, "_dbuf", None) is None or self._dbuf[0] < max_n:
+            self._dbuf = (max_n, (ctypes.c_uint64 * max_n)(), np.empty(max_n), np.empty(max_n),
+                          (ctypes.c_int32 * max_n)(), ctypes.c_int32())
+        _, t, sub, done, st, cnt = self._dbuf
+        _check(self._lib.fd_serve_drain(self.handle, max_n, t, _dptr(sub), _dptr(done), st,
+                                        ctypes.byref(cnt)))
+        k = cnt.value
+        return (np.frombuffer(t, dtype=np.uint64)[:k].copy(), sub[:k].copy(), done[:k].copy(),
+                np.frombuffer(st, dtype=np.int32)[:k].copy())
+
+    def stats(self):
+        s = _Stats()
+        _check(self._lib.fd_serve_stats(self.handle, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.fd_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -99,3 +99,17 @@ def test_python_binding_refuses_cpu_tensors():
         pytest.skip("checks the no-GPU path")
     with pytest.raises(fd.FDError):
         fd.ChainSet(synth.random_chains([2], seed=0))
+
+
+def test_server_without_a_device_fails_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-GPU path")
+    g = (ctypes.c_double * 3)(0.0, 0.0, -9.81)
+    h = ctypes.c_void_p()
+    lib.fd_serve_create.argtypes = [ctypes.c_int32, ctypes.c_size_t,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_void_p)]
+    assert lib.fd_serve_create(0, 64 << 20, g, 0, ctypes.byref(h)) == 4
+    assert lib.fd_serve_create(0, 1 << 10, g, 0, ctypes.byref(h)) == 1   # budget too small
+    assert h.value is None
