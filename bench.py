@@ -22,6 +22,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_1609_06779_gb300 import dist as fdist  # noqa: E402
 from paper_1609_06779_gb300 import roofline, synth  # noqa: E402
 
 N_CHAINS = 65536
@@ -44,16 +45,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return fdist.env()
 
 
 class Clocks:
@@ -224,6 +223,126 @@ def serve_bench(seconds=10.0, rate=20000.0, per_size=False, budget=40 << 30, see
     return out
 
 
+def _time_ms(fn, reps=3, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_configs(dev):
+    """The paper-shaped workloads besides the headline batch: one 7-link chain
+    with 1024 states (launch-bound; CUDA-graph replay), long chains (256 x 256,
+    64 x 1024) and an uneven batch of 100 000 chains (6..512 links, mixed
+    precision) as one launch against one launch per distinct length."""
+    import torch
+    from paper_1609_06779_gb300 import fd
+    t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    res = {}
+
+    # 1 chain x 7 links, 1024 states (shared model), FP64
+    m = synth.random_chains([7], seed=0)
+    ci, _ = synth.replicate_model(m, 1024)
+    st = synth.random_states(7 * 1024, seed=1)
+    cs = fd.ChainSet(m, device=dev.index or 0)
+    b = fd.Batch(cs, ci)
+    q, qd, tau = t64(st.q), t64(st.qdot), t64(st.tau)
+    r1 = {}
+    for a in ALGOS:
+        team = fd.autotune(b, q, qd, tau, algo=a)
+        ws = fd.workspace(b, a, "fp64", 0, dev)
+        out = torch.empty_like(q)
+        launch_us = 1e3 * _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, out=out, ws=ws), 50, 5)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            fd.solve(b, q, qd, tau, algo=a, out=out, ws=ws)
+        torch.cuda.current_stream(dev).wait_stream(s)
+        with torch.cuda.graph(g):
+            fd.solve(b, q, qd, tau, algo=a, out=out, ws=ws)
+        graph_us = 1e3 * _time_ms(g.replay, 50, 5)
+        r1[a] = {"team": team, "launch_us": launch_us, "graph_replay_us": graph_us,
+                 "solves_per_s": 1024 / (graph_us * 1e-6)}
+    res["1x7_links_1024_states_fp64"] = r1
+    del cs, b
+
+    # long chains, FP64
+    for n, count in ((256, 256), (1024, 64)):
+        m = synth.random_chains([n] * count, seed=n)
+        st = synth.random_states(m.n_links_total, seed=n + 1)
+        cs = fd.ChainSet(m, device=dev.index or 0)
+        b = fd.Batch(cs)
+        q, qd, tau = t64(st.q), t64(st.qdot), t64(st.tau)
+        rl = {}
+        for a in ALGOS:
+            if a == "jsiia" and n > 256:
+                continue  # cubic in n: about 0.3 s per solve of this batch
+            team = 128 if a == "jsiia" else fd.autotune(b, q, qd, tau, algo=a)
+            ws = fd.workspace(b, a, "fp64", team, dev)
+            out = torch.empty_like(q)
+            ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, team=team, out=out, ws=ws))
+            fl = roofline.flops(a, [n] * count)
+            rl[a] = {"team": team, "ms": ms, "solves_per_s": count / (ms * 1e-3),
+                     "tflops": fl / (ms * 1e-3) / 1e12,
+                     "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+        res[f"{count}x{n}_links_fp64"] = rl
+        del cs, b, q, qd, tau
+        torch.cuda.empty_cache()
+
+    # uneven batch: 100 000 chains, n log-uniform in [6, 512], mixed precision
+    lengths = synth.log_uniform_lengths(100000, 6, 512, seed=0)
+    m = synth.random_chains(lengths, seed=1)
+    st = synth.random_states(m.n_links_total, seed=2)
+    cs = fd.ChainSet(m, device=dev.index or 0)
+    b = fd.Batch(cs)
+    t32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    q, qd, tau = t32(st.q), t32(st.qdot), t32(st.tau)
+    ru = {"chains": 100000, "links": int(m.n_links_total), "prec": "mixed"}
+    for a in ("abia", "cfa"):
+        team = fd.autotune(b, q, qd, tau, algo=a, prec="mixed")
+        ws = fd.workspace(b, a, "mixed", 0, dev)
+        out = torch.empty_like(q)
+        one_ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, prec="mixed", out=out, ws=ws))
+        del ws
+        # one launch per distinct chain length (static batching per size)
+        groups = []
+        off = m.offsets
+        for ln in np.unique(lengths):
+            idx = np.nonzero(lengths == ln)[0].astype(np.int32)
+            links = np.concatenate([np.arange(off[i], off[i + 1]) for i in idx])
+            li = torch.tensor(links, device=dev)
+            bb = fd.Batch(cs, idx)
+            groups.append((bb, q[li].contiguous(), qd[li].contiguous(), tau[li].contiguous(),
+                           torch.empty(len(links), dtype=torch.float32, device=dev),
+                           fd.workspace(bb, a, "mixed", 0, dev)))
+
+        def per_size():
+            for bb, gq, gqd, gtau, go, gw in groups:
+                fd.solve(bb, gq, gqd, gtau, algo=a, prec="mixed", out=go, ws=gw)
+
+        ps_ms = _time_ms(per_size)
+        ru[a] = {"team": team, "one_launch_ms": one_ms, "per_size_launches_ms": ps_ms,
+                 "per_size_launches": len(groups),
+                 "solves_per_s_one_launch": 100000 / (one_ms * 1e-3),
+                 "solves_per_s_per_size": 100000 / (ps_ms * 1e-3)}
+        del groups
+        torch.cuda.empty_cache()
+    w = torch.randn(m.n_links_total, dtype=torch.float32, device=dev)
+    adj_ms = _time_ms(lambda: fd.adjoint(b, q, qd, tau, w, algo="cfa", prec="mixed",
+                                         masses=False))
+    ru["adjoint_cfa_ms"] = adj_ms
+    ru["adjoint_solves_per_s"] = 100000 / (adj_ms * 1e-3)
+    res["100000_uneven_6_512_mixed"] = ru
+    return res
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -321,10 +440,7 @@ def main():
     total_ms = t_begin.elapsed_time(t_end)
     per_algo_ms = {a: float(np.mean([evs[s][k].elapsed_time(evs[s][k + 1])
                                      for s in range(args.steps)])) for k, a in enumerate(ALGOS)}
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = fdist.max_over_ranks(total_ms, dev)
     solves = 3 * args.chains * world * args.steps
     value = solves / (total_ms / 1e3)
 
@@ -400,19 +516,20 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        if world > 1:
-            tt = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = fdist.max_over_ranks(ms, dev)
         nb = q.numel() * 8
         e2e = {"value": 3 * args.chains * world * ksteps / (ms / 1e3), "unit": "FD solves/s",
                "h2d_bytes_per_step": 3 * nb, "d2h_bytes_per_step": 3 * nb,
                "steps": ksteps}
 
+    del ws, out
+    torch.cuda.empty_cache()
+    extra = None
+    if rank == 0 and not args.no_extra:
+        extra = extra_configs(dev)
+        torch.cuda.empty_cache()
     serving = None
     if rank == 0 and not args.no_serve:
-        del ws, out
-        torch.cuda.empty_cache()
         serving = {"continuous": serve_bench(args.serve_seconds, args.serve_rate, False,
                                              device=local),
                    "per_size_baseline": serve_bench(args.serve_seconds, args.serve_rate, True,
@@ -434,6 +551,7 @@ def main():
                            "parallelism": f"replicas x{world}, chains partitioned, no exchange"},
                 "per_algo": rl, "variants_fp32": variants,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
+                "configs": extra,
                 "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:

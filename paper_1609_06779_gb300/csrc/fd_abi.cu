@@ -4,12 +4,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/fd_gb300.h"
@@ -245,14 +247,45 @@ fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const d
     if (!std::isfinite(gravity[k])) return fail(FD_ERR_INVALID_ARG, "fd_create_chain: gravity");
 
   // Canonical link frames (joint axis = x axis of the child frame), model records.
+  // Chains are independent: pack them on several host threads.
   bool rigid = true;
   std::vector<double> rec64(static_cast<size_t>(std::max<int64_t>(L, 1)) * fdk::REC, 0.0);
-  for (int32_t k = 0; k < n_chains; ++k) {
-    const fd_status st = fdk_pack_chain(link_offsets[k], link_offsets[k + 1] - link_offsets[k],
-                                        joint_axes, link_frames, spatial_inertias,
-                                        rec64.data() + static_cast<size_t>(link_offsets[k]) * fdk::REC,
-                                        &rigid);
-    if (st != FD_OK) return st;
+  {
+    const int hw = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+    const int nt = static_cast<int>(std::min<int64_t>(std::min(hw, 32), std::max<int64_t>(L / 65536, 1)));
+    std::vector<fd_status> sts(nt, FD_OK);
+    std::vector<std::string> msgs(nt);
+    std::vector<char> rig(nt, 1);
+    std::atomic<int32_t> next{0};
+    auto work = [&](int t) {
+      bool rg = true;
+      for (;;) {
+        const int32_t k0 = next.fetch_add(256);
+        if (k0 >= n_chains || sts[t] != FD_OK) break;
+        for (int32_t k = k0; k < std::min(n_chains, k0 + 256); ++k) {
+          const fd_status st = fdk_pack_chain(
+              link_offsets[k], link_offsets[k + 1] - link_offsets[k], joint_axes, link_frames,
+              spatial_inertias, rec64.data() + static_cast<size_t>(link_offsets[k]) * fdk::REC, &rg);
+          if (st != FD_OK) {
+            sts[t] = st;
+            msgs[t] = g_err;
+            break;
+          }
+        }
+      }
+      rig[t] = rg;
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto &th : pool) th.join();
+    for (int t = 0; t < nt; ++t) {
+      if (sts[t] != FD_OK) {
+        g_err = msgs[t];
+        return sts[t];
+      }
+      rigid = rigid && rig[t];
+    }
   }
   std::vector<float> rec32(rec64.size());
   for (size_t k = 0; k < rec64.size(); ++k) rec32[k] = static_cast<float>(rec64[k]);

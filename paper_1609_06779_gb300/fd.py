@@ -320,16 +320,17 @@ def forward_dynamics(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", team=0):
     return _FD_FN.apply(q, qd, tau, batch, algo, prec, team)
 
 
-def autotune(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", max_workspace_bytes=8 << 30,
+def autotune(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", max_workspace_bytes=32 << 30,
              stream=None) -> int:
     """Time the team sizes (fd_autotune) and record the fastest in the batch plan;
-    returns it. Uses a workspace of at most ``max_workspace_bytes``."""
+    returns it. Team sizes whose workspace exceeds ``max_workspace_bytes`` are
+    skipped, except the smallest."""
     torch = _torch()
     dt = _state_dtype(prec)
     for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau")):
         _check_state(t, batch, dt, nm)
-    need = 0
-    t = 1
+    need = batch.workspace_size(algo, prec, 1)
+    t = 2
     while t <= 256:
         n = batch.workspace_size(algo, prec, t)
         if n <= max_workspace_bytes:
