@@ -403,16 +403,21 @@ def main():
     out = {a: torch.empty_like(q) for a in ALGOS}
     teams = {}
     for a in ALGOS:  # schedule per algorithm, chosen by timing (untimed here)
-        teams[a] = args.team if args.team else fd.autotune(batch, q, qd, tau, algo=a, prec="fp64")
+        if a == "abia":
+            teams[a] = 1            # the articulated-inertia recursion is serial per chain
+        elif args.team:
+            teams[a] = args.team
+        else:
+            teams[a] = fd.autotune(batch, q, qd, tau, algo=a, prec="fp64")
     torch.cuda.empty_cache()
-    ws = {a: fd.workspace(batch, a, "fp64", args.team, dev) for a in ALGOS}
+    ws = {a: fd.workspace(batch, a, "fp64", teams[a], dev) for a in ALGOS}
     stream = torch.cuda.current_stream(dev)
 
     def step(evs=None):
         for k, a in enumerate(ALGOS):
             if evs is not None:
                 evs[k].record(stream)
-            fd.solve(batch, q, qd, tau, algo=a, prec="fp64", team=args.team, out=out[a],
+            fd.solve(batch, q, qd, tau, algo=a, prec="fp64", team=teams[a], out=out[a],
                      ws=ws[a], stream=stream)
         if evs is not None:
             evs[3].record(stream)
@@ -455,11 +460,12 @@ def main():
     dom = max(ALGOS, key=lambda a: per_algo_ms[a])
     tr = traffic_record(f"{dom}_kernel")
     traffic = None
-    if tr is not None:
+    if tr is not None and tr.get("team") == teams[dom]:
+        # DRAM bytes of one launch: the capture's bytes per link x this launch's links
         traffic = tr["bytes_per_link"] * args.chains * args.links
     roof = {"bound": "alu", "achieved": rl[dom]["tflops"], "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": rl[dom]["frac"], "traffic": traffic,
-            "kernel": f"{dom}_kernel<double,double,team>",
+            "kernel": f"{dom}_kernel<double,double,{teams[dom]}>",
             "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s), not measured",
             "algorithmic_flops_per_launch": roofline.flops(dom, lengths),
             "algorithmic_bytes_per_launch": roofline.bytes_per_link("fp64") * args.chains * args.links}
@@ -470,17 +476,18 @@ def main():
         q32, qd32, tau32 = (x.float() for x in (q, qd, tau))
         for prec in ("fp32", "mixed"):
             for a in ALGOS:
-                if not args.team:
+                tv = 1 if a == "abia" else args.team
+                if not tv:
                     fd.autotune(batch, q32, qd32, tau32, algo=a, prec=prec)
-                w = fd.workspace(batch, a, prec, args.team, dev)
+                w = fd.workspace(batch, a, prec, tv, dev)
                 o = torch.empty_like(q32)
                 for _ in range(2):
-                    fd.solve(batch, q32, qd32, tau32, algo=a, prec=prec, team=args.team,
+                    fd.solve(batch, q32, qd32, tau32, algo=a, prec=prec, team=tv,
                              out=o, ws=w)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 for _ in range(3):
-                    fd.solve(batch, q32, qd32, tau32, algo=a, prec=prec, team=args.team,
+                    fd.solve(batch, q32, qd32, tau32, algo=a, prec=prec, team=tv,
                              out=o, ws=w)
                 e1.record(stream)
                 torch.cuda.synchronize()
@@ -500,7 +507,7 @@ def main():
             dqd.copy_(hqd, non_blocking=True)
             dtau.copy_(htau, non_blocking=True)
             for a in ALGOS:
-                fd.solve(batch, dq, dqd, dtau, algo=a, prec="fp64", team=args.team, out=out[a],
+                fd.solve(batch, dq, dqd, dtau, algo=a, prec="fp64", team=teams[a], out=out[a],
                          ws=ws[a], stream=stream)
                 hout[a].copy_(out[a], non_blocking=True)
 

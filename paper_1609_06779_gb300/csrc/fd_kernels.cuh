@@ -224,8 +224,46 @@ __device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, TA *U
   }
 }
 
+// Per row and level, once: the Cholesky factor L of D, G = L^{-1} U and
+// g = L^{-1} R. Both neighbours of the row reuse them (SolvSys of Algorithm 2
+// with D = L L^T): E U_{i+d} = Z G_{i+d}, E R_{i+d} = Z g_{i+d} with
+// Z = U_i L_{i+d}^{-T}, and K U_{i-d} = G^T G, K R_{i-d} = G^T g of row i-d.
+template <class TA>
+__device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD, int srcU,
+                                           int srcR) {
+  TA *row = wa + static_cast<int64_t>(m) * NA_CFA;
+  TA Dm[15], L[15], inv[5];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) Dm[k] = row[srcD + k];
+  const bool ok = chol5(Dm, L, inv);
+#pragma unroll
+  for (int k = 0; k < 15; ++k) row[A_L + k] = L[k];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) row[A_LI + k] = inv[k];
+  TA r[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) r[k] = row[srcR + k];
+  fwd5(L, inv, r);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) row[A_GR + k] = r[k];
+  if (m + d < n) {  // U_m couples row m to m + d; zero beyond
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      TA col[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) col[k] = row[srcU + 5 * k + c];
+      fwd5(L, inv, col);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) row[A_G + 5 * k + c] = col[k];
+    }
+  }
+  return ok;
+}
+
 // One OEE update of row i at distance d (Section IV, update rule and Algorithm 2,
-// right-hand sides all at level j-1).
+// right-hand sides all at level j-1):
+//   D_i -= E_i U_i^T + K_i U_{i-d},  R_i -= E_i R_{i+d} + K_i R_{i-d},
+//   U_i = -E_i U_{i+d},  E_i = U_i D_{i+d}^{-1},  K_i = U_{i-d}^T D_{i-d}^{-1}.
 template <class TA>
 __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int srcD, int srcU,
                                         int srcR, TA *Dn, TA *Un, TA *Rn) {
@@ -260,13 +298,11 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
         Dn[l5(r, c)] -= s;  // E_i U_i^T = Z Z^T
       }
 #pragma unroll
-    for (int k = 0; k < 5; ++k) bwd5(L, inv, Z[k]);  // now Z = E_i = U_i D_{i+d}^{-1}
-#pragma unroll
     for (int r = 0; r < 5; ++r) {
       TA s = TA(0);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) s += Z[r][k] * nb[srcR + k];
-      Rn[r] -= s;  // E_i R_{i+d}
+      for (int k = 0; k < 5; ++k) s += Z[r][k] * nb[A_GR + k];
+      Rn[r] -= s;  // E_i R_{i+d} = Z g_{i+d}
     }
     if (i + 2 * d < n) {
 #pragma unroll
@@ -275,50 +311,39 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
         for (int c = 0; c < 5; ++c) {
           TA s = TA(0);
 #pragma unroll
-          for (int k = 0; k < 5; ++k) s += Z[r][k] * nb[srcU + 5 * k + c];
-          Un[5 * r + c] = -s;  // U_i <- -E_i U_{i+d}
+          for (int k = 0; k < 5; ++k) s += Z[r][k] * nb[A_G + 5 * k + c];
+          Un[5 * r + c] = -s;  // U_i <- -E_i U_{i+d} = -Z G_{i+d}
         }
     }
   }
   if (i - d >= 0) {
     const TA *pr = wa + static_cast<int64_t>(i - d) * NA_CFA;
-    TA L[15], inv[5];
+    TA G[5][5];
 #pragma unroll
-    for (int k = 0; k < 15; ++k) L[k] = pr[A_L + k];
+    for (int k = 0; k < 5; ++k)
 #pragma unroll
-    for (int k = 0; k < 5; ++k) inv[k] = pr[A_LI + k];
-    TA Zt[5][5];  // Zt[l] = column l of L^{-1} U_{i-d}
-#pragma unroll
-    for (int l = 0; l < 5; ++l) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) Zt[l][k] = pr[srcU + 5 * k + l];
-      fwd5(L, inv, Zt[l]);
-    }
+      for (int c = 0; c < 5; ++c) G[k][c] = pr[A_G + 5 * k + c];
 #pragma unroll
     for (int r = 0; r < 5; ++r)
 #pragma unroll
       for (int c = 0; c <= r; ++c) {
         TA s = TA(0);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) s += Zt[r][k] * Zt[c][k];
-        Dn[l5(r, c)] -= s;  // K_i U_{i-d} = (L^{-1}U)^T (L^{-1}U)
+        for (int k = 0; k < 5; ++k) s += G[k][r] * G[k][c];
+        Dn[l5(r, c)] -= s;  // K_i U_{i-d} = G^T G
       }
-    TA w[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) w[k] = pr[srcR + k];
-    fwd5(L, inv, w);
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
       TA s = TA(0);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) s += Zt[r][k] * w[k];
-      Rn[r] -= s;  // K_i R_{i-d}
+      for (int k = 0; k < 5; ++k) s += G[k][r] * pr[A_GR + k];
+      Rn[r] -= s;  // K_i R_{i-d} = G^T g
     }
   }
 }
 
 template <class T, class TA, int P>
-__global__ void __launch_bounds__(block_for<P>()) cfa_kernel(KArgs A) {
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(KArgs A) {
   Team<P> tm;
   Prob<T> pb;
   if (!load_problem<T, P>(A, tm, pb, NT)) return;
@@ -382,12 +407,7 @@ __global__ void __launch_bounds__(block_for<P>()) cfa_kernel(KArgs A) {
     const int d = 1 << (j - 1);
     const int sD = src ? A_D1 : A_D0, sU = src ? A_U1 : A_U0, sR = src ? A_R1 : A_R0;
     const int tD = src ? A_D0 : A_D1, tU = src ? A_U0 : A_U1, tR = src ? A_R0 : A_R1;
-    for (int m = a; m < b; ++m) {
-      TA *row = wa + static_cast<int64_t>(m) * NA_CFA;
-      TA Dm[15];
-      for (int k = 0; k < 15; ++k) Dm[k] = row[sD + k];
-      bad |= !chol5(Dm, row + A_L, row + A_LI);
-    }
+    for (int m = a; m < b; ++m) bad |= !oee_factor<TA>(m, d, n, wa, sD, sU, sR);
     tm.sync();
     for (int i = a; i < b; ++i) {
       TA Dn[15], Un[25], Rn[5];

@@ -43,24 +43,27 @@ def jsiia_flops(n: int) -> int:
 
 
 def oee_flops(n: int) -> int:
-    """Odd-even elimination (Algorithm 2): ceil(log2 n) levels of per-row
-    Cholesky, the E part (Z, Z Z^T, E, E R: 470, plus E U: 250 while row i+2d
-    exists) and the K part (370), then the final block solves (110 per row)."""
+    """Odd-even elimination (Algorithm 2): ceil(log2 n) levels; per row and
+    level the Cholesky factor of D (60) and g = L^{-1} R (25), and while the row
+    has an upper neighbour G = L^{-1} U (125); the E part (Z = U L^{-T} 125,
+    Z Z^T 165, Z g 50) and, while row i + 2d exists, Z G (250); the K part
+    (G^T G 165, G^T g 55); then the final block solves (110 per row)."""
     levels = math.ceil(math.log2(n)) if n > 1 else 0
     f = 0
     for j in range(1, levels + 1):
         d = 1 << (j - 1)
-        f += n * CHOL5
-        e_rows = max(n - d, 0)
-        f += e_rows * (5 * TRI5 + 165 + 5 * TRI5 + 55)
+        pairs = max(n - d, 0)            # rows with an upper neighbour (= with a lower one)
+        f += n * (CHOL5 + TRI5) + pairs * 5 * TRI5
+        f += pairs * (5 * TRI5 + 165 + 50)
         f += max(n - 2 * d, 0) * 250
-        f += e_rows * (5 * TRI5 + 165 + TRI5 + 55)
+        f += pairs * (165 + 55)
     return f + n * (CHOL5 + 2 * TRI5)
 
 
 def cfa_flops(n: int) -> int:
-    """ID + A blocks (D 477, U 540) + R = -B tau (120) + OEE + CalcAcc (120)."""
-    return id_flops(n) + n * (477 + 540 + 120) + oee_flops(n) + n * 120
+    """ID + A blocks (D 477; U 357: five columns of J^{-1} Ad^T restricted to
+    unit vectors, 27 + 5 x 66) + R = -B tau (120) + OEE + CalcAcc (120)."""
+    return id_flops(n) + n * (477 + 357 + 120) + oee_flops(n) + n * 120
 
 
 FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops}
