@@ -71,13 +71,16 @@ __device__ __forceinline__ void cross3(const T *a, const T *b, T *c) {
 }
 
 // y = Ad_{g^{-1}} x: omega' = R^T omega, v' = R^T (v + omega x p)
+// (the cross product accumulates onto v in fused multiply-adds)
 template <class T>
 __device__ __forceinline__ void adinv(const SE3<T> &g, const T *x, T *y) {
-  T wp[3], u[3];
-  cross3(x, g.p, wp);
-  u[0] = x[3] + wp[0];
-  u[1] = x[4] + wp[1];
-  u[2] = x[5] + wp[2];
+  T u[3];
+  u[0] = x[3] + x[1] * g.p[2];
+  u[0] -= x[2] * g.p[1];
+  u[1] = x[4] + x[2] * g.p[0];
+  u[1] -= x[0] * g.p[2];
+  u[2] = x[5] + x[0] * g.p[1];
+  u[2] -= x[1] * g.p[0];
   T o[6];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -97,10 +100,13 @@ __device__ __forceinline__ void adinvT(const SE3<T> &g, const T *x, T *y) {
     Rn[i] = g.R[3 * i] * x[0] + g.R[3 * i + 1] * x[1] + g.R[3 * i + 2] * x[2];
     Rf[i] = g.R[3 * i] * x[3] + g.R[3 * i + 1] * x[4] + g.R[3 * i + 2] * x[5];
   }
-  cross3(g.p, Rf, pf);
-  y[0] = Rn[0] + pf[0];
-  y[1] = Rn[1] + pf[1];
-  y[2] = Rn[2] + pf[2];
+  // n' = R n + p x (R f), accumulated in fused multiply-adds
+  pf[0] = Rn[0] + g.p[1] * Rf[2];
+  pf[1] = Rn[1] + g.p[2] * Rf[0];
+  pf[2] = Rn[2] + g.p[0] * Rf[1];
+  y[0] = pf[0] - g.p[2] * Rf[1];
+  y[1] = pf[1] - g.p[0] * Rf[2];
+  y[2] = pf[2] - g.p[1] * Rf[0];
   y[3] = Rf[0];
   y[4] = Rf[1];
   y[5] = Rf[2];
@@ -135,6 +141,21 @@ __device__ __forceinline__ void sym6_apply(const TK *K, const T *x, T *y) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     T s = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += T(K[s6(i, j)]) * x[j];
+    o[i] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y[i] = o[i];
+}
+
+// y += K x, K packed symmetric 6x6 (accumulates in fused multiply-adds)
+template <class T, class TK>
+__device__ __forceinline__ void sym6_apply_add(const TK *K, const T *x, T *y) {
+  T o[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    T s = y[i];
 #pragma unroll
     for (int j = 0; j < 6; ++j) s += T(K[s6(i, j)]) * x[j];
     o[i] = s;

@@ -126,12 +126,12 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
     accel_step(i, x);
     T *w = pb.wt + static_cast<int64_t>(i) * NT;
     const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
-    T V[6], JV[6], JA[6], c[6];
+    T V[6], JV[6], JA[6];
     ldv<T, 6>(w + W_V, V);
-    sym6_apply(rec + REC_J, x, JA);
     sym6_apply(rec + REC_J, V, JV);
-    adT_apply(V, JV, c);
-    for (int k = 0; k < 6; ++k) JA[k] -= c[k];
+    adT_apply(V, JV, JA);
+    for (int k = 0; k < 6; ++k) JA[k] = -JA[k];
+    sym6_apply_add(rec + REC_J, x, JA);  // J Vd - ad_V^T J V
     stv<T, 6>(w + W_F, JA);
   }
 
@@ -291,19 +291,16 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
 #pragma unroll
     for (int r = 0; r < 5; ++r)
 #pragma unroll
-      for (int c = 0; c <= r; ++c) {
-        TA s = TA(0);
+      for (int c = 0; c <= r; ++c)
 #pragma unroll
-        for (int k = 0; k < 5; ++k) s += Z[r][k] * Z[c][k];
-        Dn[l5(r, c)] -= s;  // E_i U_i^T = Z Z^T
-      }
+        for (int k = 0; k < 5; ++k) Dn[l5(r, c)] -= Z[r][k] * Z[c][k];  // E_i U_i^T = Z Z^T
+    TA gr[5];
 #pragma unroll
-    for (int r = 0; r < 5; ++r) {
-      TA s = TA(0);
+    for (int k = 0; k < 5; ++k) gr[k] = nb[A_GR + k];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) s += Z[r][k] * nb[A_GR + k];
-      Rn[r] -= s;  // E_i R_{i+d} = Z g_{i+d}
-    }
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Rn[r] -= Z[r][k] * gr[k];  // E_i R_{i+d} = Z g_{i+d}
     if (i + 2 * d < n) {
 #pragma unroll
       for (int r = 0; r < 5; ++r)
@@ -326,19 +323,16 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
 #pragma unroll
     for (int r = 0; r < 5; ++r)
 #pragma unroll
-      for (int c = 0; c <= r; ++c) {
-        TA s = TA(0);
+      for (int c = 0; c <= r; ++c)
 #pragma unroll
-        for (int k = 0; k < 5; ++k) s += G[k][r] * G[k][c];
-        Dn[l5(r, c)] -= s;  // K_i U_{i-d} = G^T G
-      }
+        for (int k = 0; k < 5; ++k) Dn[l5(r, c)] -= G[k][r] * G[k][c];  // K_i U_{i-d} = G^T G
+    TA gr[5];
 #pragma unroll
-    for (int r = 0; r < 5; ++r) {
-      TA s = TA(0);
+    for (int k = 0; k < 5; ++k) gr[k] = pr[A_GR + k];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) s += G[k][r] * pr[A_GR + k];
-      Rn[r] -= s;  // K_i R_{i-d} = G^T g
-    }
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Rn[r] -= G[k][r] * gr[k];  // K_i R_{i-d} = G^T g
   }
 }
 
@@ -474,7 +468,7 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(K
 // ------------------------------------------------------------------ JSIIA
 
 template <class T, class TA, int P>
-__global__ void __launch_bounds__(block_for<P>()) jsiia_kernel(KArgs A) {
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel(KArgs A) {
   Team<P> tm;
   Prob<T> pb;
   if (!load_problem<T, P>(A, tm, pb, NT)) return;
@@ -491,8 +485,12 @@ __global__ void __launch_bounds__(block_for<P>()) jsiia_kernel(KArgs A) {
   tm.sync();
 
   // columns of M: ID with qdd = e_k, qdot = 0, no gravity (Section II-C); the
-  // lower triangle i >= k of column k needs links k..n-1 only.
-  for (int k = tm.r; k < n; k += P) {
+  // lower triangle i >= k of column k needs links k..n-1 only, so column k costs
+  // about n - k: lanes take columns in snake order (round t: t P + r, then
+  // t P + P - 1 - r) to balance that work.
+  for (int t = 0; t * P < n; ++t) {
+    const int k = t * P + ((t & 1) ? (P - 1 - tm.r) : tm.r);
+    if (k >= n) continue;
     TA x[6] = {TA(1), TA(0), TA(0), TA(0), TA(0), TA(0)};
     for (int c = 0; c < 6; ++c) myacc[static_cast<int64_t>(k) * 6 + c] = x[c];
     for (int i = k + 1; i < n; ++i) {
@@ -506,10 +504,9 @@ __global__ void __launch_bounds__(block_for<P>()) jsiia_kernel(KArgs A) {
     }
     TA y[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
     for (int i = n - 1; i >= k; --i) {
-      TA f[6], va[6];
+      TA va[6];
       for (int c = 0; c < 6; ++c) va[c] = myacc[static_cast<int64_t>(i) * 6 + c];
-      sym6_apply(pb.rec + static_cast<int64_t>(i) * REC + REC_J, va, f);
-      for (int c = 0; c < 6; ++c) y[c] += f[c];
+      sym6_apply_add(pb.rec + static_cast<int64_t>(i) * REC + REC_J, va, y);
       M[static_cast<int64_t>(i) * n + k] = y[0];
       SE3<T> g;
       ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
@@ -620,10 +617,11 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     ra[A_UU] = u;
     if (i == 0) break;
     // Pa = P - h h^T / D, pa = p + h u / D
-    TA Pa[21], pa[6];
+    TA Pa[21], pa[6], hs[6];
+    for (int k = 0; k < 6; ++k) hs[k] = h[k] * Dinv;
     for (int r = 0; r < 6; ++r)
-      for (int c = r; c < 6; ++c) Pa[s6(r, c)] = Pm[s6(r, c)] - h[r] * h[c] * Dinv;
-    for (int k = 0; k < 6; ++k) pa[k] = pbias[k] + h[k] * u * Dinv;
+      for (int c = r; c < 6; ++c) Pa[s6(r, c)] = Pm[s6(r, c)] - h[r] * hs[c];
+    for (int k = 0; k < 6; ++k) pa[k] = pbias[k] + hs[k] * u;
     SE3<T> g;
     ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
     SE3<TA> ga;
