@@ -1,23 +1,19 @@
-// JSIIA kernels: instantiations and launcher.
-#include "fd_kernels.cuh"
+// JSIIA kernels: launcher dispatching to the per-precision translation units.
 #include "fd_launch.h"
 
 namespace fdk {
 
-template <class T, class TA>
-static cudaError_t go(const KArgs &a, int team, cudaStream_t s) {
-  const unsigned g = grid_for(a.n_problems, team);
-  switch (team) {
-    FDK_TEAM_CASES(jsiia_kernel, T, TA)
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
+cudaError_t launch_jsiia_f64(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_jsiia_f32(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_jsiia_mixed(const KArgs &a, int team, cudaStream_t s);
 
 cudaError_t launch_jsiia(const KArgs &a, int prec, int team, cudaStream_t s) {
-  if (prec == 0) return go<double, double>(a, team, s);
-  if (prec == 1) return go<float, float>(a, team, s);
-  return go<float, double>(a, team, s);
+  switch (prec) {
+    case 0: return launch_jsiia_f64(a, team, s);
+    case 1: return launch_jsiia_f32(a, team, s);
+    case 2: return launch_jsiia_mixed(a, team, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace fdk
