@@ -470,8 +470,20 @@ def main():
             "algorithmic_flops_per_launch": roofline.flops(dom, lengths),
             "algorithmic_bytes_per_launch": roofline.bytes_per_link("fp64") * args.chains * args.links}
 
-    # FP32 and mixed variants of each algorithm (context; not part of the step)
+    # CFA with block cyclic reduction in place of OEE (context; not part of the step)
     variants = {}
+    if rank == 0:
+        tcr = args.team or fd.autotune(batch, q, qd, tau, algo="cfa_cr", prec="fp64")
+        wcr = fd.workspace(batch, "cfa_cr", "fp64", tcr, dev)
+        ocr = torch.empty_like(q)
+        ms = _time_ms(lambda: fd.solve(batch, q, qd, tau, algo="cfa_cr", team=tcr, out=ocr,
+                                       ws=wcr), reps=5, warm=2)
+        fl = roofline.flops("cfa_cr", lengths)
+        variants["cfa_cr_fp64"] = {"team": tcr, "ms": ms, "solves_per_s": args.chains / (ms * 1e-3),
+                                   "tflops": fl / (ms * 1e-3) / 1e12,
+                                   "frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+        del wcr, ocr
+    # FP32 and mixed variants of each algorithm (context; not part of the step)
     if rank == 0:
         q32, qd32, tau32 = (x.float() for x in (q, qd, tau))
         for prec in ("fp32", "mixed"):
@@ -556,7 +568,7 @@ def main():
                            "team": teams,
                            "l2": "inputs larger than L2 (FP64 model arena 940 MB), no flush",
                            "parallelism": f"replicas x{world}, chains partitioned, no exchange"},
-                "per_algo": rl, "variants_fp32": variants,
+                "per_algo": rl, "variants": variants,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
                 "configs": extra,
                 "gpu_launches": 3 * args.steps, "clocks": clk.summary()}

@@ -44,7 +44,11 @@ typedef struct fd_batch_s *fd_batch_t; /* a batch plan: which chain each problem
 typedef enum fd_algo {
   FD_ABIA = 0,  /* articulated-body inertia factorisation (Section II-C) */
   FD_JSIIA = 1, /* joint-space inertia by ID columns + Cholesky (Section II-C) */
-  FD_CFA = 2    /* constraint force algorithm with OEE (Section III, Alg. 1-2) */
+  FD_CFA = 2,   /* constraint force algorithm with OEE (Section III, Alg. 1-2) */
+  FD_CFA_CR = 3 /* CFA with the block tri-diagonal system solved by block cyclic
+                   reduction instead of OEE: about n row updates instead of
+                   n ceil(log2 n), the same result (not in the paper's
+                   experiments; the reduction OEE is a variant of, Section IV) */
 } fd_algo;
 
 typedef enum fd_prec {

@@ -446,7 +446,7 @@ namespace {
 int resolve_team(const fd_batch_s *b, int32_t algo, fd_prec prec, int32_t team) {
   if (algo == FD_ABIA) return 1;
   if (team > 0) return team;
-  const int tuned = (algo >= 0 && algo < 3 && prec >= 0 && prec < 3) ? b->tuned[algo][prec] : 0;
+  const int tuned = (algo >= 0 && algo < 4 && prec >= 0 && prec < 3) ? b->tuned[algo][prec] : 0;
   if (tuned > 0) return tuned;
   // about four resident warps' worth of lanes per FP64 unit of the GPU
   // (152 SMs x 2048 threads), but no more lanes than links and at most 256
@@ -469,7 +469,7 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int team) {
   const size_t as = prec == FD_FP32 ? 4 : 8;
   const size_t L = static_cast<size_t>(b->n_state_links);
   WsPlan w{align256(L * fdk::NT * ts), 0};
-  if (algo == FD_CFA) w.a_bytes = L * fdk::NA_CFA * as;
+  if (algo == FD_CFA || algo == FD_CFA_CR) w.a_bytes = L * fdk::NA_CFA * as;
   if (algo == FD_JSIIA)
     w.a_bytes = (L * (fdk::NA_JSIIA + fdk::NP_JSIIA * team) +
                  static_cast<size_t>(b->sum_sq) * fdk::NSQ_JSIIA) * as;
@@ -500,7 +500,7 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
-  if (algo != -1 && algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA)
+  if (algo != -1 && algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, algo);
   if (team < 0 || (team > 0 && !valid_team(team)))
     return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 256", who, team);
@@ -540,6 +540,7 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   auto s = static_cast<cudaStream_t>(stream);
   if (algo == -1) e = fdk::launch_id(a, prec_k, t, s);
   else if (algo == FD_CFA) e = fdk::launch_cfa(a, prec_k, t, s);
+  else if (algo == FD_CFA_CR) e = fdk::launch_cfa_cr(a, prec_k, t, s);
   else if (algo == FD_JSIIA) e = fdk::launch_jsiia(a, prec_k, t, s);
   else e = fdk::launch_abia(a, prec_k, s);
   cudaSetDevice(prev);
@@ -581,7 +582,7 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
                            int32_t *status, void *stream) {
   const char *who = "fd_solve_adjoint";
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
-  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA)
+  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, static_cast<int>(algo));
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
@@ -633,6 +634,7 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
   auto s = static_cast<cudaStream_t>(stream);
   auto run_fd = [&](fdk::KArgs &k) {
     if (algo == FD_CFA) return fdk::launch_cfa(k, prec_k, t, s);
+    if (algo == FD_CFA_CR) return fdk::launch_cfa_cr(k, prec_k, t, s);
     if (algo == FD_JSIIA) return fdk::launch_jsiia(k, prec_k, t, s);
     return fdk::launch_abia(k, prec_k, s);
   };
@@ -680,7 +682,7 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
                                  int32_t *best_team) {
   const char *who = "fd_autotune";
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
-  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA)
+  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision", who);

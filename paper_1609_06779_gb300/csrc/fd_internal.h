@@ -31,7 +31,7 @@ struct fd_batch_s {
   int64_t *d_state_off = nullptr;
   int64_t *d_sq_off = nullptr;
   int32_t *d_order = nullptr;
-  int tuned[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // autotuned team per [algo][prec]
+  int tuned[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // autotuned team per [algo][prec]
 };
 
 // Sets the calling thread's fd_last_error message and returns st.

@@ -336,8 +336,104 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
   }
 }
 
-template <class T, class TA, int P>
-__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(KArgs A) {
+// Block cyclic reduction of the symmetric block tri-diagonal system (the
+// work-efficient alternative to OEE): at level j (distance d = 2^{j-1}) the
+// active rows are i with (i + 1) % d == 0; those with (i + 1) / d odd are
+// eliminated: they factor themselves (L, G = L^{-1} U, g = L^{-1} R, as in OEE)
+// and keep their lower coupling; the others are updated in place with the OEE
+// row formulas. About n row updates in total instead of n ceil(log2 n). Back
+// substitution then solves the rows level by level from the last one down:
+// x_i = D_i^{-1} (R_i - U_{i-d}^T x_{i-d} - U_i x_{i+d}).
+template <class TA, int P>
+__device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, int a, int b) {
+  bool bad = false;
+  int levels = 0;
+  while ((1 << levels) < n) ++levels;
+  for (int j = 1; j <= levels; ++j) {
+    const int d = 1 << (j - 1);
+    for (int m = a; m < b; ++m) {  // eliminated rows: factors and saved coupling
+      if ((m + 1) % d != 0 || (((m + 1) / d) & 1) == 0) continue;
+      bad |= !oee_factor<TA>(m, d, n, wa, A_D0, A_U0, A_R0);
+      if (m - d >= 0) {
+        const TA *lo = wa + static_cast<int64_t>(m - d) * NA_CFA + A_U0;
+        TA *row = wa + static_cast<int64_t>(m) * NA_CFA;
+#pragma unroll
+        for (int k = 0; k < 25; ++k) row[A_LO + k] = lo[k];
+      }
+    }
+    tm.sync();
+    for (int i = a; i < b; ++i) {  // kept rows: update in place
+      if ((i + 1) % d != 0 || (((i + 1) / d) & 1) != 0) continue;
+      TA Dn[15], Un[25], Rn[5];
+      oee_row<TA>(i, d, n, wa, A_D0, A_U0, A_R0, Dn, Un, Rn);
+      TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+#pragma unroll
+      for (int k = 0; k < 15; ++k) row[A_D0 + k] = Dn[k];
+#pragma unroll
+      for (int k = 0; k < 25; ++k) row[A_U0 + k] = Un[k];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) row[A_R0 + k] = Rn[k];
+    }
+    tm.sync();
+  }
+  // rows never eliminated (n a power of two: row n - 1) are decoupled by now;
+  // a row is eliminated at level 1 + (trailing zeros of i + 1)
+  for (int i = a; i < b; ++i) {
+    const int je = __ffs(i + 1);
+    if (je <= levels) continue;
+    TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    TA Dm[15], L[15], inv[5], r[5];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) Dm[k] = row[A_D0 + k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r[k] = row[A_R0 + k];
+    bad |= !chol5(Dm, L, inv);
+    fwd5(L, inv, r);
+    bwd5(L, inv, r);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) row[A_FC + k] = r[k];
+  }
+  tm.sync();
+  for (int j = levels; j >= 1; --j) {
+    const int d = 1 << (j - 1);
+    for (int i = a; i < b; ++i) {
+      if ((i + 1) % d != 0 || (((i + 1) / d) & 1) == 0) continue;
+      TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+      TA r[5], L[15], inv[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) r[k] = row[A_R0 + k];
+      if (i + d < n) {  // - U_i x_{i+d}
+        const TA *xn = wa + static_cast<int64_t>(i + d) * NA_CFA + A_FC;
+#pragma unroll
+        for (int rr = 0; rr < 5; ++rr)
+#pragma unroll
+          for (int k = 0; k < 5; ++k) r[rr] -= row[A_U0 + 5 * rr + k] * xn[k];
+      }
+      if (i - d >= 0) {  // - U_{i-d}^T x_{i-d}
+        const TA *xp = wa + static_cast<int64_t>(i - d) * NA_CFA + A_FC;
+#pragma unroll
+        for (int rr = 0; rr < 5; ++rr)
+#pragma unroll
+          for (int k = 0; k < 5; ++k) r[rr] -= row[A_LO + 5 * k + rr] * xp[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 15; ++k) L[k] = row[A_L + k];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) inv[k] = row[A_LI + k];
+      fwd5(L, inv, r);
+      bwd5(L, inv, r);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) row[A_FC + k] = r[k];
+    }
+    tm.sync();
+  }
+  return bad;
+}
+
+// Algorithm 1 for one problem; BTD selects SolvBTDSys: 0 = odd-even
+// elimination (Algorithm 2), 1 = block cyclic reduction.
+template <class T, class TA, int P, int BTD>
+__device__ __forceinline__ void cfa_body(const KArgs &A) {
   Team<P> tm;
   Prob<T> pb;
   if (!load_problem<T, P>(A, tm, pb, NT)) return;
@@ -393,6 +489,10 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(K
   }
   tm.sync();
 
+  if constexpr (BTD == 1) {
+    // SolvBTDSys by block cyclic reduction
+    bad |= cr_solve<TA, P>(tm, wa, n, a, b);
+  } else {
   // SolvBTDSys: odd-even elimination, ceil(log2 n) levels (Algorithm 2)
   int levels = 0;
   while ((1 << levels) < n) ++levels;
@@ -426,6 +526,7 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(K
     for (int k = 0; k < 5; ++k) row[A_FC + k] = r[k];
   }
   tm.sync();
+  }
 
   // CalcAcc: qdd = C tau_delta + B^T F_c = S^T (I-Gamma) J^{-1} (I-Gamma)^T F,
   // F_i = S tau_delta_i + W F_c,i (Eq. force-decomposition-global)
@@ -463,6 +564,16 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(K
   }
   const bool any_bad = tm.any(bad);
   if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
+}
+
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(KArgs A) {
+  cfa_body<T, TA, P, 0>(A);
+}
+
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_cr_kernel(KArgs A) {
+  cfa_body<T, TA, P, 1>(A);
 }
 
 // ------------------------------------------------------------------ JSIIA

@@ -44,7 +44,8 @@ constexpr int A_LI = 105;
 constexpr int A_FC = 110;  // F_c (5)
 constexpr int A_G = 115;   // G = L^{-1} U (row-major 5x5) and g = L^{-1} R of this level
 constexpr int A_GR = 140;
-constexpr int NA_CFA = 146;
+constexpr int A_LO = 145;  // cyclic reduction: the lower coupling U_{i-d} kept for back substitution
+constexpr int NA_CFA = 170;
 
 // JSIIA: per-link TA entries (right-hand side), n*n TA entries (M), and per team
 // lane 6 TA entries per link (the column's accelerations).

@@ -66,7 +66,34 @@ def cfa_flops(n: int) -> int:
     return id_flops(n) + n * (477 + 357 + 120) + oee_flops(n) + n * 120
 
 
-FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops}
+def cr_flops(n: int) -> int:
+    """Block cyclic reduction of the same system: at each level the eliminated
+    rows factor themselves (60 + 25, and G = L^{-1} U 125 when they have an upper
+    neighbour) and the kept rows take the OEE row update (E part 340 + Z G 250,
+    K part 220); back substitution 150 per row; the root row solves directly."""
+    levels = math.ceil(math.log2(n)) if n > 1 else 0
+    f = 0
+    for j in range(1, levels + 1):
+        d = 1 << (j - 1)
+        for i in range(d - 1, n, d):
+            if ((i + 1) // d) % 2 == 1:        # eliminated at this level
+                f += CHOL5 + TRI5 + (5 * TRI5 if i + d < n else 0)
+                f += 150
+            else:                              # kept: updated
+                if i + d < n:
+                    f += 5 * TRI5 + 165 + 50 + (250 if i + 2 * d < n else 0)
+                if i - d >= 0:
+                    f += 165 + 55
+    roots = 1 if n >= 1 and (n & (n - 1)) == 0 else 0
+    return f + roots * (CHOL5 + 2 * TRI5)
+
+
+def cfa_cr_flops(n: int) -> int:
+    return id_flops(n) + n * (477 + 357 + 120) + cr_flops(n) + n * 120
+
+
+FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops,
+         "cfa_cr": cfa_cr_flops}
 
 
 def flops(algo: str, lengths) -> int:
