@@ -254,7 +254,7 @@ def extra_configs(dev):
     b = fd.Batch(cs, ci)
     q, qd, tau = t64(st.q), t64(st.qdot), t64(st.tau)
     r1 = {}
-    for a in ALGOS:
+    for a in ALGOS + ("cfa_cr",):
         team = fd.autotune(b, q, qd, tau, algo=a)
         ws = fd.workspace(b, a, "fp64", 0, dev)
         out = torch.empty_like(q)
@@ -281,7 +281,7 @@ def extra_configs(dev):
         b = fd.Batch(cs)
         q, qd, tau = t64(st.q), t64(st.qdot), t64(st.tau)
         rl = {}
-        for a in ALGOS:
+        for a in ALGOS + ("cfa_cr",):
             if a == "jsiia" and n > 256:
                 continue  # cubic in n: about 0.3 s per solve of this batch
             team = 128 if a == "jsiia" else fd.autotune(b, q, qd, tau, algo=a)

@@ -137,9 +137,12 @@ fd_status fd_batch_info(fd_batch_t batch, int32_t *n_problems, int64_t *n_state_
  * precision, else a size that fills the GPU); otherwise a power of two from 1
  * (one thread per chain: serial recursions) through 32 (one warp per chain:
  * warp-shuffle scans and OEE levels across lanes) to 256 (one block per chain:
- * scans across warps through shared memory). FD_ABIA runs its articulated-
- * inertia recursion serially (the paper notes it cannot be parallelised beyond
- * a constant factor, Section III) and accepts only team 1 (or 0).
+ * scans across warps through shared memory). FD_ABIA keeps its articulated-
+ * inertia recursion serial over the links (the paper notes it cannot be
+ * parallelised beyond a constant factor, Section III) and takes that constant
+ * factor: team 1 runs one thread per problem, teams 8, 16 and 32 spread the
+ * six rows of each step's 6x6 update over six lanes and run inverse dynamics
+ * as a scan; other sizes return FD_ERR_UNSUPPORTED.
  */
 
 /* Bytes of device workspace fd_solve_batch / fd_inverse_dynamics need for

@@ -444,10 +444,12 @@ fd_status fd_batch_info(fd_batch_t b, int32_t *n_problems, int64_t *n_state_link
 namespace {
 
 int resolve_team(const fd_batch_s *b, int32_t algo, fd_prec prec, int32_t team) {
-  if (algo == FD_ABIA) return 1;
   if (team > 0) return team;
   const int tuned = (algo >= 0 && algo < 4 && prec >= 0 && prec < 3) ? b->tuned[algo][prec] : 0;
   if (tuned > 0) return tuned;
+  // ABIA: one thread per problem once a warp per FP64 unit (152 SMs x 4) is
+  // busy with 32 problems each; below that, spread each step over a team of 8
+  if (algo == FD_ABIA) return b->n_problems > 152 * 4 * 8 ? 1 : 8;
   // about four resident warps' worth of lanes per FP64 unit of the GPU
   // (152 SMs x 2048 threads), but no more lanes than links and at most 256
   const long long want = 152LL * 2048;
@@ -504,8 +506,9 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, algo);
   if (team < 0 || (team > 0 && !valid_team(team)))
     return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 256", who, team);
-  if (algo == FD_ABIA && team > 1)
-    return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs one thread per problem (team 1)", who);
+  if (algo == FD_ABIA && team > 0 && !fdk::abia_team_ok(team))
+    return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs teams of 1, 8, 16 or 32 lanes, not %d", who,
+                team);
   if (b->n_problems == 0 || b->n_state_links == 0) return FD_OK;
   if (!q || !qd || !in3 || !out) return fail(FD_ERR_INVALID_ARG, "%s: NULL state array", who);
   const int t = resolve_team(b, algo, prec, team);
@@ -542,7 +545,7 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   else if (algo == FD_CFA) e = fdk::launch_cfa(a, prec_k, t, s);
   else if (algo == FD_CFA_CR) e = fdk::launch_cfa_cr(a, prec_k, t, s);
   else if (algo == FD_JSIIA) e = fdk::launch_jsiia(a, prec_k, t, s);
-  else e = fdk::launch_abia(a, prec_k, s);
+  else e = fdk::launch_abia(a, prec_k, t, s);
   cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, who);
   return FD_OK;
@@ -588,8 +591,9 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
   if (team < 0 || (team > 0 && !valid_team(team)))
     return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 256", who, team);
-  if (algo == FD_ABIA && team > 1)
-    return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs one thread per problem (team 1)", who);
+  if (algo == FD_ABIA && team > 0 && !fdk::abia_team_ok(team))
+    return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs teams of 1, 8, 16 or 32 lanes, not %d", who,
+                team);
   if (mass_bar && !b->chain->rigid)
     return fail(FD_ERR_UNSUPPORTED,
                 "%s: mass gradients need rigid-body inertias (J = [[I - m c^c^, m c^], "
@@ -636,7 +640,7 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
     if (algo == FD_CFA) return fdk::launch_cfa(k, prec_k, t, s);
     if (algo == FD_CFA_CR) return fdk::launch_cfa_cr(k, prec_k, t, s);
     if (algo == FD_JSIIA) return fdk::launch_jsiia(k, prec_k, t, s);
-    return fdk::launch_abia(k, prec_k, s);
+    return fdk::launch_abia(k, prec_k, t, s);
   };
   // 1. qdd (unless given)
   const void *qdd = qddot;
@@ -689,9 +693,8 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
   int cap = 1;
   while (cap < b->max_links && cap < 256) cap *= 2;
   std::vector<int> cand;
-  if (algo == FD_ABIA) cand.push_back(1);
-  else
-    for (int t = 1; t <= cap; t *= 2) cand.push_back(t);
+  for (int t = 1; t <= cap; t *= 2)
+    if (algo != FD_ABIA || fdk::abia_team_ok(t)) cand.push_back(t);
   if (b->n_problems == 0 || b->n_state_links == 0) {
     if (best_team) *best_team = 1;
     return FD_OK;

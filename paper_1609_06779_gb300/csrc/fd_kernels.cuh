@@ -764,4 +764,108 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
   set_status(A.status, pb.p, bad ? 2 : 0);
 }
 
+
+// ABIA with a team of P (8..32) lanes per problem. Inverse dynamics runs as the
+// segmented scans of the other kernels. The articulated-inertia recursion
+// stays serial in i, but each step's rank-1 update and congruence
+// P_{i-1} = J_{i-1} + X_i^T Pa_i X_i (X_i = Ad_{g_i^{-1}}) is spread over six
+// lanes, lane r carrying row r of the symmetric P: lane r forms column r of
+// N = X_i^T Pa_i, the team transposes N through shared memory, and lane r then
+// forms row r of N X_i = X_i^T N^T. Each lane thus spends two SE(3) transports
+// per link instead of twelve. The bias force and the short acceleration pass
+// run redundantly on every lane.
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
+  static_assert(P >= 8 && P <= 32, "six rows of P need a team of 8..32 lanes");
+  __shared__ TA xbuf[128 / P][2][36];
+  Team<P> tm;
+  Prob<T> pb;
+  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  const int n = pb.n;
+  const int r = tm.r < 6 ? tm.r : 5;  // lanes 6.. shadow row 5 and write nothing
+  TA(*xb)[36] = xbuf[(threadIdx.x & 127) / P];
+  TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_ABIA;
+  bool bad = false;
+  id_team<T, P>(tm, pb, A.grav, A.mode);
+  tm.sync();
+
+  TA prow[6], pbias[6];
+  if (n > 0) {
+    const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) prow[c] = TA(J[s6(r, c)]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) pbias[k] = TA(0);
+  for (int i = n - 1; i >= 0; --i) {
+    TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
+    TA h[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) h[c] = __shfl_sync(tm.mask, prow[c], 0, P);
+    const TA D = h[0];
+    const TA u = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]) - pbias[0];
+    bad |= !(D > TA(0));
+    const TA Dinv = TA(1) / D;
+    if (tm.r < 6) ra[A_H + tm.r] = prow[0];
+    if (tm.r == 0) {
+      ra[A_DD] = Dinv;
+      ra[A_UU] = u;
+    }
+    if (i == 0) break;
+    // row r of Pa = P - h h^T / D, and pa = p + h u / D
+    TA hs[6], par[6], pa[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      hs[c] = h[c] * Dinv;
+      par[c] = prow[c] - prow[0] * hs[c];
+      pa[c] = pbias[c] + hs[c] * u;
+    }
+    SE3<T> g;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+    SE3<TA> ga;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
+    TA ncol[6], nrow[6], orow[6];
+    adinvT(ga, par, ncol);  // column r of N = X^T Pa
+    TA *x = xb[i & 1];
+    if (tm.r < 6) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) x[k * 6 + r] = ncol[k];
+    }
+    tm.sync();
+#pragma unroll
+    for (int c = 0; c < 6; ++c) nrow[c] = x[r * 6 + c];
+    adinvT(ga, nrow, orow);  // row r of N X = X^T Pa X
+    const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) prow[c] = TA(J[s6(r, c)]) + orow[c];
+    adinvT(ga, pa, pbias);
+  }
+  tm.sync();
+  // forward: a' = X_i a_{i-1}, qdd_i = (u_i - h_i . a') / D_i, a_i = a' + e_1 qdd_i
+  TA acc[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+  for (int i = 0; i < n; ++i) {
+    const TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
+    SE3<T> g;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+    SE3<TA> ga;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
+    adinv(ga, acc, acc);
+    TA s = TA(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s += ra[A_H + k] * acc[k];
+    const TA qdd = (ra[A_UU] - s) * ra[A_DD];
+    acc[0] += qdd;
+    const T v = T(qdd);
+    if ((i & (P - 1)) == tm.r) pb.out[i] = v;
+    if (!finite_t(v)) bad = true;
+  }
+  if (tm.r == 0) set_status(A.status, pb.p, bad ? 2 : 0);
+}
+
 }  // namespace fdk

@@ -14,7 +14,10 @@ cudaError_t launch_id(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_cfa(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_cfa_cr(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_jsiia(const KArgs &a, int prec, int team, cudaStream_t s);
-cudaError_t launch_abia(const KArgs &a, int prec, cudaStream_t s);
+// team 1: one thread per problem; 8, 16, 32: rows of the articulated inertia
+// spread over six lanes of the team.
+cudaError_t launch_abia(const KArgs &a, int prec, int team, cudaStream_t s);
+inline bool abia_team_ok(int team) { return team == 1 || team == 8 || team == 16 || team == 32; }
 cudaError_t launch_adjoint_rnea(const KArgs &a, int prec, int team, cudaStream_t s);
 
 inline unsigned grid_for(int n_problems, int team) {

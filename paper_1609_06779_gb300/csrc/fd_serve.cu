@@ -127,6 +127,7 @@ struct Arena {
 
 constexpr int kTeamCFA = 8;     // fixed, so a request's arithmetic does not depend on the mix
 constexpr int kTeamReverse = 8;
+constexpr int kTeamABIA = 8;
 
 __global__ void scatter_kernel(const double *stage, const UpDesc *d, int nd, Arena A) {
   const int k = blockIdx.x;
@@ -430,8 +431,8 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
         a.team = kTeamCFA;
         return fdk::launch_cfa(a, 0, kTeamCFA, S->stream);
       }
-      a.team = 1;
-      return fdk::launch_abia(a, 0, S->stream);
+      a.team = kTeamABIA;
+      return fdk::launch_abia(a, 0, kTeamABIA, S->stream);
     });
   };
   if (e == cudaSuccess)

@@ -44,7 +44,7 @@ def test_long_chains_fp64(n, count):
                           model.offsets) for a, o in (("abia", "aba"), ("cfa", "cfa"))}
     floors["jsiia"] = floors["abia"]
     floors["cfa_cr"] = floors["cfa"]
-    for algo, team in (("abia", 1), ("cfa", 32), ("cfa", 8), ("cfa", 256), ("jsiia", 32),
+    for algo, team in (("abia", 1), ("abia", 8), ("abia", 32), ("cfa", 32), ("cfa", 8), ("cfa", 256), ("jsiia", 32),
                        ("jsiia", 128), ("cfa_cr", 1), ("cfa_cr", 32), ("cfa_cr", 256)):
         got, status = _gpu(model, st, algo, "fp64", team)
         assert (status == 0).all(), (algo, team)

@@ -56,10 +56,10 @@ RAGGED = [1, 2, 3, 5, 7, 8, 13, 31, 32, 33, 47, 64, 100]
 
 
 @pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr"])
-@pytest.mark.parametrize("team", [1, 2, 4, 8, 32, 64, 128, 256])
+@pytest.mark.parametrize("team", [1, 2, 4, 8, 16, 32, 64, 128, 256])
 def test_fd_fp64_ragged_parity(algo, team):
-    if algo == "abia" and team != 1:
-        pytest.skip("ABIA runs one thread per problem")
+    if algo == "abia" and team not in (1, 8, 16, 32):
+        pytest.skip("ABIA teams are 1, 8, 16, 32")
     model = synth.random_chains(RAGGED * 2, seed=7)
     st = synth.random_states(model.n_links_total, seed=8)
     ref, aba = _floor(model, st, model.offsets)
@@ -80,7 +80,7 @@ def test_fd_fp32_parity_short_chains(prec, algo):
     model = synth.random_chains([1, 2, 4, 7, 7, 7, 8] * 8, seed=11)
     st = synth.random_states(model.n_links_total, seed=12)
     ref = oracle.fd(model, st.q, st.qdot, st.tau)
-    for team in ([1] if algo == "abia" else [1, 8]):
+    for team in ([1, 8, 32] if algo == "abia" else [1, 8]):
         got, status = _run(model, st, algo, prec, team)
         assert (status == 0).all()
         err = _rel_err(got, ref, model.offsets)
@@ -125,7 +125,7 @@ def test_all_algorithms_and_teams_agree():
     st = synth.random_states(model.n_links_total, seed=22)
     base, _ = _run(model, st, "cfa", "fp64", 32)
     for algo, team in (("cfa", 1), ("cfa", 4), ("jsiia", 1), ("jsiia", 32), ("abia", 1),
-                       ("cfa_cr", 1), ("cfa_cr", 8), ("cfa_cr", 32)):
+                       ("abia", 8), ("abia", 32), ("cfa_cr", 1), ("cfa_cr", 8), ("cfa_cr", 32)):
         got, _ = _run(model, st, algo, "fp64", team)
         assert _rel_err(got, base, model.offsets).max() < 1e-10, (algo, team)
 
@@ -168,7 +168,7 @@ def test_bad_arguments_raise():
     with pytest.raises(fd.FDError):
         fd.solve(b, x[:7], x[:7], x[:7])                   # wrong size
     with pytest.raises(fd.FDError):
-        fd.solve(b, x, x, x, algo="abia", team=4)          # ABIA is one thread per chain
+        fd.solve(b, x, x, x, algo="abia", team=4)          # ABIA teams are 1, 8, 16, 32
     with pytest.raises(fd.FDError):
         fd.solve(b, x, x, x, team=3)                       # not a power of two
     ws = fd.workspace(b, "cfa")
@@ -217,7 +217,7 @@ def test_autotune_records_a_team_and_matches():
         best = fd.autotune(b, q, qd, tau, algo=algo)
         assert best in (1, 2, 4, 8, 16, 32), (algo, best)
         if algo == "abia":
-            assert best == 1
+            assert best in (1, 8, 16, 32)
         # team 0 now uses the tuned size: same workspace size as asking for it
         assert b.workspace_size(algo, "fp64", 0) == b.workspace_size(algo, "fp64", best)
         got = fd.solve(b, q, qd, tau, algo=algo).cpu().numpy()
