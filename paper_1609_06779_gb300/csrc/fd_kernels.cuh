@@ -49,6 +49,122 @@ __device__ __forceinline__ bool load_problem(const KArgs &A, const Team<P> &tm, 
 
 // -------------------------------------------------------- inverse dynamics
 
+// Chains up to this many links run inverse dynamics on component lanes
+// (id_lanes) when the team has 8..32 lanes; longer ones take the segmented scans.
+// The scans cost about three compositions per level of log2 P levels per lane;
+// the component lanes about nineteen FP64 instructions per link per lane.
+template <int P>
+__host__ __device__ constexpr int lanes_id_max_links() {
+  return P == 8 ? 30 : (P == 16 ? 40 : (P == 32 ? 50 : 0));
+}
+
+// Eq. 2a-2c with the six components of every twist, acceleration and force on
+// lanes 0..5 of the team (lanes 6.. shadow lane 5 and store nothing): the
+// recursions run serially over the links, one transport per lane per link,
+//   (Ad_{g^-1} x)_k   = (R^T w)_k                        (k < 3)
+//                     = (R^T v)_k + (w' x R^T p)_k,  w' = R^T w,
+//   (Ad_{g^-1}^T y)_k = (R n)_k + (p x R f)_k          (k < 3)
+//                     = (R f)_k,
+// the cross-product terms taking the other lanes' rotated components by
+// shuffle. Joint transforms and f_i = J_i Vd_i - ad_{V_i}^T J_i V_i, which do
+// not recur, run one link per lane. Same outputs as the scans (W_G, W_TD; V_i in
+// W_V, f_i in W_F), visible to the whole team on return.
+template <class T, int P>
+__device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, const double *grav,
+                                         int mode) {
+  static_assert(P >= 8 && P <= 32, "component lanes need a team of 8..32 lanes");
+  const int n = pb.n;
+  const bool mode_fd = mode == MODE_FD;
+  const int r = tm.r < 6 ? tm.r : 5;
+  const bool top = r < 3;
+  const int k = top ? r : r - 3;
+  const int ka = k == 2 ? 0 : k + 1, kb = k == 0 ? 2 : k - 1;  // k+1, k+2 mod 3
+  const bool store = tm.r < 6;
+
+  // joint transforms and R^T p, one link per lane
+  for (int i = tm.r; i < n; i += P) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    SE3<T> g;
+    joint_transform(pb.rec + static_cast<int64_t>(i) * REC, pb.q[i], g);
+    st_se3(w + W_G, g);
+    if (mode == MODE_LINEAR) {
+      w[W_TD] = pb.in3[i];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        w[W_PT + j] = g.R[j] * g.p[0] + g.R[3 + j] * g.p[1] + g.R[6 + j] * g.p[2];
+    }
+  }
+  tm.sync();
+  if (mode == MODE_LINEAR) return;
+
+  // twist V_i (Eq. 2a) and acceleration Vd_i (Eq. 2b), forward; Vd_i parks in W_F
+  T V[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  T Ac[6] = {T(0), T(0), T(0), T(-grav[0]), T(-grav[1]), T(-grav[2])};
+  for (int i = 0; i < n; ++i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    const T c0 = w[W_G + k], c1 = w[W_G + 3 + k], c2 = w[W_G + 6 + k];
+    const T pa = w[W_PT + ka], pbk = w[W_PT + kb];
+    const T qdi = pb.qd[i];
+    const T e0 = (r == 0) ? qdi : T(0);
+    // twist
+    T t = top ? c0 * V[0] + c1 * V[1] + c2 * V[2] : c0 * V[3] + c1 * V[4] + c2 * V[5];
+    T oa = __shfl_sync(tm.mask, t, ka, P), ob = __shfl_sync(tm.mask, t, kb, P);
+    T y = top ? t + e0 : t + oa * pbk - ob * pa;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) V[j] = __shfl_sync(tm.mask, y, j, P);
+    if (store) w[W_V + r] = y;
+    // acceleration: + ad_{V_i} e_1 qd_i = (0, w_z, -w_y; 0, v_z, -v_y) qd_i (+ e_1 qdd_i)
+    const T cv = r == 1 ? V[2] : (r == 2 ? -V[1] : (r == 4 ? V[5] : (r == 5 ? -V[4] : T(0))));
+    const T a0 = (r == 0 && !mode_fd) ? pb.in3[i] : T(0);
+    t = top ? c0 * Ac[0] + c1 * Ac[1] + c2 * Ac[2] : c0 * Ac[3] + c1 * Ac[4] + c2 * Ac[5];
+    oa = __shfl_sync(tm.mask, t, ka, P);
+    ob = __shfl_sync(tm.mask, t, kb, P);
+    y = top ? (t + a0) + cv * qdi : ((t + oa * pbk) - ob * pa) + cv * qdi;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) Ac[j] = __shfl_sync(tm.mask, y, j, P);
+    if (store) w[W_F + r] = y;
+  }
+  tm.sync();
+
+  // f_i = J_i Vd_i - ad_{V_i}^T J_i V_i, one link per lane
+  for (int i = tm.r; i < n; i += P) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+    T Vi[6], Ai[6], JV[6], f[6];
+    ldv<T, 6>(w + W_V, Vi);
+    ldv<T, 6>(w + W_F, Ai);
+    sym6_apply(rec + REC_J, Vi, JV);
+    adT_apply(Vi, JV, f);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) f[j] = -f[j];
+    sym6_apply_add(rec + REC_J, Ai, f);
+    stv<T, 6>(w + W_F, f);
+  }
+  tm.sync();
+
+  // force F_i = Ad_{g_{i+1}^{-1}}^T F_{i+1} + f_i (Eq. 2c), backward; tau_i = F_i[0] (2d)
+  T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  for (int i = n - 1; i >= 0; --i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    const T fi = w[W_F + r];
+    T y = fi;
+    if (i + 1 < n) {
+      const T *wn = w + NT;
+      const T c0 = wn[W_G + 3 * k], c1 = wn[W_G + 3 * k + 1], c2 = wn[W_G + 3 * k + 2];
+      const T pa = wn[W_G + 9 + ka], pbk = wn[W_G + 9 + kb];
+      const T t = top ? c0 * F[0] + c1 * F[1] + c2 * F[2] : c0 * F[3] + c1 * F[4] + c2 * F[5];
+      const T fa = __shfl_sync(tm.mask, t, 3 + ka, P), fb = __shfl_sync(tm.mask, t, 3 + kb, P);
+      y = top ? ((t + pa * fb) - pbk * fa) + fi : t + fi;
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) F[j] = __shfl_sync(tm.mask, y, j, P);
+    if (tm.r == 0) w[W_TD] = mode_fd ? pb.in3[i] - y : y;
+  }
+  tm.sync();
+}
+
+
 // Eq. 2a-2d for one problem: the twist and acceleration recursions (forward,
 // block lower bi-diagonal) and the force recursion (backward, block upper
 // bi-diagonal), each as a segmented scan over SE(3)-affine operators.
@@ -58,6 +174,12 @@ __device__ __forceinline__ bool load_problem(const KArgs &A, const Team<P> &tm, 
 template <class T, int P>
 __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, const double *grav,
                                         int mode) {
+  if constexpr (P >= 8 && P <= 32) {
+    if (pb.n <= lanes_id_max_links<P>()) {
+      id_lanes<T, P>(tm, pb, grav, mode);
+      return;
+    }
+  }
   const int a = pb.a, b = pb.b;
   const bool mode_fd = mode == MODE_FD;
   SegOp<T> op;
@@ -725,7 +847,7 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     const TA Dinv = TA(1) / D;
     for (int k = 0; k < 6; ++k) ra[A_H + k] = h[k];
     ra[A_DD] = Dinv;
-    ra[A_UU] = u;
+    ra[A_UU] = u * Dinv;
     if (i == 0) break;
     // Pa = P - h h^T / D, pa = p + h u / D
     TA Pa[21], pa[6], hs[6];
@@ -755,7 +877,7 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     adinv(ga, acc, acc);
     TA s = TA(0);
     for (int k = 0; k < 6; ++k) s += ra[A_H + k] * acc[k];
-    const TA qdd = (ra[A_UU] - s) * ra[A_DD];
+    const TA qdd = ra[A_UU] - s * ra[A_DD];
     acc[0] += qdd;
     const T v = T(qdd);
     pb.out[i] = v;
@@ -765,15 +887,15 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
 }
 
 
-// ABIA with a team of P (8..32) lanes per problem. Inverse dynamics runs as the
-// segmented scans of the other kernels. The articulated-inertia recursion
-// stays serial in i, but each step's rank-1 update and congruence
+// ABIA with a team of P (8..32) lanes per problem. Inverse dynamics runs on
+// the team (component lanes or segmented scans). The articulated-inertia
+// recursion stays serial in i, but each step's rank-1 update and congruence
 // P_{i-1} = J_{i-1} + X_i^T Pa_i X_i (X_i = Ad_{g_i^{-1}}) is spread over six
 // lanes, lane r carrying row r of the symmetric P: lane r forms column r of
 // N = X_i^T Pa_i, the team transposes N through shared memory, and lane r then
-// forms row r of N X_i = X_i^T N^T. Each lane thus spends two SE(3) transports
-// per link instead of twelve. The bias force and the short acceleration pass
-// run redundantly on every lane.
+// forms row r of N X_i = X_i^T N^T. The bias force and the acceleration pass
+// carry one component per lane, as in the component-lane inverse dynamics.
+// Each step's operands are loaded one step ahead (the loop is latency-bound).
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
   static_assert(P >= 8 && P <= 32, "six rows of P need a team of 8..32 lanes");
@@ -783,83 +905,139 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
   if (!load_problem<T, P>(A, tm, pb, NT)) return;
   const int n = pb.n;
   const int r = tm.r < 6 ? tm.r : 5;  // lanes 6.. shadow row 5 and write nothing
+  const bool top = r < 3;
+  const int k = top ? r : r - 3;
+  const int ka = k == 2 ? 0 : k + 1, kb = k == 0 ? 2 : k - 1;  // k+1, k+2 mod 3
   TA(*xb)[36] = xbuf[(threadIdx.x & 127) / P];
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_ABIA;
   bool bad = false;
   id_team<T, P>(tm, pb, A.grav, A.mode);
   tm.sync();
 
-  TA prow[6], pbias[6];
+  // operands of step i: tau_delta_i, g_i, row r of J_{i-1}
+  TA nt_td = TA(0), nt_J[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+  SE3<T> nt_g;
+  se3_identity(nt_g);
+  auto fetch = [&](int i) {
+    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    nt_td = TA(w[W_TD]);
+    if (i > 0) {
+      ld_se3(w + W_G, nt_g);
+      const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) nt_J[c] = TA(J[s6(r, c)]);
+    }
+  };
+  TA prow[6], pbr = TA(0);  // row r of P_i; component r of the bias force p_i
   if (n > 0) {
     const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
 #pragma unroll
     for (int c = 0; c < 6; ++c) prow[c] = TA(J[s6(r, c)]);
+    fetch(n - 1);
   }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) pbias[k] = TA(0);
   for (int i = n - 1; i >= 0; --i) {
+    const TA td = nt_td;
+    SE3<TA> ga;
+    TA Jr[6];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ga.R[c] = TA(nt_g.R[c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ga.p[c] = TA(nt_g.p[c]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) Jr[c] = nt_J[c];
+    if (i > 0) fetch(i - 1);
     TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
     TA h[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) h[c] = __shfl_sync(tm.mask, prow[c], 0, P);
+    const TA p0 = __shfl_sync(tm.mask, pbr, 0, P);
     const TA D = h[0];
-    const TA u = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]) - pbias[0];
     bad |= !(D > TA(0));
     const TA Dinv = TA(1) / D;
+    const TA uD = (td - p0) * Dinv;  // u_i / D_i
     if (tm.r < 6) ra[A_H + tm.r] = prow[0];
     if (tm.r == 0) {
       ra[A_DD] = Dinv;
-      ra[A_UU] = u;
+      ra[A_UU] = uD;
     }
     if (i == 0) break;
-    // row r of Pa = P - h h^T / D, and pa = p + h u / D
-    TA hs[6], par[6], pa[6];
+    // row r of Pa = P - h h^T / D; component r of pa = p + h u / D
+    const TA tr = prow[0] * Dinv;
+    TA par[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      hs[c] = h[c] * Dinv;
-      par[c] = prow[c] - prow[0] * hs[c];
-      pa[c] = pbias[c] + hs[c] * u;
-    }
-    SE3<T> g;
-    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
-    SE3<TA> ga;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
+    for (int c = 0; c < 6; ++c) par[c] = prow[c] - tr * h[c];
+    const TA par_b = pbr + prow[0] * uD;
     TA ncol[6], nrow[6], orow[6];
     adinvT(ga, par, ncol);  // column r of N = X^T Pa
     TA *x = xb[i & 1];
     if (tm.r < 6) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) x[k * 6 + r] = ncol[k];
+      for (int c = 0; c < 6; ++c) x[c * 6 + r] = ncol[c];
     }
+    // bias p_{i-1} = X^T pa, component r (the other lanes' components by shuffle)
+    TA pa[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) pa[c] = __shfl_sync(tm.mask, par_b, c, P);
+    const TA tb = top ? ga.R[3 * k] * pa[0] + ga.R[3 * k + 1] * pa[1] + ga.R[3 * k + 2] * pa[2]
+                      : ga.R[3 * k] * pa[3] + ga.R[3 * k + 1] * pa[4] + ga.R[3 * k + 2] * pa[5];
+    const TA fa = __shfl_sync(tm.mask, tb, 3 + ka, P), fb = __shfl_sync(tm.mask, tb, 3 + kb, P);
+    pbr = top ? (tb + ga.p[ka] * fb) - ga.p[kb] * fa : tb;
     tm.sync();
 #pragma unroll
     for (int c = 0; c < 6; ++c) nrow[c] = x[r * 6 + c];
     adinvT(ga, nrow, orow);  // row r of N X = X^T Pa X
-    const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) prow[c] = TA(J[s6(r, c)]) + orow[c];
-    adinvT(ga, pa, pbias);
+    for (int c = 0; c < 6; ++c) prow[c] = Jr[c] + orow[c];
   }
   tm.sync();
-  // forward: a' = X_i a_{i-1}, qdd_i = (u_i - h_i . a') / D_i, a_i = a' + e_1 qdd_i
+
+  // forward: a' = X_i a_{i-1}, qdd_i = u_i / D_i - (h_i . a') / D_i, a_i = a' + e_1 qdd_i;
+  // lane r forms component r of a' (as in the component-lane inverse dynamics)
+  TA nx_h[6], nx_dd = TA(0), nx_ud = TA(0), nx_c[3], nx_p[3];
+  auto fetch_f = [&](int i) {
+    const TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
+    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) nx_h[c] = ra[A_H + c];
+    nx_dd = ra[A_DD];
+    nx_ud = ra[A_UU];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      nx_c[c] = TA(w[W_G + 3 * c + k]);  // column k of R
+      nx_p[c] = TA(w[W_G + 9 + c]);
+    }
+  };
+  if (n > 0) fetch_f(0);
   TA acc[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
   for (int i = 0; i < n; ++i) {
-    const TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
-    SE3<T> g;
-    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
-    SE3<TA> ga;
+    TA hh[6], cc[3], pp[3];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
+    for (int c = 0; c < 6; ++c) hh[c] = nx_h[c];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
-    adinv(ga, acc, acc);
-    TA s = TA(0);
+    for (int c = 0; c < 3; ++c) {
+      cc[c] = nx_c[c];
+      pp[c] = nx_p[c];
+    }
+    const TA dd = nx_dd, ud = nx_ud;
+    if (i + 1 < n) fetch_f(i + 1);
+    // (Ad_{g^-1} a)_k = R^T w (k < 3), R^T (v + w x p) (k >= 3)
+    TA xv[3];
+    if (top) {
+      xv[0] = acc[0];
+      xv[1] = acc[1];
+      xv[2] = acc[2];
+    } else {
+      xv[0] = acc[3] + acc[1] * pp[2] - acc[2] * pp[1];
+      xv[1] = acc[4] + acc[2] * pp[0] - acc[0] * pp[2];
+      xv[2] = acc[5] + acc[0] * pp[1] - acc[1] * pp[0];
+    }
+    const TA y = cc[0] * xv[0] + cc[1] * xv[1] + cc[2] * xv[2];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) s += ra[A_H + k] * acc[k];
-    const TA qdd = (ra[A_UU] - s) * ra[A_DD];
+    for (int c = 0; c < 6; ++c) acc[c] = __shfl_sync(tm.mask, y, c, P);
+    TA sh = TA(0);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sh += hh[c] * acc[c];
+    const TA qdd = ud - sh * dd;
     acc[0] += qdd;
     const T v = T(qdd);
     if ((i & (P - 1)) == tm.r) pb.out[i] = v;

@@ -30,6 +30,8 @@ constexpr int W_V = 12;   // twist V_i
 constexpr int W_F = 18;   // f_i = J_i Vd_i - ad_{V_i}^T J_i V_i
 constexpr int W_TD = 24;  // tau_delta_i (or tau_i for inverse dynamics)
 constexpr int W_Z = 25;   // CFA: J^{-1} (I - Gamma)^T F products
+constexpr int W_PT = 25;  // R^T p of g_i while the component-lane inverse dynamics runs
+                          // (3 entries; CFA overwrites them with its W_Z products later)
 constexpr int NT = 32;    // T entries per link
 
 // Per-row workspace of the accumulation type TA for CFA's odd-even elimination.
@@ -54,7 +56,7 @@ constexpr int NA_JSIIA = 2;
 constexpr int NSQ_JSIIA = 1;
 constexpr int NP_JSIIA = 6;
 
-// ABIA: per-link TA entries: h_i = P_i S_i (6), D_i (1), u_i (1).
+// ABIA: per-link TA entries: h_i = P_i S_i (6), 1 / D_i (1), u_i / D_i (1).
 constexpr int A_H = 0;
 constexpr int A_DD = 6;
 constexpr int A_UU = 7;
