@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--chains", type=int, default=N_CHAINS)
     ap.add_argument("--links", type=int, default=N_LINKS)
-    ap.add_argument("--team", type=int, default=0)
+    ap.add_argument("--teams", default="",
+                    help="fixed teams, e.g. abia=1,jsiia=8,cfa=16,cfa_cr=4 (others autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -49,6 +50,14 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     return ap.parse_args()
+
+
+def fixed_teams(spec: str) -> dict:
+    out = {}
+    for item in filter(None, spec.split(",")):
+        k, v = item.split("=")
+        out[k.strip()] = int(v)
+    return out
 
 
 def dist_env():
@@ -100,17 +109,18 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_record(kernel: str):
-    """DRAM bytes per link of `kernel` from the committed ncu summary, if the
-    kernel sources are unchanged since the capture."""
+def traffic_record(kernel: str, team: int):
+    """DRAM bytes per link of `kernel` at `team` from the committed ncu summary,
+    if the kernel sources are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
-        rec = json.load(open(path))[kernel]
+        rec = json.load(open(path))
+        ent = rec[kernel][str(team)]
     except Exception:
         return None
     if rec.get("csrc_sha") != csrc_sha():
         return None
-    return rec
+    return ent
 
 
 def csrc_sha() -> str:
@@ -402,13 +412,9 @@ def main():
     q, qd, tau = (t(x, torch.float64) for x in (st.q, st.qdot, st.tau))
     out = {a: torch.empty_like(q) for a in ALGOS}
     teams = {}
+    forced = fixed_teams(args.teams)
     for a in ALGOS:  # schedule per algorithm, chosen by timing (untimed here)
-        if a == "abia":
-            teams[a] = 1            # the articulated-inertia recursion is serial per chain
-        elif args.team:
-            teams[a] = args.team
-        else:
-            teams[a] = fd.autotune(batch, q, qd, tau, algo=a, prec="fp64")
+        teams[a] = forced.get(a) or fd.autotune(batch, q, qd, tau, algo=a, prec="fp64")
     torch.cuda.empty_cache()
     ws = {a: fd.workspace(batch, a, "fp64", teams[a], dev) for a in ALGOS}
     stream = torch.cuda.current_stream(dev)
@@ -458,9 +464,9 @@ def main():
         rl[a] = {"ms": per_algo_ms[a], "tflops": ach, "frac": ach / FP64_PEAK_TFLOPS,
                  "solves_per_s": args.chains / (per_algo_ms[a] / 1e3)}
     dom = max(ALGOS, key=lambda a: per_algo_ms[a])
-    tr = traffic_record(f"{dom}_kernel")
+    tr = traffic_record(f"{dom}_kernel", teams[dom])
     traffic = None
-    if tr is not None and tr.get("team") == teams[dom]:
+    if tr is not None:
         # DRAM bytes of one launch: the capture's bytes per link x this launch's links
         traffic = tr["bytes_per_link"] * args.chains * args.links
     roof = {"bound": "alu", "achieved": rl[dom]["tflops"], "peak": FP64_PEAK_TFLOPS,
@@ -473,7 +479,7 @@ def main():
     # CFA with block cyclic reduction in place of OEE (context; not part of the step)
     variants = {}
     if rank == 0:
-        tcr = args.team or fd.autotune(batch, q, qd, tau, algo="cfa_cr", prec="fp64")
+        tcr = forced.get("cfa_cr") or fd.autotune(batch, q, qd, tau, algo="cfa_cr", prec="fp64")
         wcr = fd.workspace(batch, "cfa_cr", "fp64", tcr, dev)
         ocr = torch.empty_like(q)
         ms = _time_ms(lambda: fd.solve(batch, q, qd, tau, algo="cfa_cr", team=tcr, out=ocr,
@@ -488,7 +494,7 @@ def main():
         q32, qd32, tau32 = (x.float() for x in (q, qd, tau))
         for prec in ("fp32", "mixed"):
             for a in ALGOS:
-                tv = 1 if a == "abia" else args.team
+                tv = forced.get(a, 0)
                 if not tv:
                     fd.autotune(batch, q32, qd32, tau32, algo=a, prec=prec)
                 w = fd.workspace(batch, a, prec, tv, dev)
