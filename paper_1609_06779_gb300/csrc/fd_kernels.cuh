@@ -294,11 +294,28 @@ __global__ void __launch_bounds__(block_for<P>()) id_kernel(KArgs A) {
 
 // -------------------------------------------------------------------- CFA
 
+// Row i of a chain's CFA workspace: NA_CFA entries of TA, stored field-major
+// over the chain's n rows (entry k of row i at base[k n + i]), so that the lanes
+// of a team, working on neighbouring rows, touch neighbouring addresses.
+template <class E>
+struct RowP {
+  E *p;
+  int s;
+  __device__ __forceinline__ E &operator[](int k) const { return p[static_cast<int64_t>(k) * s]; }
+  __device__ __forceinline__ RowP operator+(int k) const {
+    return RowP{p + static_cast<int64_t>(k) * s, s};
+  }
+};
+template <class E>
+__device__ __forceinline__ RowP<E> rowp(E *wa, int n, int i) {
+  return RowP<E>{wa + i, n};
+}
+
 // (X K X^T)[1..5][1..5] + Kd[1..5][1..5] into packed lower 5x5, X = Ad_{g^{-1}},
 // K, Kd packed symmetric 6x6 (T_ii of Algorithm 1's CalcA, W_i^T T_ii W_i).
-template <class T, class TA>
+template <class T, class TA, class Out>
 __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, const T *Kself,
-                                            TA *D) {
+                                            Out D) {
   TA acc[15];
 #pragma unroll
   for (int r = 0; r < 5; ++r)
@@ -332,8 +349,8 @@ __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, con
 }
 
 // U_i = W_i^T T_{i,i+1} W_{i+1} = -(J_i^{-1} Ad_{g_{i+1}^{-1}}^T)[1..5][1..5]
-template <class T, class TA>
-__device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, TA *U) {
+template <class T, class TA, class Out>
+__device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, Out U) {
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     T e[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -353,7 +370,7 @@ __device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, TA *U
 template <class TA>
 __device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD, int srcU,
                                            int srcR) {
-  TA *row = wa + static_cast<int64_t>(m) * NA_CFA;
+  const RowP<TA> row = rowp(wa, n, m);
   TA Dm[15], L[15], inv[5];
 #pragma unroll
   for (int k = 0; k < 15; ++k) Dm[k] = row[srcD + k];
@@ -389,7 +406,7 @@ __device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD
 template <class TA>
 __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int srcD, int srcU,
                                         int srcR, TA *Dn, TA *Un, TA *Rn) {
-  const TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+  const RowP<const TA> row = rowp(wa, n, i);
 #pragma unroll
   for (int k = 0; k < 15; ++k) Dn[k] = row[srcD + k];
 #pragma unroll
@@ -397,7 +414,7 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
 #pragma unroll
   for (int k = 0; k < 25; ++k) Un[k] = TA(0);
   if (i + d < n) {
-    const TA *nb = wa + static_cast<int64_t>(i + d) * NA_CFA;
+    const RowP<const TA> nb = rowp(wa, n, i + d);
     TA L[15], inv[5];
 #pragma unroll
     for (int k = 0; k < 15; ++k) L[k] = nb[A_L + k];
@@ -436,7 +453,7 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
     }
   }
   if (i - d >= 0) {
-    const TA *pr = wa + static_cast<int64_t>(i - d) * NA_CFA;
+    const RowP<const TA> pr = rowp(wa, n, i - d);
     TA G[5][5];
 #pragma unroll
     for (int k = 0; k < 5; ++k)
@@ -467,28 +484,30 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
 // substitution then solves the rows level by level from the last one down:
 // x_i = D_i^{-1} (R_i - U_{i-d}^T x_{i-d} - U_i x_{i+d}).
 template <class TA, int P>
-__device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, int a, int b) {
+__device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n) {
   bool bad = false;
   int levels = 0;
   while ((1 << levels) < n) ++levels;
+  // the active rows of level j are i = (t + 1) d - 1, t = 0, 1, ...: lanes take t
+  // round robin (t even: eliminated, t odd: kept)
   for (int j = 1; j <= levels; ++j) {
     const int d = 1 << (j - 1);
-    for (int m = a; m < b; ++m) {  // eliminated rows: factors and saved coupling
-      if ((m + 1) % d != 0 || (((m + 1) / d) & 1) == 0) continue;
+    for (int t = 2 * tm.r; (t + 1) * d - 1 < n; t += 2 * P) {  // eliminated rows
+      const int m = (t + 1) * d - 1;
       bad |= !oee_factor<TA>(m, d, n, wa, A_D0, A_U0, A_R0);
-      if (m - d >= 0) {
-        const TA *lo = wa + static_cast<int64_t>(m - d) * NA_CFA + A_U0;
-        TA *row = wa + static_cast<int64_t>(m) * NA_CFA;
+      if (m - d >= 0) {  // keep the lower coupling for the back substitution
+        const RowP<TA> lo = rowp(wa, n, m - d) + A_U0;
+        const RowP<TA> row = rowp(wa, n, m);
 #pragma unroll
         for (int k = 0; k < 25; ++k) row[A_LO + k] = lo[k];
       }
     }
     tm.sync();
-    for (int i = a; i < b; ++i) {  // kept rows: update in place
-      if ((i + 1) % d != 0 || (((i + 1) / d) & 1) != 0) continue;
+    for (int t = 2 * tm.r + 1; (t + 1) * d - 1 < n; t += 2 * P) {  // kept rows: update in place
+      const int i = (t + 1) * d - 1;
       TA Dn[15], Un[25], Rn[5];
       oee_row<TA>(i, d, n, wa, A_D0, A_U0, A_R0, Dn, Un, Rn);
-      TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+      const RowP<TA> row = rowp(wa, n, i);
 #pragma unroll
       for (int k = 0; k < 15; ++k) row[A_D0 + k] = Dn[k];
 #pragma unroll
@@ -500,10 +519,10 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, int a
   }
   // rows never eliminated (n a power of two: row n - 1) are decoupled by now;
   // a row is eliminated at level 1 + (trailing zeros of i + 1)
-  for (int i = a; i < b; ++i) {
+  for (int i = tm.r; i < n; i += P) {
     const int je = __ffs(i + 1);
     if (je <= levels) continue;
-    TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    const RowP<TA> row = rowp(wa, n, i);
     TA Dm[15], L[15], inv[5], r[5];
 #pragma unroll
     for (int k = 0; k < 15; ++k) Dm[k] = row[A_D0 + k];
@@ -518,21 +537,21 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, int a
   tm.sync();
   for (int j = levels; j >= 1; --j) {
     const int d = 1 << (j - 1);
-    for (int i = a; i < b; ++i) {
-      if ((i + 1) % d != 0 || (((i + 1) / d) & 1) == 0) continue;
-      TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    for (int t = 2 * tm.r; (t + 1) * d - 1 < n; t += 2 * P) {
+      const int i = (t + 1) * d - 1;
+      const RowP<TA> row = rowp(wa, n, i);
       TA r[5], L[15], inv[5];
 #pragma unroll
       for (int k = 0; k < 5; ++k) r[k] = row[A_R0 + k];
       if (i + d < n) {  // - U_i x_{i+d}
-        const TA *xn = wa + static_cast<int64_t>(i + d) * NA_CFA + A_FC;
+        const RowP<TA> xn = rowp(wa, n, i + d) + A_FC;
 #pragma unroll
         for (int rr = 0; rr < 5; ++rr)
 #pragma unroll
           for (int k = 0; k < 5; ++k) r[rr] -= row[A_U0 + 5 * rr + k] * xn[k];
       }
       if (i - d >= 0) {  // - U_{i-d}^T x_{i-d}
-        const TA *xp = wa + static_cast<int64_t>(i - d) * NA_CFA + A_FC;
+        const RowP<TA> xp = rowp(wa, n, i - d) + A_FC;
 #pragma unroll
         for (int rr = 0; rr < 5; ++rr)
 #pragma unroll
@@ -559,7 +578,7 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
   Team<P> tm;
   Prob<T> pb;
   if (!load_problem<T, P>(A, tm, pb, NT)) return;
-  const int n = pb.n, a = pb.a, b = pb.b;
+  const int n = pb.n;
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_CFA;
   bool bad = false;
 
@@ -567,11 +586,12 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
   id_team<T, P>(tm, pb, A.grav, A.mode);
   tm.sync();
 
-  // CalcA: D_i, U_i; R = -B tau_delta applied as -W^T (I-Gamma) J^{-1} (I-Gamma)^T S tau_delta
-  for (int i = a; i < b; ++i) {
+  // CalcA: D_i, U_i; R = -B tau_delta applied as -W^T (I-Gamma) J^{-1} (I-Gamma)^T S tau_delta.
+  // From here on lanes take rows round robin (neighbouring rows on neighbouring lanes).
+  for (int i = tm.r; i < n; i += P) {
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
     const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
-    TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    const RowP<TA> row = rowp(wa, n, i);
     SE3<T> g;
     ld_se3(w + W_G, g);
     calc_dblock<T, TA>(i > 0 ? &g : nullptr, i > 0 ? rec - REC + REC_JI : nullptr,
@@ -595,7 +615,7 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
   }
   tm.sync();
-  for (int i = a; i < b; ++i) {
+  for (int i = tm.r; i < n; i += P) {
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
     T z[6];
     ldv<T, 6>(w + W_Z, z);
@@ -606,14 +626,14 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
       adinv(g, w - NT + W_Z, t);
       for (int k = 0; k < 6; ++k) z[k] -= t[k];
     }
-    TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    const RowP<TA> row = rowp(wa, n, i);
     for (int k = 0; k < 5; ++k) row[A_R0 + k] = TA(-z[k + 1]);
   }
   tm.sync();
 
   if constexpr (BTD == 1) {
     // SolvBTDSys by block cyclic reduction
-    bad |= cr_solve<TA, P>(tm, wa, n, a, b);
+    bad |= cr_solve<TA, P>(tm, wa, n);
   } else {
   // SolvBTDSys: odd-even elimination, ceil(log2 n) levels (Algorithm 2)
   int levels = 0;
@@ -623,12 +643,12 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     const int d = 1 << (j - 1);
     const int sD = src ? A_D1 : A_D0, sU = src ? A_U1 : A_U0, sR = src ? A_R1 : A_R0;
     const int tD = src ? A_D0 : A_D1, tU = src ? A_U0 : A_U1, tR = src ? A_R0 : A_R1;
-    for (int m = a; m < b; ++m) bad |= !oee_factor<TA>(m, d, n, wa, sD, sU, sR);
+    for (int m = tm.r; m < n; m += P) bad |= !oee_factor<TA>(m, d, n, wa, sD, sU, sR);
     tm.sync();
-    for (int i = a; i < b; ++i) {
+    for (int i = tm.r; i < n; i += P) {
       TA Dn[15], Un[25], Rn[5];
       oee_row<TA>(i, d, n, wa, sD, sU, sR, Dn, Un, Rn);
-      TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+      const RowP<TA> row = rowp(wa, n, i);
       for (int k = 0; k < 15; ++k) row[tD + k] = Dn[k];
       for (int k = 0; k < 25; ++k) row[tU + k] = Un[k];
       for (int k = 0; k < 5; ++k) row[tR + k] = Rn[k];
@@ -637,8 +657,8 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     src ^= 1;
   }
   // F_c,i = D_i^{-1} R_i
-  for (int i = a; i < b; ++i) {
-    TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+  for (int i = tm.r; i < n; i += P) {
+    const RowP<TA> row = rowp(wa, n, i);
     TA Dm[15], L[15], inv[5], r[5];
     for (int k = 0; k < 15; ++k) Dm[k] = row[(src ? A_D1 : A_D0) + k];
     for (int k = 0; k < 5; ++k) r[k] = row[(src ? A_R1 : A_R0) + k];
@@ -652,16 +672,16 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
 
   // CalcAcc: qdd = C tau_delta + B^T F_c = S^T (I-Gamma) J^{-1} (I-Gamma)^T F,
   // F_i = S tau_delta_i + W F_c,i (Eq. force-decomposition-global)
-  for (int i = a; i < b; ++i) {
+  for (int i = tm.r; i < n; i += P) {
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
     const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
-    const TA *row = wa + static_cast<int64_t>(i) * NA_CFA;
+    const RowP<TA> row = rowp(wa, n, i);
     T yv[6] = {w[W_TD], T(row[A_FC]), T(row[A_FC + 1]), T(row[A_FC + 2]), T(row[A_FC + 3]),
                T(row[A_FC + 4])};
     if (i + 1 < n) {
       SE3<T> gn;
       ld_se3(w + NT + W_G, gn);
-      const TA *rn = row + NA_CFA;
+      const RowP<TA> rn = rowp(wa, n, i + 1);
       T Fn[6] = {w[NT + W_TD], T(rn[A_FC]), T(rn[A_FC + 1]), T(rn[A_FC + 2]), T(rn[A_FC + 3]),
                  T(rn[A_FC + 4])};
       T t[6];
@@ -673,7 +693,7 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
   }
   tm.sync();
-  for (int i = a; i < b; ++i) {
+  for (int i = tm.r; i < n; i += P) {
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
     T qdd = w[W_Z];
     if (i > 0) {
