@@ -473,8 +473,7 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int team) {
   WsPlan w{align256(L * fdk::NT * ts), 0};
   if (algo == FD_CFA || algo == FD_CFA_CR) w.a_bytes = L * fdk::NA_CFA * as;
   if (algo == FD_JSIIA)
-    w.a_bytes = (L * (fdk::NA_JSIIA + fdk::NP_JSIIA * team) +
-                 static_cast<size_t>(b->sum_sq) * fdk::NSQ_JSIIA) * as;
+    w.a_bytes = (L * fdk::NA_JSIIA + static_cast<size_t>(b->sum_sq) * fdk::NSQ_JSIIA) * as;
   if (algo == FD_ABIA) w.a_bytes = L * fdk::NA_ABIA * as;
   w.a_bytes = align256(w.a_bytes);
   return w;

@@ -720,97 +720,6 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_cr_kerne
 
 // ------------------------------------------------------------------ JSIIA
 
-template <class T, class TA, int P>
-__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel(KArgs A) {
-  Team<P> tm;
-  Prob<T> pb;
-  if (!load_problem<T, P>(A, tm, pb, NT)) return;
-  const int n = pb.n, a = pb.a, b = pb.b;
-  const int64_t s0 = A.state_off[pb.p];
-  TA *vec = static_cast<TA *>(A.ws_a) + s0 * (NA_JSIIA + NP_JSIIA * P) + A.sq_off[pb.p] * NSQ_JSIIA;
-  TA *M = vec + static_cast<int64_t>(n) * NA_JSIIA;               // n x n, row-major
-  TA *acc = M + static_cast<int64_t>(n) * n;                      // [P][n][6]
-  TA *myacc = acc + static_cast<int64_t>(tm.r) * n * 6;
-  bool bad = false;
-
-  id_team<T, P>(tm, pb, A.grav, A.mode);
-  for (int i = a; i < b; ++i) vec[i] = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]);
-  tm.sync();
-
-  // columns of M: ID with qdd = e_k, qdot = 0, no gravity (Section II-C); the
-  // lower triangle i >= k of column k needs links k..n-1 only, so column k costs
-  // about n - k: lanes take columns in snake order (round t: t P + r, then
-  // t P + P - 1 - r) to balance that work.
-  for (int t = 0; t * P < n; ++t) {
-    const int k = t * P + ((t & 1) ? (P - 1 - tm.r) : tm.r);
-    if (k >= n) continue;
-    TA x[6] = {TA(1), TA(0), TA(0), TA(0), TA(0), TA(0)};
-    for (int c = 0; c < 6; ++c) myacc[static_cast<int64_t>(k) * 6 + c] = x[c];
-    for (int i = k + 1; i < n; ++i) {
-      SE3<T> g;
-      ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
-      SE3<TA> ga;
-      for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
-      for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
-      adinv(ga, x, x);
-      for (int c = 0; c < 6; ++c) myacc[static_cast<int64_t>(i) * 6 + c] = x[c];
-    }
-    TA y[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
-    for (int i = n - 1; i >= k; --i) {
-      TA va[6];
-      for (int c = 0; c < 6; ++c) va[c] = myacc[static_cast<int64_t>(i) * 6 + c];
-      sym6_apply_add(pb.rec + static_cast<int64_t>(i) * REC + REC_J, va, y);
-      M[static_cast<int64_t>(i) * n + k] = y[0];
-      SE3<T> g;
-      ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
-      SE3<TA> ga;
-      for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
-      for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
-      adinvT(ga, y, y);
-    }
-  }
-  tm.sync();
-
-  // Cholesky M = L L^T (right-looking, rows shared by the team), then the two
-  // triangular solves (the "inversion" of Section II-C read as a factorisation).
-  for (int j = 0; j < n; ++j) {
-    const TA djj = M[static_cast<int64_t>(j) * n + j];
-    bad |= !(djj > TA(0));
-    const TA r = djj > TA(0) ? rsqrt_t(djj) : TA(0);
-    for (int i = j + 1 + tm.r; i < n; i += P) M[static_cast<int64_t>(i) * n + j] *= r;
-    tm.sync();
-    if (tm.r == 0) M[static_cast<int64_t>(j) * n + j] = djj * r;
-    for (int i = j + 1 + tm.r; i < n; i += P) {
-      const TA lij = M[static_cast<int64_t>(i) * n + j];
-      for (int l = j + 1; l <= i; ++l) M[static_cast<int64_t>(i) * n + l] -= lij * M[static_cast<int64_t>(l) * n + j];
-    }
-    tm.sync();
-  }
-  for (int j = 0; j < n; ++j) {  // L y = b
-    const TA yj = vec[j] / M[static_cast<int64_t>(j) * n + j];
-    for (int i = j + 1 + tm.r; i < n; i += P) vec[i] -= M[static_cast<int64_t>(i) * n + j] * yj;
-    tm.sync();
-    if (tm.r == 0) vec[j] = yj;
-    tm.sync();
-  }
-  for (int j = n - 1; j >= 0; --j) {  // L^T x = y
-    const TA xj = vec[j] / M[static_cast<int64_t>(j) * n + j];
-    for (int i = tm.r; i < j; i += P) vec[i] -= M[static_cast<int64_t>(j) * n + i] * xj;
-    tm.sync();
-    if (tm.r == 0) vec[j] = xj;
-    tm.sync();
-  }
-  for (int i = a; i < b; ++i) {
-    const T v = T(vec[i]);
-    pb.out[i] = v;
-    if (!finite_t(v)) bad = true;
-  }
-  const bool any_bad = tm.any(bad);
-  if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
-}
-
-// ------------------------------------------------------------------- ABIA
-
 // Ad_{g^{-1}}^T P Ad_{g^{-1}} of a packed symmetric 6x6 P, added to Out.
 template <class TA>
 __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, TA *Out) {
@@ -835,6 +744,170 @@ __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, T
     for (int k = i; k < 6; ++k) Out[s6(i, k)] += o[k];
   }
 }
+
+
+// JSIIA (Section II-C): M by the unit-acceleration inverse dynamics of every
+// column, its Cholesky factor, two triangular solves.
+//
+// Column k's inverse dynamics (qdd = e_k, qdot = 0, no gravity) has the
+// accelerations x_i = X_{i<-k} e_1 (i >= k) and the force recursion
+// F_i = X_{i+1}^T F_{i+1} + J_i x_i. Every column's force recursion composes the
+// same operators, and composing them once gives the composite inertias
+// I^c_{i-1} = J_{i-1} + X_i^T I^c_i X_i with F_i = I^c_i x_i, so
+//   M[i][k] = e_1^T F_i = (X_{k+1}^T ... X_i^T h_i)[0],  h_i = I^c_i e_1:
+// one SE(3) transport per entry of the lower triangle. The composite recursion
+// runs on six lanes (row r of I^c on lane r, the congruence as two transports
+// per lane through a shared-memory transpose) for teams of 8 and more, on one
+// lane for smaller teams.
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel(KArgs A) {
+  constexpr int NXB = P >= 8 ? block_for<P>() / P : 1;
+  __shared__ TA xbuf[NXB][2][36];
+  Team<P> tm;
+  Prob<T> pb;
+  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  const int n = pb.n, a = pb.a, b = pb.b;
+  const int64_t s0 = A.state_off[pb.p];
+  TA *vec = static_cast<TA *>(A.ws_a) + s0 * NA_JSIIA + A.sq_off[pb.p] * NSQ_JSIIA;
+  TA *H = vec + n;                                   // h_i = I^c_i e_1, [n][6]
+  TA *M = vec + static_cast<int64_t>(n) * NA_JSIIA;  // n x n, column-major, lower triangle
+  // entry (i, l) of M (and of L) at M[l n + i]: the lanes, on neighbouring rows,
+  // touch neighbouring addresses
+  auto Mat = [&](int i, int l) -> TA & { return M[static_cast<int64_t>(l) * n + i]; };
+  bool bad = false;
+
+  id_team<T, P>(tm, pb, A.grav, A.mode);
+  for (int i = a; i < b; ++i) vec[i] = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]);
+
+  // composite inertias, backward over the links; h_i = column 0 of I^c_i
+  auto load_g = [&](int i, SE3<TA> &ga) {
+    SE3<T> g;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
+  };
+  if constexpr (P >= 8) {
+    tm.sync();  // the g_i of every link
+    if (P <= 32 || tm.r < 32) {  // warp 0 of the team
+      const unsigned wmask = P <= 32 ? tm.mask : 0xffffffffu;
+      const int r = tm.r < 6 ? tm.r : 5;  // lanes 6.. shadow row 5 and write nothing
+      TA(*xb)[36] = xbuf[(threadIdx.x % block_for<P>()) / P];
+      TA prow[6];
+      if (n > 0) {
+        const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) prow[c] = TA(J[s6(r, c)]);
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        if (tm.r < 6) H[static_cast<int64_t>(i) * 6 + r] = prow[0];
+        if (i == 0) break;
+        SE3<TA> ga;
+        load_g(i, ga);
+        TA Jr[6], ncol[6], nrow[6], orow[6];
+        const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Jr[c] = TA(J[s6(r, c)]);
+        adinvT(ga, prow, ncol);  // column r of N = X^T I^c
+        TA *x = xb[i & 1];
+        if (tm.r < 6) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) x[c * 6 + r] = ncol[c];
+        }
+        __syncwarp(wmask);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) nrow[c] = x[r * 6 + c];
+        adinvT(ga, nrow, orow);  // row r of N X = X^T I^c X
+#pragma unroll
+        for (int c = 0; c < 6; ++c) prow[c] = Jr[c] + orow[c];
+      }
+    }
+  } else {
+    tm.sync();
+    if (tm.r == 0) {
+      TA Pm[21];
+      if (n > 0) {
+        const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
+        for (int k = 0; k < 21; ++k) Pm[k] = TA(J[k]);
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        for (int c = 0; c < 6; ++c) H[static_cast<int64_t>(i) * 6 + c] = Pm[s6(0, c)];
+        if (i == 0) break;
+        SE3<TA> ga;
+        load_g(i, ga);
+        TA Pn[21];
+        const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
+        for (int k = 0; k < 21; ++k) Pn[k] = TA(J[k]);
+        congruence_add(ga, Pm, Pn);
+        for (int k = 0; k < 21; ++k) Pm[k] = Pn[k];
+      }
+    }
+  }
+  tm.sync();
+
+  // lower triangle, row by row: row i costs i transports, so lanes take rows in
+  // snake order (round t: t P + r, then t P + P - 1 - r) to balance the work
+  for (int t = 0; t * P < n; ++t) {
+    const int i = t * P + ((t & 1) ? (P - 1 - tm.r) : tm.r);
+    if (i >= n) continue;
+    TA z[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) z[c] = H[static_cast<int64_t>(i) * 6 + c];
+    Mat(i, i) = z[0];
+    for (int j = i; j >= 1; --j) {
+      SE3<TA> ga;
+      load_g(j, ga);
+      adinvT(ga, z, z);
+      Mat(i, j - 1) = z[0];
+    }
+  }
+  tm.sync();
+
+  // Cholesky M = L L^T (right-looking, rows shared by the team), then the two
+  // triangular solves (the "inversion" of Section II-C read as a factorisation);
+  // 1 / L_jj is kept in h_j[0] so the solves multiply instead of dividing.
+  for (int j = 0; j < n; ++j) {
+    const TA djj = Mat(j, j);
+    bad |= !(djj > TA(0));
+    const TA r = djj > TA(0) ? rsqrt_t(djj) : TA(0);
+    for (int i = j + 1 + tm.r; i < n; i += P) Mat(i, j) *= r;
+    tm.sync();
+    if (tm.r == 0) {
+      Mat(j, j) = djj * r;
+      H[static_cast<int64_t>(j) * 6] = r;
+    }
+    for (int i = j + 1 + tm.r; i < n; i += P) {
+      const TA lij = Mat(i, j);
+      for (int l = j + 1; l <= i; ++l) Mat(i, l) -= lij * Mat(l, j);
+    }
+    tm.sync();
+  }
+  for (int j = 0; j < n; ++j) {  // L y = b
+    const TA yj = vec[j] * H[static_cast<int64_t>(j) * 6];
+    for (int i = j + 1 + tm.r; i < n; i += P) vec[i] -= Mat(i, j) * yj;
+    tm.sync();
+    if (tm.r == 0) vec[j] = yj;
+    tm.sync();
+  }
+  for (int j = n - 1; j >= 0; --j) {  // L^T x = y
+    const TA xj = vec[j] * H[static_cast<int64_t>(j) * 6];
+    for (int i = tm.r; i < j; i += P) vec[i] -= Mat(j, i) * xj;
+    tm.sync();
+    if (tm.r == 0) vec[j] = xj;
+    tm.sync();
+  }
+  for (int i = a; i < b; ++i) {
+    const T v = T(vec[i]);
+    pb.out[i] = v;
+    if (!finite_t(v)) bad = true;
+  }
+  const bool any_bad = tm.any(bad);
+  if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
+}
+
+// ------------------------------------------------------------------- ABIA
+
 
 // ABIA (Section II-C): tau_delta by inverse dynamics, the articulated-body
 // inertia recursion P_{i-1} = J_{i-1} + X_i^T (P_i - P_i S D_i^{-1} S^T P_i) X_i

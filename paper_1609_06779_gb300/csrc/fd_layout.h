@@ -49,12 +49,10 @@ constexpr int A_GR = 140;
 constexpr int A_LO = 145;  // cyclic reduction: the lower coupling U_{i-d} kept for back substitution
 constexpr int NA_CFA = 170;
 
-// JSIIA: per-link TA entries (right-hand side), n*n TA entries (M), and per team
-// lane 6 TA entries per link (the column's accelerations).
-constexpr int A_B = 0;
-constexpr int NA_JSIIA = 2;
+// JSIIA: per-link TA entries (right-hand side 1, h_i = I^c_i e_1 6, pad 1) and
+// n*n TA entries (M).
+constexpr int NA_JSIIA = 8;
 constexpr int NSQ_JSIIA = 1;
-constexpr int NP_JSIIA = 6;
 
 // ABIA: per-link TA entries: h_i = P_i S_i (6), 1 / D_i (1), u_i / D_i (1).
 constexpr int A_H = 0;

@@ -35,11 +35,12 @@ def abia_flops(n: int) -> int:
 
 
 def jsiia_flops(n: int) -> int:
-    """ID + lower-triangle columns of M by ID (forward transports, then J Vd,
-    accumulation and transport per link of the column) + Cholesky n^3/3 + two
-    triangular solves 2 n^2."""
-    cols = ADJ * n * (n - 1) // 2 + (SYM6 + 6 + ADJ) * n * (n + 1) // 2
-    return id_flops(n) + cols + (n ** 3) // 3 + 2 * n * n
+    """ID + the composite inertias of the unit-acceleration columns (n - 1
+    congruences X^T I X: 12 transports, + J 21) + one transport per entry below
+    the diagonal of M + Cholesky n^3/3 + two triangular solves 2 n^2."""
+    composite = max(n - 1, 0) * (12 * ADJ + 21)
+    entries = ADJ * n * (n - 1) // 2
+    return id_flops(n) + composite + entries + (n ** 3) // 3 + 2 * n * n
 
 
 def oee_flops(n: int) -> int:
