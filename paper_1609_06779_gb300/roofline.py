@@ -27,10 +27,15 @@ def id_flops(n: int) -> int:
     return n * (JT + (ADJ + 1) + (ADJ + 8) + (2 * SYM6 + ADT + 6) + (ADJ + 7))
 
 
+# X^T P X + J in rotated 3x3 blocks (R A, R B, R C 135; B' 45; C' 30;
+# B'' = B' + p^ C' 36; top-left block with its cross terms 84; + J 15)
+CONG_BLOCKS = 345
+
+
 def abia_flops(n: int) -> int:
-    """ID + articulated-inertia recursion (Pa 63 + 1, pa 18, congruence 12 adjoint
-    applications, + J 21, bias transport 42) for n-1 links + forward pass 56."""
-    per_abi = 64 + 18 + 12 * ADJ + 21 + ADJ
+    """ID + articulated-inertia recursion (Pa 63 + 1, pa 18, congruence with J
+    in blocks 345, bias transport 42) for n-1 links + forward pass 56."""
+    per_abi = 64 + 18 + CONG_BLOCKS + ADJ
     return id_flops(n) + max(n - 1, 0) * per_abi + n * (ADJ + 14)
 
 
