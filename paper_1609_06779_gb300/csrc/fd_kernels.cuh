@@ -53,9 +53,11 @@ __device__ __forceinline__ bool load_problem(const KArgs &A, const Team<P> &tm, 
 // (id_lanes) when the team has 8..32 lanes; longer ones take the segmented scans.
 // The scans cost about three compositions per level of log2 P levels per lane;
 // the component lanes about nineteen FP64 instructions per link per lane.
+// Measured on GB300 (teams 8, 16, 32): the component lanes are faster up to 32
+// links (by 7-50%), even at 64, slower from 128 on.
 template <int P>
 __host__ __device__ constexpr int lanes_id_max_links() {
-  return P == 8 ? 30 : (P == 16 ? 40 : (P == 32 ? 50 : 0));
+  return (P >= 8 && P <= 32) ? 64 : 0;
 }
 
 // Eq. 2a-2c with the six components of every twist, acceleration and force on
