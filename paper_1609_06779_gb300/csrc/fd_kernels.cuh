@@ -920,7 +920,18 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
     }
     for (int i = j + 1 + tm.r; i < n; i += P) {
       const TA lij = Mat(i, j);
-      for (int l = j + 1; l <= i; ++l) Mat(i, l) -= lij * Mat(l, j);
+      int l = j + 1;
+      for (; l + 4 <= i + 1; l += 4) {  // loads of a batch first, so they overlap
+        TA x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[u] = Mat(i, l + u);
+          y[u] = Mat(l + u, j);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) Mat(i, l + u) = x[u] - lij * y[u];
+      }
+      for (; l <= i; ++l) Mat(i, l) -= lij * Mat(l, j);
     }
     tm.sync();
   }
