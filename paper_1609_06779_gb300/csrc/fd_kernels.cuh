@@ -905,50 +905,135 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
   }
   tm.sync();
 
-  // Cholesky M = L L^T (right-looking, rows shared by the team), then the two
-  // triangular solves (the "inversion" of Section II-C read as a factorisation);
-  // 1 / L_jj is kept in h_j[0] so the solves multiply instead of dividing.
-  for (int j = 0; j < n; ++j) {
-    const TA djj = Mat(j, j);
-    bad |= !(djj > TA(0));
-    const TA r = djj > TA(0) ? rsqrt_t(djj) : TA(0);
-    for (int i = j + 1 + tm.r; i < n; i += P) Mat(i, j) *= r;
+  // Cholesky M = L L^T by blocks of four columns (right-looking, rows shared by
+  // the team): every lane factors the 4x4 diagonal block, each lane forms the
+  // panel of its rows below it, then applies the rank-4 update to its rows of
+  // the trailing matrix (four fused operations per load and store). Then the
+  // two triangular solves, also by blocks of four (the "inversion" of Section
+  // II-C read as a factorisation). 1 / L_jj is kept in h_j[0].
+  constexpr int NB = 4;
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int jb = min(NB, n - j0);
+    TA Ld[NB][NB], rinv[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+#pragma unroll
+      for (int v = 0; v < NB; ++v) Ld[u][v] = (u < jb && v <= u) ? Mat(j0 + u, j0 + v) : TA(0);
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      rinv[u] = TA(0);
+      if (u < jb) {
+        TA d = Ld[u][u];
+#pragma unroll
+        for (int w = 0; w < u; ++w) d -= Ld[u][w] * Ld[u][w];
+        bad |= !(d > TA(0));
+        const TA r = d > TA(0) ? rsqrt_t(d) : TA(0);
+        Ld[u][u] = d * r;
+        rinv[u] = r;
+#pragma unroll
+        for (int v = u + 1; v < NB; ++v) {
+          TA x = Ld[v][u];
+#pragma unroll
+          for (int w = 0; w < u; ++w) x -= Ld[v][w] * Ld[u][w];
+          Ld[v][u] = x * r;
+        }
+      }
+    }
+    // panel: L(i, j0+u) = (M(i, j0+u) - sum_{w<u} L(i, j0+w) L(j0+u, j0+w)) / L(j0+u, j0+u)
+    for (int i = j0 + jb + tm.r; i < n; i += P) {  // below the block, jb == NB
+      TA li[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        TA x = Mat(i, j0 + u);
+#pragma unroll
+        for (int w = 0; w < u; ++w) x -= li[w] * Ld[u][w];
+        li[u] = x * rinv[u];
+      }
+#pragma unroll
+      for (int u = 0; u < NB; ++u) Mat(i, j0 + u) = li[u];
+    }
+    tm.sync();
+    if (tm.r == 0) {  // every lane has read the diagonal block by now
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        if (u < jb) {
+#pragma unroll
+          for (int v = 0; v <= u; ++v) Mat(j0 + u, j0 + v) = Ld[u][v];
+          H[static_cast<int64_t>(j0 + u) * 6] = rinv[u];
+        }
+      }
+    }
+    // rank-4 update of the trailing rows: M(i, l) -= sum_u L(i, j0+u) L(l, j0+u)
+    for (int i = j0 + jb + tm.r; i < n; i += P) {
+      TA li[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) li[u] = Mat(i, j0 + u);
+#pragma unroll 2
+      for (int l = j0 + jb; l <= i; ++l) {
+        TA x = Mat(i, l);
+#pragma unroll
+        for (int u = 0; u < NB; ++u) x -= li[u] * Mat(l, j0 + u);
+        Mat(i, l) = x;
+      }
+    }
+    tm.sync();
+  }
+  for (int j0 = 0; j0 < n; j0 += NB) {  // L y = b
+    const int jb = min(NB, n - j0);
+    TA y[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      y[u] = TA(0);
+      if (u < jb) {
+        TA x = vec[j0 + u];
+#pragma unroll
+        for (int w = 0; w < u; ++w) x -= Mat(j0 + u, j0 + w) * y[w];
+        y[u] = x * H[static_cast<int64_t>(j0 + u) * 6];
+      }
+    }
+    for (int i = j0 + jb + tm.r; i < n; i += P) {
+      TA x = vec[i];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) x -= Mat(i, j0 + u) * y[u];
+      vec[i] = x;
+    }
+    tm.sync();
+    if (tm.r == 0) {  // after every lane has read this block's right-hand side
+#pragma unroll
+      for (int u = 0; u < NB; ++u)
+        if (u < jb) vec[j0 + u] = y[u];
+    }
+  }
+  tm.sync();
+  for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {  // L^T x = y
+    const int jb = min(NB, n - j0);
+    TA x[NB];
+#pragma unroll
+    for (int u = NB - 1; u >= 0; --u) {
+      x[u] = TA(0);
+      if (u < jb) {
+        TA t = vec[j0 + u];
+#pragma unroll
+        for (int w = u + 1; w < NB; ++w)
+          if (w < jb) t -= Mat(j0 + w, j0 + u) * x[w];
+        x[u] = t * H[static_cast<int64_t>(j0 + u) * 6];
+      }
+    }
+    for (int i = tm.r; i < j0; i += P) {
+      TA t = vec[i];
+#pragma unroll
+      for (int u = 0; u < NB; ++u)
+        if (u < jb) t -= Mat(j0 + u, i) * x[u];
+      vec[i] = t;
+    }
     tm.sync();
     if (tm.r == 0) {
-      Mat(j, j) = djj * r;
-      H[static_cast<int64_t>(j) * 6] = r;
-    }
-    for (int i = j + 1 + tm.r; i < n; i += P) {
-      const TA lij = Mat(i, j);
-      int l = j + 1;
-      for (; l + 4 <= i + 1; l += 4) {  // loads of a batch first, so they overlap
-        TA x[4], y[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          x[u] = Mat(i, l + u);
-          y[u] = Mat(l + u, j);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) Mat(i, l + u) = x[u] - lij * y[u];
-      }
-      for (; l <= i; ++l) Mat(i, l) -= lij * Mat(l, j);
+      for (int u = 0; u < NB; ++u)
+        if (u < jb) vec[j0 + u] = x[u];
     }
-    tm.sync();
   }
-  for (int j = 0; j < n; ++j) {  // L y = b
-    const TA yj = vec[j] * H[static_cast<int64_t>(j) * 6];
-    for (int i = j + 1 + tm.r; i < n; i += P) vec[i] -= Mat(i, j) * yj;
-    tm.sync();
-    if (tm.r == 0) vec[j] = yj;
-    tm.sync();
-  }
-  for (int j = n - 1; j >= 0; --j) {  // L^T x = y
-    const TA xj = vec[j] * H[static_cast<int64_t>(j) * 6];
-    for (int i = tm.r; i < j; i += P) vec[i] -= Mat(j, i) * xj;
-    tm.sync();
-    if (tm.r == 0) vec[j] = xj;
-    tm.sync();
-  }
+  tm.sync();
   for (int i = a; i < b; ++i) {
     const T v = T(vec[i]);
     pb.out[i] = v;
