@@ -125,9 +125,15 @@ struct Arena {
   double *r_dt;                                     // per slot: dt
 };
 
-constexpr int kTeamCFA = 8;     // fixed, so a request's arithmetic does not depend on the mix
-constexpr int kTeamReverse = 8;
-constexpr int kTeamABIA = 8;
+// Teams depend on a request's algorithm and chain length only, so its arithmetic
+// does not depend on the mix. CFA and the reverse sweep take about one lane per
+// four links (8..64): long chains bound a tick's latency, and a small team
+// leaves a 256-link chain's OEE levels serial on eight lanes. ABIA takes 8.
+enum TeamKind { kTeamCFA, kTeamReverse, kTeamABIA };
+int team_for(TeamKind k, int n) {
+  if (k == kTeamABIA) return 8;
+  return n <= 32 ? 8 : (n <= 64 ? 16 : (n <= 128 ? 32 : 64));
+}
 
 __global__ void scatter_kernel(const double *stage, const UpDesc *d, int nd, Arena A) {
   const int k = blockIdx.x;
@@ -154,10 +160,12 @@ __global__ void scatter_kernel(const double *stage, const UpDesc *d, int nd, Are
 }
 
 // one semi-implicit Euler step per rollout: qd += dt qdd, q += dt qd, then the
-// next step's torque from the request's history
+// next step's torque from the request's history; one warp per rollout, lanes
+// over its links
 __global__ void rollout_step_kernel(const int32_t *prob_chain, const int64_t *model_off,
                                     const int64_t *state_off, int np, Arena A) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
   if (p >= np) return;
   const int c = prob_chain[p];
   const int n = static_cast<int>(model_off[c + 1] - model_off[c]);
@@ -165,13 +173,15 @@ __global__ void rollout_step_kernel(const int32_t *prob_chain, const int64_t *mo
   const double dt = A.r_dt[s];
   const int step = A.r_step[s] + 1;
   const bool more = step < A.r_steps[s];
-  for (int i = 0; i < n; ++i) {
+  const int64_t h = A.r_hist[s] + static_cast<int64_t>(step - 1) * n;
+  for (int i = lane; i < n; i += 32) {
     const double v = A.qd[s + i] + dt * A.qdd[s + i];
     A.qd[s + i] = v;
     A.q[s + i] += dt * v;
-    if (more) A.tau[s + i] = A.hist[A.r_hist[s] + static_cast<int64_t>(step - 1) * n + i];
+    if (more) A.tau[s + i] = A.hist[h + i];
   }
-  A.r_step[s] = step;
+  __syncwarp();
+  if (lane == 0) A.r_step[s] = step;
 }
 
 __global__ void gather_kernel(const OutDesc *d, int nd, Arena A, const int32_t *status,
@@ -285,22 +295,23 @@ fdk::KArgs base_args(fd_server_s *S) {
   return a;
 }
 
-// Launch kernel `fn` over the problems [p0, p0 + np), either at once or, in the
-// per-size mode, once per distinct chain length.
+// Launch kernel `fn(first, count, team)` over the problems [p0, p0 + np), sorted
+// by length within their group: once per team class (a handful of launches) or,
+// in the per-size mode, once per distinct chain length.
 template <class F>
-cudaError_t over(fd_server_s *S, const std::vector<Req *> &all, int p0, int np, F fn) {
+cudaError_t over(fd_server_s *S, const std::vector<Req *> &all, int p0, int np, TeamKind k,
+                 F fn) {
   if (np <= 0) return cudaSuccess;
-  if (!(S->flags & FD_SERVE_PER_SIZE)) {
-    ++S->launches;
-    return fn(p0, np);
-  }
-  // the problems [p0, p0+np) are sorted by length within their group
+  const bool per_size = (S->flags & FD_SERVE_PER_SIZE) != 0;
   int s = p0;
   while (s < p0 + np) {
+    const int t = team_for(k, all[s]->n);
     int e = s + 1;
-    while (e < p0 + np && all[e]->n == all[s]->n) ++e;
+    while (e < p0 + np &&
+           (per_size ? all[e]->n == all[s]->n : team_for(k, all[e]->n) == t))
+      ++e;
     ++S->launches;
-    cudaError_t err = fn(s, e - s);
+    cudaError_t err = fn(s, e - s, t);
     if (err != cudaSuccess) return err;
     s = e;
   }
@@ -416,7 +427,8 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
 
   // 3. forward dynamics of every active request
   auto fd_launch = [&](int algo, int mode, const double *in3, double *out, int p0, int cnt) {
-    return over(S, all, p0, cnt, [&](int s, int c) {
+    const TeamKind k = algo == FD_CFA ? kTeamCFA : kTeamABIA;
+    return over(S, all, p0, cnt, k, [&](int s, int c, int t) {
       fdk::KArgs a = base_args(S);
       a.prob_chain = S->d_prob + s;
       a.state_off = S->d_soff + s;
@@ -427,12 +439,9 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       a.out = out;
       a.mode = mode;
       a.status = mode == fdk::MODE_FD ? S->d_status + s : nullptr;
-      if (algo == FD_CFA) {
-        a.team = kTeamCFA;
-        return fdk::launch_cfa(a, 0, kTeamCFA, S->stream);
-      }
-      a.team = kTeamABIA;
-      return fdk::launch_abia(a, 0, kTeamABIA, S->stream);
+      a.team = t;
+      if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, S->stream);
+      return fdk::launch_abia(a, 0, t, S->stream);
     });
   };
   if (e == cudaSuccess)
@@ -445,12 +454,12 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
   if (e == cudaSuccess)
     e = fd_launch(FD_ABIA, fdk::MODE_LINEAR, S->A.w, S->A.tbar, gstart[2], gstart[3] - gstart[2]);
   auto reverse = [&](int p0, int cnt) {
-    return over(S, all, p0, cnt, [&](int s, int c) {
+    return over(S, all, p0, cnt, kTeamReverse, [&](int s, int c, int t) {
       fdk::KArgs a = base_args(S);
       a.prob_chain = S->d_prob + s;
       a.state_off = S->d_soff + s;
       a.n_problems = c;
-      a.team = kTeamReverse;
+      a.team = t;
       a.q = S->A.q;
       a.qd = S->A.qd;
       a.in3 = S->A.qdd;
@@ -458,7 +467,7 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       a.out = S->A.qbar;
       a.out2 = S->A.qdbar;
       a.out3 = nullptr;
-      return fdk::launch_adjoint_rnea(a, 0, kTeamReverse, S->stream);
+      return fdk::launch_adjoint_rnea(a, 0, t, S->stream);
     });
   };
   if (e == cudaSuccess) e = reverse(gstart[0], gstart[1] - gstart[0]);
@@ -474,7 +483,7 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
   auto roll = [&](int p0, int cnt) {
     if (cnt <= 0) return cudaSuccess;
     ++S->launches;
-    rollout_step_kernel<<<(cnt + 127) / 128, 128, 0, S->stream>>>(S->d_prob + p0, S->d_moff,
+    rollout_step_kernel<<<(cnt + 3) / 4, 128, 0, S->stream>>>(S->d_prob + p0, S->d_moff,
                                                                 S->d_soff + p0, cnt, S->A);
     return cudaGetLastError();
   };
