@@ -118,7 +118,12 @@ struct OutDesc {
 struct Arena {
   double *model;                                    // model records [cap_rec][REC]
   double *q, *qd, *tau, *qdd, *w, *qbar, *qdbar, *tbar;  // [cap] per link slot
-  double *ws_t, *ws_a;                              // [cap][NT_ADJ], [cap][NA_CFA]
+  // workspaces per link slot, one region per kernel kind: the kinds index them
+  // with different strides and run concurrently on the side streams
+  double *ws_t;                                     // [cap][NT]      FD kernels
+  double *ws_r;                                     // [cap][NT_ADJ]  reverse sweep
+  double *ws_c;                                     // [cap][NA_CFA]  CFA rows
+  double *ws_b;                                     // [cap][NA_ABIA] ABIA
   double *hist;                                     // rollout torques
   int64_t *r_hist;                                  // per slot: history start
   int32_t *r_step, *r_steps;                        // per slot: step, total steps
@@ -133,6 +138,10 @@ enum TeamKind { kTeamCFA, kTeamReverse, kTeamABIA };
 int team_for(TeamKind k, int n) {
   if (k == kTeamABIA) return 8;
   return n <= 32 ? 8 : (n <= 64 ? 16 : (n <= 128 ? 32 : 64));
+}
+// side stream of a launch: ABIA requests on stream 4, CFA team classes 8..64 on 0..3
+int aux_of(bool abia, int team) {
+  return abia ? 4 : (team <= 8 ? 0 : (team <= 16 ? 1 : (team <= 32 ? 2 : 3)));
 }
 
 __global__ void scatter_kernel(const double *stage, const UpDesc *d, int nd, Arena A) {
@@ -246,6 +255,12 @@ struct fd_server_s {
   OutDesc *h_outd = nullptr;
   size_t c_prob = 0, c_moff = 0, c_soff = 0, c_stage = 0, c_out = 0, c_up = 0, c_outd = 0;
   cudaStream_t stream = nullptr;
+  // side streams of a tick: one per CFA team class and one for ABIA; a request's
+  // launches (FD, the linear solve of its adjoint, the reverse sweep) stay on one
+  // of them, in order, and the classes run concurrently
+  static constexpr int kAux = 5;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
 
   RangeAlloc slots, recs, hist;
   std::unordered_map<int, Model> models;
@@ -290,7 +305,7 @@ fdk::KArgs base_args(fd_server_s *S) {
   a.sq_off = S->d_soff;
   a.order = nullptr;
   a.ws_t = S->A.ws_t;
-  a.ws_a = S->A.ws_a;
+  a.ws_a = S->A.ws_c;
   std::memcpy(a.grav, S->grav, sizeof a.grav);
   return a;
 }
@@ -425,7 +440,10 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
     e = cudaMemcpyAsync(S->d_soff, S->h_soff, np * sizeof(int64_t), cudaMemcpyHostToDevice,
                         S->stream);
 
-  // 3. forward dynamics of every active request
+  // 3. forward dynamics of every active request, on the side streams
+  if (e == cudaSuccess) e = cudaEventRecord(S->ev_fork, S->stream);
+  for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(S->aux[k], S->ev_fork, 0);
   auto fd_launch = [&](int algo, int mode, const double *in3, double *out, int p0, int cnt) {
     const TeamKind k = algo == FD_CFA ? kTeamCFA : kTeamABIA;
     return over(S, all, p0, cnt, k, [&](int s, int c, int t) {
@@ -440,8 +458,10 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       a.mode = mode;
       a.status = mode == fdk::MODE_FD ? S->d_status + s : nullptr;
       a.team = t;
-      if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, S->stream);
-      return fdk::launch_abia(a, 0, t, S->stream);
+      cudaStream_t st = S->aux[aux_of(algo != FD_CFA, t)];
+      a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
+      if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, st);
+      return fdk::launch_abia(a, 0, t, st);
     });
   };
   if (e == cudaSuccess)
@@ -453,7 +473,7 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
     e = fd_launch(FD_CFA, fdk::MODE_LINEAR, S->A.w, S->A.tbar, gstart[0], gstart[1] - gstart[0]);
   if (e == cudaSuccess)
     e = fd_launch(FD_ABIA, fdk::MODE_LINEAR, S->A.w, S->A.tbar, gstart[2], gstart[3] - gstart[2]);
-  auto reverse = [&](int p0, int cnt) {
+  auto reverse = [&](int p0, int cnt, bool abia) {
     return over(S, all, p0, cnt, kTeamReverse, [&](int s, int c, int t) {
       fdk::KArgs a = base_args(S);
       a.prob_chain = S->d_prob + s;
@@ -467,11 +487,16 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       a.out = S->A.qbar;
       a.out2 = S->A.qdbar;
       a.out3 = nullptr;
-      return fdk::launch_adjoint_rnea(a, 0, t, S->stream);
+      a.ws_t = S->A.ws_r;
+      return fdk::launch_adjoint_rnea(a, 0, t, S->aux[aux_of(abia, t)]);
     });
   };
-  if (e == cudaSuccess) e = reverse(gstart[0], gstart[1] - gstart[0]);
-  if (e == cudaSuccess) e = reverse(gstart[2], gstart[3] - gstart[2]);
+  if (e == cudaSuccess) e = reverse(gstart[0], gstart[1] - gstart[0], false);
+  if (e == cudaSuccess) e = reverse(gstart[2], gstart[3] - gstart[2], true);
+  for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(S->ev_join[k], S->aux[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->stream, S->ev_join[k], 0);
+  }
 
   // 4. which requests finish this tick; rollouts advance one step
   std::vector<Req *> done;
@@ -573,9 +598,20 @@ void worker_main(fd_server_s *S) {
 }
 
 size_t per_link_bytes() {
-  return 8 * sizeof(double) + fdk::NT_ADJ * sizeof(double) +
-         fdk::NA_CFA * sizeof(double) + sizeof(int64_t) + 2 * sizeof(int32_t) + sizeof(double) +
+  return 8 * sizeof(double) + (fdk::NT + fdk::NT_ADJ + fdk::NA_CFA + fdk::NA_ABIA) * sizeof(double) +
+         sizeof(int64_t) + 2 * sizeof(int32_t) + sizeof(double) +
          2 * sizeof(int32_t) + 3 * sizeof(int64_t);
+}
+
+// streams and events of a server (null handles are skipped)
+void destroy_streams(fd_server_s *S) {
+  for (int k = 0; k < fd_server_s::kAux; ++k) {
+    if (S->aux[k]) cudaStreamSynchronize(S->aux[k]);
+    if (S->aux[k]) cudaStreamDestroy(S->aux[k]);
+    if (S->ev_join[k]) cudaEventDestroy(S->ev_join[k]);
+  }
+  if (S->ev_fork) cudaEventDestroy(S->ev_fork);
+  if (S->stream) cudaStreamDestroy(S->stream);
 }
 
 }  // namespace
@@ -616,10 +652,16 @@ fd_status fd_serve_create(int32_t device, size_t mem_budget_bytes, const double 
   cudaSetDevice(device);
   cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&S->mem), mem_budget_bytes);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&S->aux[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming);
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (S->mem) cudaFree(S->mem);
+    destroy_streams(S);
     delete S;
     return sfail(e == cudaErrorMemoryAllocation ? FD_ERR_OOM : FD_ERR_CUDA,
                  "fd_serve_create: device allocation of the budget failed");
@@ -638,8 +680,10 @@ fd_status fd_serve_create(int32_t device, size_t mem_budget_bytes, const double 
   double **arrs[] = {&S->A.q, &S->A.qd, &S->A.tau, &S->A.qdd, &S->A.w, &S->A.qbar, &S->A.qdbar,
                      &S->A.tbar};
   for (double **a : arrs) *a = reinterpret_cast<double *>(take(size_t(C) * 8));
-  S->A.ws_t = reinterpret_cast<double *>(take(size_t(C) * fdk::NT_ADJ * 8));
-  S->A.ws_a = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_CFA * 8));
+  S->A.ws_t = reinterpret_cast<double *>(take(size_t(C) * fdk::NT * 8));
+  S->A.ws_r = reinterpret_cast<double *>(take(size_t(C) * fdk::NT_ADJ * 8));
+  S->A.ws_c = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_CFA * 8));
+  S->A.ws_b = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_ABIA * 8));
   S->A.r_hist = reinterpret_cast<int64_t *>(take(size_t(C) * 8));
   S->A.r_step = reinterpret_cast<int32_t *>(take(size_t(C) * 4));
   S->A.r_steps = reinterpret_cast<int32_t *>(take(size_t(C) * 4));
@@ -652,7 +696,7 @@ fd_status fd_serve_create(int32_t device, size_t mem_budget_bytes, const double 
   S->d_outd = reinterpret_cast<OutDesc *>(take(size_t(C) * sizeof(OutDesc)));
   if (p > S->mem + mem_budget_bytes) {
     cudaFree(S->mem);
-    cudaStreamDestroy(S->stream);
+    destroy_streams(S);
     delete S;
     return sfail(FD_ERR_INVALID_ARG, "fd_serve_create: budget too small for its tables");
   }
@@ -676,7 +720,7 @@ fd_status fd_serve_destroy(fd_server_t S) {
   cudaGetDevice(&prev);
   cudaSetDevice(S->device);
   cudaStreamSynchronize(S->stream);
-  cudaStreamDestroy(S->stream);
+  destroy_streams(S);
   cudaFree(S->mem);
   cudaFreeHost(S->h_prob);
   cudaFreeHost(S->h_moff);
