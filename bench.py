@@ -123,6 +123,13 @@ def traffic_record(kernel: str, team: int):
     return ent
 
 
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return None
+
+
 def csrc_sha() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1609_06779_gb300", "csrc")
@@ -152,9 +159,39 @@ def cpu_oracle(model, st, n_problems, budget_s=10.0, threads=None):
         el = time.perf_counter() - t0
         if el > budget_s:
             break
+    # the same sample on one core, for a shorter budget
+    t1 = time.perf_counter()
+    one = 0
+    while True:
+        for a in ALGOS:
+            oracle.fd(sub, q, qd, tau, algo=algos[a], n_threads=1)
+            one += sample
+        el1 = time.perf_counter() - t1
+        if el1 > budget_s / 3:
+            break
     return {"value": solved / el, "unit": "FD solves/s", "cores": threads, "kind": "oracle",
+            "value_1core": one / el1,
             "sample": f"first {sample} of {n_problems} chains x {{ABA, Cholesky (JSIIA), CFA+OEE}},"
-                      f" {solved} solves in {el:.1f} s, FP64, OpenMP across chains"}
+                      f" {solved} solves in {el:.1f} s on {threads} cores (OpenMP across chains),"
+                      f" {one} in {el1:.1f} s on one core, FP64"}
+
+
+def accuracy(model, st, outs, sample=1024):
+    """Largest error per chain, max |qdd - ref| / max(max |ref|, 1), of each output
+    against the FP64 oracle (dense Cholesky) on the first `sample` chains."""
+    import oracle
+    n = int(model.offsets[1] - model.offsets[0])
+    sample = min(sample, model.n_chains)
+    L = sample * n
+    sub = synth.ChainModel(model.axes[:L], model.frames[:L], model.inertias[:L],
+                           model.offsets[:sample + 1].copy(), model.gravity)
+    ref = oracle.fd(sub, st.q[:L], st.qdot[:L], st.tau[:L], algo="cholesky").reshape(sample, n)
+    scale = np.maximum(np.abs(ref).max(axis=1), 1.0)
+    res = {"sample_chains": sample, "reference": "FP64 CPU oracle, dense Cholesky"}
+    for k, v in outs.items():
+        got = v[:L].double().cpu().numpy().reshape(sample, n)
+        res[k] = float((np.abs(got - ref).max(axis=1) / scale).max())
+    return res
 
 
 def serve_bench(seconds=10.0, rate=20000.0, per_size=False, budget=40 << 30, seed=0,
@@ -233,6 +270,13 @@ def serve_bench(seconds=10.0, rate=20000.0, per_size=False, budget=40 << 30, see
     return out
 
 
+def occupancy(n_problems: int, team: int) -> dict:
+    """Warps a launch runs and how many fall on each of the 608 SM sub-partitions
+    (152 SMs x 4): below one, the batch is latency-bound, not throughput-bound."""
+    warps = -(-n_problems * team // 32)
+    return {"warps": warps, "warps_per_subpartition": warps / 608.0}
+
+
 def _time_ms(fn, reps=3, warm=1):
     import torch
     for _ in range(warm):
@@ -246,11 +290,14 @@ def _time_ms(fn, reps=3, warm=1):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_configs(dev):
+def extra_configs(dev, keep=None):
     """The paper-shaped workloads besides the headline batch: one 7-link chain
     with 1024 states (launch-bound; CUDA-graph replay), long chains (256 x 256,
     64 x 1024) and an uneven batch of 100 000 chains (6..512 links, mixed
-    precision) as one launch against one launch per distinct length."""
+    precision) as one launch against one launch per distinct length. Appends to
+    `keep` a sample of each configuration's results for the accuracy check of
+    the CPU leg."""
+    keep = [] if keep is None else keep
     import torch
     from paper_1609_06779_gb300 import fd
     t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
@@ -258,12 +305,14 @@ def extra_configs(dev):
 
     # 1 chain x 7 links, 1024 states (shared model), FP64
     m = synth.random_chains([7], seed=0)
-    ci, _ = synth.replicate_model(m, 1024)
+    ci, so1 = synth.replicate_model(m, 1024)
     st = synth.random_states(7 * 1024, seed=1)
     cs = fd.ChainSet(m, device=dev.index or 0)
     b = fd.Batch(cs, ci)
     q, qd, tau = t64(st.q), t64(st.qdot), t64(st.tau)
     r1 = {}
+    k1 = {"config": "1x7_links_1024_states_fp64", "model": m, "chain_index": ci,
+          "state_offsets": so1, "st": st, "problems": None, "outs": {}}
     for a in ALGOS + ("cfa_cr",):
         team = fd.autotune(b, q, qd, tau, algo=a)
         ws = fd.workspace(b, a, "fp64", 0, dev)
@@ -278,9 +327,11 @@ def extra_configs(dev):
         with torch.cuda.graph(g):
             fd.solve(b, q, qd, tau, algo=a, out=out, ws=ws)
         graph_us = 1e3 * _time_ms(g.replay, 50, 5)
+        k1["outs"][a] = out.cpu().numpy()
         r1[a] = {"team": team, "launch_us": launch_us, "graph_replay_us": graph_us,
-                 "solves_per_s": 1024 / (graph_us * 1e-6)}
+                 "solves_per_s": 1024 / (graph_us * 1e-6), "occupancy": occupancy(1024, team)}
     res["1x7_links_1024_states_fp64"] = r1
+    keep.append(k1)
     del cs, b
 
     # long chains, FP64
@@ -291,6 +342,8 @@ def extra_configs(dev):
         b = fd.Batch(cs)
         q, qd, tau = t64(st.q), t64(st.qdot), t64(st.tau)
         rl = {}
+        kl = {"config": f"{count}x{n}_links_fp64", "model": m, "chain_index": None, "st": st,
+              "problems": [0, 1] if n <= 256 else [0], "outs": {}}
         for a in ALGOS + ("cfa_cr",):
             if a == "jsiia" and n > 256:
                 continue  # cubic in n: about 0.3 s per solve of this batch
@@ -298,11 +351,14 @@ def extra_configs(dev):
             ws = fd.workspace(b, a, "fp64", team, dev)
             out = torch.empty_like(q)
             ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, team=team, out=out, ws=ws))
+            kl["outs"][a] = out.cpu().numpy()
             fl = roofline.flops(a, [n] * count)
             rl[a] = {"team": team, "ms": ms, "solves_per_s": count / (ms * 1e-3),
+                     "occupancy": occupancy(count, team),
                      "tflops": fl / (ms * 1e-3) / 1e12,
                      "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
         res[f"{count}x{n}_links_fp64"] = rl
+        keep.append(kl)
         del cs, b, q, qd, tau
         torch.cuda.empty_cache()
 
@@ -315,11 +371,15 @@ def extra_configs(dev):
     t32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
     q, qd, tau = t32(st.q), t32(st.qdot), t32(st.tau)
     ru = {"chains": 100000, "links": int(m.n_links_total), "prec": "mixed"}
+    ku = {"config": "100000_uneven_6_512_mixed", "model": m, "chain_index": None, "st": st,
+          "problems": np.random.default_rng(5).choice(100000, 64, replace=False).tolist(),
+          "outs": {}}
     for a in ("abia", "cfa"):
         team = fd.autotune(b, q, qd, tau, algo=a, prec="mixed")
         ws = fd.workspace(b, a, "mixed", 0, dev)
         out = torch.empty_like(q)
         one_ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, prec="mixed", out=out, ws=ws))
+        ku["outs"][a + "_mixed"] = out.double().cpu().numpy()
         del ws
         # one launch per distinct chain length (static batching per size)
         groups = []
@@ -350,7 +410,42 @@ def extra_configs(dev):
     ru["adjoint_cfa_ms"] = adj_ms
     ru["adjoint_solves_per_s"] = 100000 / (adj_ms * 1e-3)
     res["100000_uneven_6_512_mixed"] = ru
+    keep.append(ku)
     return res
+
+
+def config_accuracy(keep):
+    """Per configuration and path: the largest error per problem,
+    max |qdd - ref| / max(max |ref|, 1), on the sampled problems against the FP64
+    oracle's dense Cholesky, beside the oracle's own ABA on the same problems (the
+    FP64 floor those chains allow)."""
+    import oracle
+    out = {}
+    for k in keep:
+        m, st = k["model"], k["st"]
+        ci = k["chain_index"]
+        probs = k["problems"]
+        n_prob = len(ci) if ci is not None else m.n_chains
+        probs = list(range(n_prob)) if probs is None else probs
+        kw = dict(chain_index=ci, state_offsets=k.get("state_offsets"),
+                  n_threads=os.cpu_count() or 1)
+        if k["problems"] is not None:
+            kw["problems"] = probs
+        ref = oracle.fd(m, st.q, st.qdot, st.tau, algo="cholesky", **kw)
+        aba = oracle.fd(m, st.q, st.qdot, st.tau, algo="aba", **kw)
+        offs = m.offsets if ci is None else np.asarray(k["state_offsets"])
+
+        def err(x):
+            e = 0.0
+            for p in probs:
+                a, b = int(offs[p]), int(offs[p + 1])
+                e = max(e, float(np.abs(x[a:b] - ref[a:b]).max() / max(np.abs(ref[a:b]).max(), 1.0)))
+            return e
+        r = {"sampled_problems": len(probs), "oracle_aba_floor": err(aba)}
+        for name, x in k["outs"].items():
+            r[name] = err(x)
+        out[k["config"]] = r
+    return out
 
 
 def reference_arm(args):
@@ -469,12 +564,22 @@ def main():
     if tr is not None:
         # DRAM bytes of one launch: the capture's bytes per link x this launch's links
         traffic = tr["bytes_per_link"] * args.chains * args.links
+    hbm_peak = measured_hbm_gbs()
+    alg_bytes = roofline.bytes_per_link("fp64") * args.chains * args.links
+    hbm_gbs = alg_bytes / (per_algo_ms[dom] / 1e3) / 1e9
     roof = {"bound": "alu", "achieved": rl[dom]["tflops"], "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": rl[dom]["frac"], "traffic": traffic,
             "kernel": f"{dom}_kernel<double,double,{teams[dom]}>",
             "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s), not measured",
             "algorithmic_flops_per_launch": roofline.flops(dom, lengths),
-            "algorithmic_bytes_per_launch": roofline.bytes_per_link("fp64") * args.chains * args.links}
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak,
+                    "frac": (hbm_gbs / hbm_peak) if hbm_peak else None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"}}
+
+    # the first chains' results of every path, for the accuracy check of the CPU leg
+    n_acc = min(args.chains, 1024) * args.links
+    acc_outs = {f"{a}_fp64": out[a][:n_acc].cpu() for a in ALGOS}
 
     # CFA with block cyclic reduction in place of OEE (context; not part of the step)
     variants = {}
@@ -485,6 +590,7 @@ def main():
         ms = _time_ms(lambda: fd.solve(batch, q, qd, tau, algo="cfa_cr", team=tcr, out=ocr,
                                        ws=wcr), reps=5, warm=2)
         fl = roofline.flops("cfa_cr", lengths)
+        acc_outs["cfa_cr_fp64"] = ocr[:n_acc].cpu()
         variants["cfa_cr_fp64"] = {"team": tcr, "ms": ms, "solves_per_s": args.chains / (ms * 1e-3),
                                    "tflops": fl / (ms * 1e-3) / 1e12,
                                    "frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -511,6 +617,7 @@ def main():
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / 3
                 variants[f"{a}_{prec}"] = {"ms": ms, "solves_per_s": args.chains / (ms / 1e3)}
+                acc_outs[f"{a}_{prec}"] = o[:n_acc].cpu()
                 del w
 
     # end to end through the C ABI with host buffers (pinned), copies timed
@@ -550,8 +657,9 @@ def main():
     del ws, out
     torch.cuda.empty_cache()
     extra = None
+    keep = []
     if rank == 0 and not args.no_extra:
-        extra = extra_configs(dev)
+        extra = extra_configs(dev, keep)
         torch.cuda.empty_cache()
     serving = None
     if rank == 0 and not args.no_serve:
@@ -560,9 +668,12 @@ def main():
                    "per_size_baseline": serve_bench(args.serve_seconds, args.serve_rate, True,
                                                     device=local)}
 
-    cpu = None
+    cpu = acc = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle(model, st, args.chains)
+        acc = accuracy(model, st, acc_outs)
+        if keep:
+            acc["configs"] = config_accuracy(keep)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "FD solves/s", "n_gpus": world,
@@ -575,7 +686,8 @@ def main():
                            "l2": "inputs larger than L2 (FP64 model arena 940 MB), no flush",
                            "parallelism": f"replicas x{world}, chains partitioned, no exchange"},
                 "per_algo": rl, "variants": variants,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
+                "roofline": roof, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e,
+                "serving": serving,
                 "configs": extra,
                 "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

@@ -62,6 +62,38 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
     srv.close()
 
 
+def test_every_team_class_alone_and_in_the_mix():
+    """Chains of 6..256 links fall into every team class of the server (and onto
+    every side stream); each result is bitwise the same alone and in the mix."""
+    from paper_1609_06779_gb300 import fd
+    rng = np.random.default_rng(3)
+    lengths = [6, 20, 40, 60, 100, 128, 160, 256]
+    models = [synth.random_chains([n], seed=300 + k) for k, n in enumerate(lengths)]
+    reqs = []
+    for r in range(24):
+        k = r % len(lengths)
+        n = lengths[k]
+        st = synth.random_states(n, seed=3000 + r)
+        algo = ("cfa", "abia")[(r // len(lengths)) % 2]
+        if r % 3 == 2:
+            reqs.append(dict(kind="rollout", model=k, q=st.q, qd=st.qdot,
+                             taus=rng.standard_normal((3, n)) * 10, dt=1e-3, algo=algo))
+        else:
+            reqs.append(dict(kind="grad", model=k, q=st.q, qd=st.qdot, tau=st.tau,
+                             w=rng.standard_normal(n), algo=algo))
+    srv = fd.Server(budget_bytes=256 << 20)
+    ids = [srv.add_model(m) for m in models]
+    mixed = _run(srv, ids, reqs)
+    for r, res in zip(reqs, mixed):
+        alone = _run(srv, ids, [r])[0]
+        assert res["status"] == 0 and alone["status"] == 0
+        keys = ("q", "qdot", "qddot") if r["kind"] == "rollout" else (
+            "qddot", "q_bar", "qdot_bar", "tau_bar")
+        for k in keys:
+            assert np.array_equal(res[k], alone[k]), (r["kind"], lengths[r["model"]], k)
+    srv.close()
+
+
 def test_served_results_agree_with_the_batch_api_and_oracle():
     from paper_1609_06779_gb300 import fd
     rng = np.random.default_rng(1)
