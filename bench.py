@@ -185,12 +185,19 @@ def accuracy(model, st, outs, sample=1024):
     L = sample * n
     sub = synth.ChainModel(model.axes[:L], model.frames[:L], model.inertias[:L],
                            model.offsets[:sample + 1].copy(), model.gravity)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
     ref = oracle.fd(sub, st.q[:L], st.qdot[:L], st.tau[:L], algo="cholesky").reshape(sample, n)
-    scale = np.maximum(np.abs(ref).max(axis=1), 1.0)
-    res = {"sample_chains": sample, "reference": "FP64 CPU oracle, dense Cholesky"}
+    ref32 = oracle.fd(sub, f32(st.q[:L]), f32(st.qdot[:L]), f32(st.tau[:L]),
+                      algo="cholesky").reshape(sample, n)
+    res = {"sample_chains": sample, "reference": "FP64 CPU oracle, dense Cholesky",
+           "float_paths_also_vs_states_rounded_to_fp32": {}}
     for k, v in outs.items():
         got = v[:L].double().cpu().numpy().reshape(sample, n)
-        res[k] = float((np.abs(got - ref).max(axis=1) / scale).max())
+        for r, dst in ((ref, res), (ref32, res["float_paths_also_vs_states_rounded_to_fp32"])):
+            if dst is not res and k.endswith("fp64"):
+                continue
+            scale = np.maximum(np.abs(r).max(axis=1), 1.0)
+            dst[k] = float((np.abs(got - r).max(axis=1) / scale).max())
     return res
 
 
@@ -433,17 +440,23 @@ def config_accuracy(keep):
             kw["problems"] = probs
         ref = oracle.fd(m, st.q, st.qdot, st.tau, algo="cholesky", **kw)
         aba = oracle.fd(m, st.q, st.qdot, st.tau, algo="aba", **kw)
+        f32 = lambda a: a.astype(np.float32).astype(np.float64)
+        ref32 = None
+        if any(not name.endswith(("fp64",)) and "mixed" in name for name in k["outs"]):
+            ref32 = oracle.fd(m, f32(st.q), f32(st.qdot), f32(st.tau), algo="cholesky", **kw)
         offs = m.offsets if ci is None else np.asarray(k["state_offsets"])
 
-        def err(x):
+        def err(x, rf=ref):
             e = 0.0
             for p in probs:
                 a, b = int(offs[p]), int(offs[p + 1])
-                e = max(e, float(np.abs(x[a:b] - ref[a:b]).max() / max(np.abs(ref[a:b]).max(), 1.0)))
+                e = max(e, float(np.abs(x[a:b] - rf[a:b]).max() / max(np.abs(rf[a:b]).max(), 1.0)))
             return e
         r = {"sampled_problems": len(probs), "oracle_aba_floor": err(aba)}
         for name, x in k["outs"].items():
             r[name] = err(x)
+            if ref32 is not None and "mixed" in name:
+                r[name + "_vs_states_rounded_to_fp32"] = err(x, ref32)
         out[k["config"]] = r
     return out
 
