@@ -324,27 +324,78 @@ __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, con
 #pragma unroll
     for (int c = 0; c <= r; ++c) acc[l5(r, c)] = TA(Kself[s6(r + 1, c + 1)]);
   if (g) {
-    // M1 = X K: X applied to each column of K
-    T M1[6][6];
+    // X K X^T with X = Ad_{g^{-1}} = [[R^T, 0], [-R^T p^, R^T]] and K = [[A, B],
+    // [B^T, C]] in 3x3 blocks: with Bt = B + A p^ (rows: a_r x p) and
+    // Cs = C - p^ B + Bt^T p^ ((Cs)_rc = C_rc - (p x b_c)_r + (bt_r x p)_c for the
+    // columns b_c of B and bt_r of Bt),
+    //   X K X^T = [[R^T A R, R^T Bt R], [R^T Bt^T R, R^T Cs R]];
+    // only rows and columns 1..5 are needed (W^T x = x[1..5]).
+    const T *R = g->R, *p = g->p;
+    T A[3][3], B[3][3], C[3][3];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      T col[6], o[6];
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int k = 0; k < 6; ++k) col[k] = Kprev[s6(k, j)];
-      adinv(*g, col, o);
+      for (int c = 0; c < 3; ++c) {
+        A[r][c] = Kprev[s6(r, c)];
+        B[r][c] = Kprev[s6(r, 3 + c)];
+        C[r][c] = Kprev[s6(3 + r, 3 + c)];
+      }
+    T Bt[3][3], Cs[3][3];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) M1[k][j] = o[k];
+    for (int r = 0; r < 3; ++r) {
+      Bt[r][0] = (B[r][0] + A[r][1] * p[2]) - A[r][2] * p[1];
+      Bt[r][1] = (B[r][1] + A[r][2] * p[0]) - A[r][0] * p[2];
+      Bt[r][2] = (B[r][2] + A[r][0] * p[1]) - A[r][1] * p[0];
     }
-    // (X K X^T) column c = X (row c of M1)
 #pragma unroll
-    for (int c = 1; c < 6; ++c) {
-      T row[6], o[6];
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int k = 0; k < 6; ++k) row[k] = M1[c][k];
-      adinv(*g, row, o);
+      for (int c = 0; c <= r; ++c) {
+        const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        T t = C[r][c];
+        t -= p[r1] * B[r2][c] - p[r2] * B[r1][c];   // (p x b_c)_r
+        t += Bt[c1][r] * p[c2] - Bt[c2][r] * p[c1];  // (bt_r x p)_c
+        Cs[r][c] = t;
+        Cs[c][r] = t;
+      }
+    // top-left rows / columns 1..2: (R^T A R)_ab = R_{:,a} . (A R_{:,b})
+    T AR[3][2];
 #pragma unroll
-      for (int r = c; r < 6; ++r) acc[l5(r - 1, c - 1)] += TA(o[r]);
-    }
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+        AR[k][b] = A[k][0] * R[1 + b] + A[k][1] * R[4 + b] + A[k][2] * R[7 + b];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b)
+        acc[l5(a, b)] += TA(R[1 + a] * AR[0][b] + R[4 + a] * AR[1][b] + R[7 + a] * AR[2][b]);
+    // off-diagonal rows 1..2 of R^T Bt R, as rows 3..5 x columns 1..2 of D
+    T RB[2][3];  // (R^T Bt)_{a,:} for a = 1, 2
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        RB[a][c] = R[1 + a] * Bt[0][c] + R[4 + a] * Bt[1][c] + R[7 + a] * Bt[2][c];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        acc[l5(2 + b, a)] +=
+            TA(RB[a][0] * R[b] + RB[a][1] * R[3 + b] + RB[a][2] * R[6 + b]);
+    // bottom-right R^T Cs R
+    T RC[3][3];  // R^T Cs
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        RC[a][c] = R[a] * Cs[0][c] + R[3 + a] * Cs[1][c] + R[6 + a] * Cs[2][c];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b)
+        acc[l5(2 + a, 2 + b)] +=
+            TA(RC[a][0] * R[b] + RC[a][1] * R[3 + b] + RC[a][2] * R[6 + b]);
   }
 #pragma unroll
   for (int k = 0; k < 15; ++k) D[k] = acc[k];

@@ -66,10 +66,17 @@ def oee_flops(n: int) -> int:
     return f + n * (CHOL5 + 2 * TRI5)
 
 
+# D_i = (X K X^T)[1..5][1..5] + K_self in rotated 3x3 blocks: Bt = B + A p^ 36,
+# Cs = C - p^ B + Bt^T p^ 48, R^T A R rows 1..2 63, rows 1..2 of R^T Bt R 66,
+# R^T Cs R 99, and the 15 additions into K_self
+D_BLOCKS = 36 + 48 + 63 + 66 + 99 + 15
+
+
 def cfa_flops(n: int) -> int:
-    """ID + A blocks (D 477; U 357: five columns of J^{-1} Ad^T restricted to
-    unit vectors, 27 + 5 x 66) + R = -B tau (120) + OEE + CalcAcc (120)."""
-    return id_flops(n) + n * (477 + 357 + 120) + oee_flops(n) + n * 120
+    """ID + A blocks (D in rotated blocks 327; U 357: five columns of J^{-1} Ad^T
+    restricted to unit vectors, 27 + 5 x 66) + R = -B tau (120) + OEE + CalcAcc
+    (120)."""
+    return id_flops(n) + n * (D_BLOCKS + 357 + 120) + oee_flops(n) + n * 120
 
 
 def cr_flops(n: int) -> int:
@@ -95,7 +102,7 @@ def cr_flops(n: int) -> int:
 
 
 def cfa_cr_flops(n: int) -> int:
-    return id_flops(n) + n * (477 + 357 + 120) + cr_flops(n) + n * 120
+    return id_flops(n) + n * (D_BLOCKS + 357 + 120) + cr_flops(n) + n * 120
 
 
 FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops,
