@@ -67,13 +67,14 @@ def oee_flops(n: int) -> int:
 
 
 # D_i = (X K X^T)[1..5][1..5] + K_self in rotated 3x3 blocks: Bt = B + A p^ 36,
-# Cs = C - p^ B + Bt^T p^ 48, R^T A R rows 1..2 63, rows 1..2 of R^T Bt R 66,
-# R^T Cs R 99, and the 15 additions into K_self
-D_BLOCKS = 36 + 48 + 63 + 66 + 99 + 15
+# Cs = C - p^ B + Bt^T p^ 48, A R_{:,1..2} 30 + its 3 entries 18, rows 1..2 of
+# R^T Bt 30 + its 6 entries 36, R^T Cs 45 + its 6 entries 36 (each entry with its
+# addition into K_self)
+D_BLOCKS = 36 + 48 + 48 + 66 + 81
 
 
 def cfa_flops(n: int) -> int:
-    """ID + A blocks (D in rotated blocks 327; U 357: five columns of J^{-1} Ad^T
+    """ID + A blocks (D in rotated blocks 279; U 357: five columns of J^{-1} Ad^T
     restricted to unit vectors, 27 + 5 x 66) + R = -B tau (120) + OEE + CalcAcc
     (120)."""
     return id_flops(n) + n * (D_BLOCKS + 357 + 120) + oee_flops(n) + n * 120
