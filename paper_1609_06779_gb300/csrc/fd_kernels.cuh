@@ -401,18 +401,30 @@ __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, con
   for (int k = 0; k < 15; ++k) D[k] = acc[k];
 }
 
-// U_i = W_i^T T_{i,i+1} W_{i+1} = -(J_i^{-1} Ad_{g_{i+1}^{-1}}^T)[1..5][1..5]
+// U_i = W_i^T T_{i,i+1} W_{i+1} = -(J_i^{-1} Ad_{g_{i+1}^{-1}}^T)[1..5][1..5].
+// Column j of Ad_{g^{-1}}^T = [[R, p^ R], [0, R]] is (R_{:,j}; 0) for j < 3 and
+// (p x R_{:,j-3}; R_{:,j-3}) for j >= 3; rows 1..5 of J^{-1} times it.
 template <class T, class TA, class Out>
 __device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, Out U) {
+  const T *R = gn.R, *p = gn.p;
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    T e[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    e[c + 1] = T(1);
-    T col[6], o[6];
-    adinvT(gn, e, col);
-    sym6_apply(Ki, col, o);
+    const int j = c + 1;
+    if (j < 3) {
 #pragma unroll
-    for (int r = 0; r < 5; ++r) U[5 * r + c] = TA(-o[r + 1]);
+      for (int r = 0; r < 5; ++r)
+        U[5 * r + c] = TA(-(Ki[s6(r + 1, 0)] * R[j] + Ki[s6(r + 1, 1)] * R[3 + j] +
+                            Ki[s6(r + 1, 2)] * R[6 + j]));
+    } else {
+      const int m = j - 3;
+      const T x0 = R[m], x1 = R[3 + m], x2 = R[6 + m];
+      const T w0 = p[1] * x2 - p[2] * x1, w1 = p[2] * x0 - p[0] * x2, w2 = p[0] * x1 - p[1] * x0;
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+        U[5 * r + c] = TA(-(Ki[s6(r + 1, 0)] * w0 + Ki[s6(r + 1, 1)] * w1 +
+                            Ki[s6(r + 1, 2)] * w2 + Ki[s6(r + 1, 3)] * x0 +
+                            Ki[s6(r + 1, 4)] * x1 + Ki[s6(r + 1, 5)] * x2));
+    }
   }
 }
 

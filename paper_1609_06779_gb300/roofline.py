@@ -71,13 +71,15 @@ def oee_flops(n: int) -> int:
 # R^T Bt 30 + its 6 entries 36, R^T Cs 45 + its 6 entries 36 (each entry with its
 # addition into K_self)
 D_BLOCKS = 36 + 48 + 48 + 66 + 81
+# U_i: columns 1, 2 of Ad^T have three nonzeros (5 rows x 5 flops), columns 3..5
+# six after one cross product (9 + 5 rows x 11 flops)
+U_BLOCK = 2 * 25 + 3 * (9 + 55)
 
 
 def cfa_flops(n: int) -> int:
-    """ID + A blocks (D in rotated blocks 279; U 357: five columns of J^{-1} Ad^T
-    restricted to unit vectors, 27 + 5 x 66) + R = -B tau (120) + OEE + CalcAcc
-    (120)."""
-    return id_flops(n) + n * (D_BLOCKS + 357 + 120) + oee_flops(n) + n * 120
+    """ID + A blocks (D in rotated blocks 279; U 242: rows 1..5 of J^{-1} times
+    the sparse columns of Ad^T) + R = -B tau (120) + OEE + CalcAcc (120)."""
+    return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 120) + oee_flops(n) + n * 120
 
 
 def cr_flops(n: int) -> int:
@@ -103,7 +105,7 @@ def cr_flops(n: int) -> int:
 
 
 def cfa_cr_flops(n: int) -> int:
-    return id_flops(n) + n * (D_BLOCKS + 357 + 120) + cr_flops(n) + n * 120
+    return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 120) + cr_flops(n) + n * 120
 
 
 FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops,
