@@ -675,8 +675,12 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
 #pragma unroll
       for (int k = 0; k < 25; ++k) row[A_U0 + k] = TA(0);
     }
+    // z = J^{-1} y with y = (y_0, y_1, y_2, 0, 0, 0): columns 0..2 only
+    const T *Ki = rec + REC_JI;
     T z[6];
-    sym6_apply(rec + REC_JI, yv, z);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      z[k] = Ki[s6(k, 0)] * yv[0] + Ki[s6(k, 1)] * yv[1] + Ki[s6(k, 2)] * yv[2];
     stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
   }
   tm.sync();

@@ -78,8 +78,9 @@ U_BLOCK = 2 * 25 + 3 * (9 + 55)
 
 def cfa_flops(n: int) -> int:
     """ID + A blocks (D in rotated blocks 279; U 242: rows 1..5 of J^{-1} times
-    the sparse columns of Ad^T) + R = -B tau (120) + OEE + CalcAcc (120)."""
-    return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 120) + oee_flops(n) + n * 120
+    the sparse columns of Ad^T) + R = -B tau (J^{-1} on three nonzero components
+    30 + 6, one transport 42) + OEE + CalcAcc (120)."""
+    return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 78) + oee_flops(n) + n * 120
 
 
 def cr_flops(n: int) -> int:
@@ -105,7 +106,7 @@ def cr_flops(n: int) -> int:
 
 
 def cfa_cr_flops(n: int) -> int:
-    return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 120) + cr_flops(n) + n * 120
+    return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 78) + cr_flops(n) + n * 120
 
 
 FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops,
