@@ -466,7 +466,7 @@ struct WsPlan {
   size_t t_bytes, a_bytes;
 };
 
-WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int team) {
+WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int /*team: no layout depends on it*/) {
   const size_t ts = prec == FD_FP64 ? 8 : 4;
   const size_t as = prec == FD_FP32 ? 4 : 8;
   const size_t L = static_cast<size_t>(b->n_state_links);
