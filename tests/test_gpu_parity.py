@@ -157,6 +157,37 @@ def test_repeat_is_bitwise_deterministic():
         assert np.array_equal(a, b), algo
 
 
+def test_cuda_graph_replay_matches_eager():
+    """fd_solve_batch enqueues only kernels on the caller's stream (no allocation,
+    no synchronisation), so it can be captured in a CUDA graph; replays with new
+    inputs copied into the captured buffers give the eager results bitwise."""
+    fd = _fd()
+    model = synth.random_chains([7] * 64 + [33, 100], seed=81)
+    cs = fd.ChainSet(model)
+    b = fd.Batch(cs)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    st0 = synth.random_states(model.n_links_total, seed=82)
+    q, qd, tau = t(st0.q), t(st0.qdot), t(st0.tau)
+    for algo, team in (("abia", 8), ("jsiia", 8), ("cfa", 8), ("cfa_cr", 4)):
+        ws = fd.workspace(b, algo, "fp64", team, q.device)
+        out = torch.empty_like(q)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fd.solve(b, q, qd, tau, algo=algo, team=team, out=out, ws=ws)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fd.solve(b, q, qd, tau, algo=algo, team=team, out=out, ws=ws)
+        for seed in (83, 84):
+            st = synth.random_states(model.n_links_total, seed=seed)
+            q.copy_(t(st.q)); qd.copy_(t(st.qdot)); tau.copy_(t(st.tau))
+            g.replay()
+            torch.cuda.synchronize()
+            eager = fd.solve(b, q, qd, tau, algo=algo, team=team, ws=ws)
+            assert torch.equal(out, eager), (algo, seed)
+
+
 def test_bad_arguments_raise():
     fd = _fd()
     model = synth.random_chains([4, 4], seed=0)
