@@ -1211,80 +1211,183 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
   id_team<T, P>(tm, pb, A.grav, A.mode);
   tm.sync();
 
-  // operands of step i: tau_delta_i, g_i, row r of J_{i-1}
-  TA nt_td = TA(0), nt_J[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
-  SE3<T> nt_g;
-  se3_identity(nt_g);
-  auto fetch = [&](int i) {
-    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    nt_td = TA(w[W_TD]);
-    if (i > 0) {
-      ld_se3(w + W_G, nt_g);
-      const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) nt_J[c] = TA(J[s6(r, c)]);
+  if constexpr (P < 16) {
+    // operands of step i: tau_delta_i, g_i, row r of J_{i-1}
+    TA nt_td = TA(0), nt_J[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    SE3<T> nt_g;
+    se3_identity(nt_g);
+    auto fetch = [&](int i) {
+      const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+      nt_td = TA(w[W_TD]);
+      if (i > 0) {
+        ld_se3(w + W_G, nt_g);
+        const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
+  #pragma unroll
+        for (int c = 0; c < 6; ++c) nt_J[c] = TA(J[s6(r, c)]);
+      }
+    };
+    TA prow[6], pbr = TA(0);  // row r of P_i; component r of the bias force p_i
+    if (n > 0) {
+      const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) prow[c] = TA(J[s6(r, c)]);
+      fetch(n - 1);
     }
-  };
-  TA prow[6], pbr = TA(0);  // row r of P_i; component r of the bias force p_i
-  if (n > 0) {
-    const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) prow[c] = TA(J[s6(r, c)]);
-    fetch(n - 1);
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    const TA td = nt_td;
-    SE3<TA> ga;
-    TA Jr[6];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) ga.R[c] = TA(nt_g.R[c]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ga.p[c] = TA(nt_g.p[c]);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) Jr[c] = nt_J[c];
-    if (i > 0) fetch(i - 1);
-    TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
-    TA h[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) h[c] = __shfl_sync(tm.mask, prow[c], 0, P);
-    const TA p0 = __shfl_sync(tm.mask, pbr, 0, P);
-    const TA D = h[0];
-    bad |= !(D > TA(0));
-    const TA Dinv = TA(1) / D;
-    const TA uD = (td - p0) * Dinv;  // u_i / D_i
-    if (tm.r < 6) ra[A_H + tm.r] = prow[0];
-    if (tm.r == 0) {
-      ra[A_DD] = Dinv;
-      ra[A_UU] = uD;
+    for (int i = n - 1; i >= 0; --i) {
+      const TA td = nt_td;
+      SE3<TA> ga;
+      TA Jr[6];
+  #pragma unroll
+      for (int c = 0; c < 9; ++c) ga.R[c] = TA(nt_g.R[c]);
+  #pragma unroll
+      for (int c = 0; c < 3; ++c) ga.p[c] = TA(nt_g.p[c]);
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) Jr[c] = nt_J[c];
+      if (i > 0) fetch(i - 1);
+      TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
+      TA h[6];
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) h[c] = __shfl_sync(tm.mask, prow[c], 0, P);
+      const TA p0 = __shfl_sync(tm.mask, pbr, 0, P);
+      const TA D = h[0];
+      bad |= !(D > TA(0));
+      const TA Dinv = TA(1) / D;
+      const TA uD = (td - p0) * Dinv;  // u_i / D_i
+      if (tm.r < 6) ra[A_H + tm.r] = prow[0];
+      if (tm.r == 0) {
+        ra[A_DD] = Dinv;
+        ra[A_UU] = uD;
+      }
+      if (i == 0) break;
+      // row r of Pa = P - h h^T / D; component r of pa = p + h u / D
+      const TA tr = prow[0] * Dinv;
+      TA par[6];
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) par[c] = prow[c] - tr * h[c];
+      const TA par_b = pbr + prow[0] * uD;
+      TA ncol[6], nrow[6], orow[6];
+      adinvT(ga, par, ncol);  // column r of N = X^T Pa
+      TA *x = xb[i & 1];
+      if (tm.r < 6) {
+  #pragma unroll
+        for (int c = 0; c < 6; ++c) x[c * 6 + r] = ncol[c];
+      }
+      // bias p_{i-1} = X^T pa, component r (the other lanes' components by shuffle)
+      TA pa[6];
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) pa[c] = __shfl_sync(tm.mask, par_b, c, P);
+      const TA tb = top ? ga.R[3 * k] * pa[0] + ga.R[3 * k + 1] * pa[1] + ga.R[3 * k + 2] * pa[2]
+                        : ga.R[3 * k] * pa[3] + ga.R[3 * k + 1] * pa[4] + ga.R[3 * k + 2] * pa[5];
+      const TA fa = __shfl_sync(tm.mask, tb, 3 + ka, P), fb = __shfl_sync(tm.mask, tb, 3 + kb, P);
+      pbr = top ? (tb + ga.p[ka] * fb) - ga.p[kb] * fa : tb;
+      tm.sync();
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) nrow[c] = x[r * 6 + c];
+      adinvT(ga, nrow, orow);  // row r of N X = X^T Pa X
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) prow[c] = Jr[c] + orow[c];
     }
-    if (i == 0) break;
-    // row r of Pa = P - h h^T / D; component r of pa = p + h u / D
-    const TA tr = prow[0] * Dinv;
-    TA par[6];
+  } else {
+    // Twelve lanes carry P in half columns: lane L < 12 holds rows 3h..3h+2 of
+    // column c = L / 2 (h = L % 2), so each transport X^T v splits between a lane
+    // pair (the bottom half R f; the top half R n + p x R f with R f from the
+    // partner): about 15 FP64 operations per lane instead of 24. Lanes 12 and 13
+    // carry the bias force p as a seventh column: the same instructions form
+    // pa = p + h u / D and X^T pa. Lanes 14.. shadow lane 13 and write nothing.
+    const int L = tm.r < 14 ? tm.r : 13;
+    const int cc = L >> 1, hh = L & 1, q0 = 3 * hh;
+    const bool colP = cc < 6;
+    const int cr = colP ? cc : 5;  // the column whose N row a bias lane reads (unused)
+    auto xt_pair = [&](const SE3<TA> &g, const TA *x3, TA *o3) {
+      TA v[3], w[3];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) par[c] = prow[c] - tr * h[c];
-    const TA par_b = pbr + prow[0] * uD;
-    TA ncol[6], nrow[6], orow[6];
-    adinvT(ga, par, ncol);  // column r of N = X^T Pa
-    TA *x = xb[i & 1];
-    if (tm.r < 6) {
+      for (int k = 0; k < 3; ++k)
+        v[k] = g.R[3 * k] * x3[0] + g.R[3 * k + 1] * x3[1] + g.R[3 * k + 2] * x3[2];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) x[c * 6 + r] = ncol[c];
+      for (int k = 0; k < 3; ++k) w[k] = __shfl_xor_sync(tm.mask, v[k], 1, P);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
+        const TA t = (v[k] + g.p[k1] * w[k2]) - g.p[k2] * w[k1];  // R n + p x R f
+        o3[k] = hh == 0 ? t : v[k];
+      }
+    };
+    TA nt_td = TA(0), nt_J[3] = {TA(0), TA(0), TA(0)};
+    SE3<T> nt_g;
+    se3_identity(nt_g);
+    auto fetch = [&](int i) {
+      const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+      nt_td = TA(w[W_TD]);
+      if (i > 0) {
+        ld_se3(w + W_G, nt_g);
+        const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nt_J[k] = colP ? TA(J[s6(q0 + k, cr)]) : TA(0);
+      }
+    };
+    TA pc[3] = {TA(0), TA(0), TA(0)};  // rows q0.. of column cc of P_i (bias lanes: p_i)
+    if (n > 0) {
+      const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pc[k] = colP ? TA(J[s6(q0 + k, cr)]) : TA(0);
+      fetch(n - 1);
     }
-    // bias p_{i-1} = X^T pa, component r (the other lanes' components by shuffle)
-    TA pa[6];
+    for (int i = n - 1; i >= 0; --i) {
+      const TA td = nt_td;
+      SE3<TA> ga;
+      TA Jr[3];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) pa[c] = __shfl_sync(tm.mask, par_b, c, P);
-    const TA tb = top ? ga.R[3 * k] * pa[0] + ga.R[3 * k + 1] * pa[1] + ga.R[3 * k + 2] * pa[2]
-                      : ga.R[3 * k] * pa[3] + ga.R[3 * k + 1] * pa[4] + ga.R[3 * k + 2] * pa[5];
-    const TA fa = __shfl_sync(tm.mask, tb, 3 + ka, P), fb = __shfl_sync(tm.mask, tb, 3 + kb, P);
-    pbr = top ? (tb + ga.p[ka] * fb) - ga.p[kb] * fa : tb;
-    tm.sync();
+      for (int c = 0; c < 9; ++c) ga.R[c] = TA(nt_g.R[c]);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) nrow[c] = x[r * 6 + c];
-    adinvT(ga, nrow, orow);  // row r of N X = X^T Pa X
+      for (int c = 0; c < 3; ++c) ga.p[c] = TA(nt_g.p[c]);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) prow[c] = Jr[c] + orow[c];
+      for (int k = 0; k < 3; ++k) Jr[k] = nt_J[k];
+      if (i > 0) fetch(i - 1);
+      TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
+      // h = column 0 of P (lanes 0, 1); D = P_00; h_cc = P_{0,cc}; p_0 on lane 12
+      const TA D = __shfl_sync(tm.mask, pc[0], 0, P);
+      const TA p0 = __shfl_sync(tm.mask, pc[0], 12, P);
+      const TA hc = __shfl_sync(tm.mask, pc[0], 2 * cr, P);
+      TA hr[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) hr[k] = __shfl_sync(tm.mask, pc[k], hh, P);
+      bad |= !(D > TA(0));
+      const TA Dinv = TA(1) / D;
+      const TA uD = (td - p0) * Dinv;  // u_i / D_i
+      if (tm.r < 2) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ra[A_H + q0 + k] = pc[k];
+      }
+      if (tm.r == 0) {
+        ra[A_DD] = Dinv;
+        ra[A_UU] = uD;
+      }
+      if (i == 0) break;
+      // Pa = P - h h^T / D (column cc); pa = p + h u / D (bias lanes)
+      const TA t = colP ? hc * Dinv : -uD;
+      TA pa[3], o[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pa[k] = pc[k] - t * hr[k];
+      xt_pair(ga, pa, o);  // column cc of N = X^T Pa; bias lanes: p_{i-1} = X^T pa
+      TA *x = xb[i & 1];
+      if (tm.r < 12) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[(q0 + k) * 6 + cc] = o[k];
+      }
+      if (!colP) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) pc[k] = o[k];
+      }
+      tm.sync();
+      TA nr[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) nr[k] = x[cr * 6 + q0 + k];  // row cc of N, half hh
+      xt_pair(ga, nr, o);  // column cc of X^T N^T = X^T Pa X
+      if (colP) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) pc[k] = Jr[k] + o[k];
+      }
+    }
   }
   tm.sync();
 
