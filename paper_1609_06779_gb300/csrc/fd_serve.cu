@@ -133,15 +133,19 @@ struct Arena {
 // Teams depend on a request's algorithm and chain length only, so its arithmetic
 // does not depend on the mix. CFA and the reverse sweep take about one lane per
 // four links (8..64): long chains bound a tick's latency, and a small team
-// leaves a 256-link chain's OEE levels serial on eight lanes. ABIA takes 8.
+// leaves a 256-link chain's OEE levels serial on eight lanes. ABIA takes 8 up to
+// 64 links and 16 (its twelve-lane step) beyond.
 enum TeamKind { kTeamCFA, kTeamReverse, kTeamABIA };
 int team_for(TeamKind k, int n) {
-  if (k == kTeamABIA) return 8;
+  if (k == kTeamABIA) return n <= 64 ? 8 : 16;
   return n <= 32 ? 8 : (n <= 64 ? 16 : (n <= 128 ? 32 : 64));
 }
-// side stream of a launch: ABIA requests on stream 4, CFA team classes 8..64 on 0..3
-int aux_of(bool abia, int team) {
-  return abia ? 4 : (team <= 8 ? 0 : (team <= 16 ? 1 : (team <= 32 ? 2 : 3)));
+// side stream of a request, by algorithm and chain length only (its FD, adjoint
+// solve and reverse sweep launches all go there, in order): CFA length classes
+// on streams 0..3, ABIA up to 64 links on 4, longer ABIA on 5
+int aux_of(bool abia, int n) {
+  if (abia) return n <= 64 ? 4 : 5;
+  return n <= 32 ? 0 : (n <= 64 ? 1 : (n <= 128 ? 2 : 3));
 }
 
 __global__ void scatter_kernel(const double *stage, const UpDesc *d, int nd, Arena A) {
@@ -258,7 +262,7 @@ struct fd_server_s {
   // side streams of a tick: one per CFA team class and one for ABIA; a request's
   // launches (FD, the linear solve of its adjoint, the reverse sweep) stay on one
   // of them, in order, and the classes run concurrently
-  static constexpr int kAux = 5;
+  static constexpr int kAux = 6;
   cudaStream_t aux[kAux] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
 
@@ -458,7 +462,7 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       a.mode = mode;
       a.status = mode == fdk::MODE_FD ? S->d_status + s : nullptr;
       a.team = t;
-      cudaStream_t st = S->aux[aux_of(algo != FD_CFA, t)];
+      cudaStream_t st = S->aux[aux_of(algo != FD_CFA, all[s]->n)];
       a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
       if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, st);
       return fdk::launch_abia(a, 0, t, st);
@@ -488,7 +492,7 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       a.out2 = S->A.qdbar;
       a.out3 = nullptr;
       a.ws_t = S->A.ws_r;
-      return fdk::launch_adjoint_rnea(a, 0, t, S->aux[aux_of(abia, t)]);
+      return fdk::launch_adjoint_rnea(a, 0, t, S->aux[aux_of(abia, all[s]->n)]);
     });
   };
   if (e == cudaSuccess) e = reverse(gstart[0], gstart[1] - gstart[0], false);
