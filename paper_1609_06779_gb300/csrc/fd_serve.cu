@@ -124,6 +124,7 @@ struct Arena {
   double *ws_r;                                     // [cap][NT_ADJ]  reverse sweep
   double *ws_c;                                     // [cap][NA_CFA]  CFA rows
   double *ws_b;                                     // [cap][NA_ABIA] ABIA
+  double *ws_t2, *ws_c2, *ws_b2;                    // the same for the adjoint's linear solves
   double *hist;                                     // rollout torques
   int64_t *r_hist;                                  // per slot: history start
   int32_t *r_step, *r_steps;                        // per slot: step, total steps
@@ -262,9 +263,12 @@ struct fd_server_s {
   // side streams of a tick: one per CFA team class and one for ABIA; a request's
   // launches (FD, the linear solve of its adjoint, the reverse sweep) stay on one
   // of them, in order, and the classes run concurrently
-  static constexpr int kAux = 6;
+  // streams 0..5: FD and reverse sweep per class; 6..11: the same classes' linear
+  // solves of the adjoint (lambda = M^-1 w needs q only, so it runs beside FD on
+  // its own workspaces), joined into the class stream before the reverse sweep
+  static constexpr int kClass = 6, kAux = 2 * kClass;
   cudaStream_t aux[kAux] = {};
-  cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {}, ev_lin[kClass] = {};
 
   RangeAlloc slots, recs, hist;
   std::unordered_map<int, Model> models;
@@ -462,8 +466,14 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       a.mode = mode;
       a.status = mode == fdk::MODE_FD ? S->d_status + s : nullptr;
       a.team = t;
-      cudaStream_t st = S->aux[aux_of(algo != FD_CFA, all[s]->n)];
-      a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
+      const bool lin = mode == fdk::MODE_LINEAR;
+      cudaStream_t st = S->aux[aux_of(algo != FD_CFA, all[s]->n) + (lin ? fd_server_s::kClass : 0)];
+      if (lin) {
+        a.ws_t = S->A.ws_t2;
+        a.ws_a = algo == FD_CFA ? S->A.ws_c2 : S->A.ws_b2;
+      } else {
+        a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
+      }
       if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, st);
       return fdk::launch_abia(a, 0, t, st);
     });
@@ -495,6 +505,10 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       return fdk::launch_adjoint_rnea(a, 0, t, S->aux[aux_of(abia, all[s]->n)]);
     });
   };
+  for (int k = 0; k < fd_server_s::kClass && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(S->ev_lin[k], S->aux[fd_server_s::kClass + k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->aux[k], S->ev_lin[k], 0);
+  }
   if (e == cudaSuccess) e = reverse(gstart[0], gstart[1] - gstart[0], false);
   if (e == cudaSuccess) e = reverse(gstart[2], gstart[3] - gstart[2], true);
   for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k) {
@@ -602,7 +616,8 @@ void worker_main(fd_server_s *S) {
 }
 
 size_t per_link_bytes() {
-  return 8 * sizeof(double) + (fdk::NT + fdk::NT_ADJ + fdk::NA_CFA + fdk::NA_ABIA) * sizeof(double) +
+  return 8 * sizeof(double) +
+         (2 * (fdk::NT + fdk::NA_CFA + fdk::NA_ABIA) + fdk::NT_ADJ) * sizeof(double) +
          sizeof(int64_t) + 2 * sizeof(int32_t) + sizeof(double) +
          2 * sizeof(int32_t) + 3 * sizeof(int64_t);
 }
@@ -614,6 +629,8 @@ void destroy_streams(fd_server_s *S) {
     if (S->aux[k]) cudaStreamDestroy(S->aux[k]);
     if (S->ev_join[k]) cudaEventDestroy(S->ev_join[k]);
   }
+  for (int k = 0; k < fd_server_s::kClass; ++k)
+    if (S->ev_lin[k]) cudaEventDestroy(S->ev_lin[k]);
   if (S->ev_fork) cudaEventDestroy(S->ev_fork);
   if (S->stream) cudaStreamDestroy(S->stream);
 }
@@ -661,6 +678,8 @@ fd_status fd_serve_create(int32_t device, size_t mem_budget_bytes, const double 
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_join[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < fd_server_s::kClass && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&S->ev_lin[k], cudaEventDisableTiming);
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -688,6 +707,9 @@ fd_status fd_serve_create(int32_t device, size_t mem_budget_bytes, const double 
   S->A.ws_r = reinterpret_cast<double *>(take(size_t(C) * fdk::NT_ADJ * 8));
   S->A.ws_c = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_CFA * 8));
   S->A.ws_b = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_ABIA * 8));
+  S->A.ws_t2 = reinterpret_cast<double *>(take(size_t(C) * fdk::NT * 8));
+  S->A.ws_c2 = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_CFA * 8));
+  S->A.ws_b2 = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_ABIA * 8));
   S->A.r_hist = reinterpret_cast<int64_t *>(take(size_t(C) * 8));
   S->A.r_step = reinterpret_cast<int32_t *>(take(size_t(C) * 4));
   S->A.r_steps = reinterpret_cast<int32_t *>(take(size_t(C) * 4));
