@@ -94,6 +94,26 @@ def test_every_team_class_alone_and_in_the_mix():
     srv.close()
 
 
+def test_per_size_baseline_computes_the_same_results():
+    """FD_SERVE_PER_SIZE (one launch per distinct length, the static baseline)
+    runs the same kernels with the same teams: results bitwise equal."""
+    from paper_1609_06779_gb300 import fd
+    rng = np.random.default_rng(5)
+    models, reqs = _requests(rng, n_models=8, n_req=30)
+    out = []
+    for per_size in (False, True):
+        srv = fd.Server(budget_bytes=256 << 20, per_size=per_size)
+        ids = [srv.add_model(m) for m in models]
+        out.append(_run(srv, ids, reqs))
+        srv.close()
+    for r, a, b in zip(reqs, out[0], out[1]):
+        assert a["status"] == 0 and b["status"] == 0
+        keys = ("q", "qdot", "qddot") if r["kind"] == "rollout" else (
+            "qddot", "q_bar", "qdot_bar", "tau_bar")
+        for k in keys:
+            assert np.array_equal(a[k], b[k]), (r["kind"], k)
+
+
 def test_served_results_agree_with_the_batch_api_and_oracle():
     from paper_1609_06779_gb300 import fd
     rng = np.random.default_rng(1)
