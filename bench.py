@@ -176,28 +176,37 @@ def cpu_oracle(model, st, n_problems, budget_s=10.0, threads=None):
                       f" {one} in {el1:.1f} s on one core, FP64"}
 
 
-def accuracy(model, st, outs, sample=1024):
+def accuracy(model, st, outs, sample32=4096):
     """Largest error per chain, max |qdd - ref| / max(max |ref|, 1), of each output
-    against the FP64 oracle (dense Cholesky) on the first `sample` chains."""
+    against the FP64 oracle (dense Cholesky): every chain for the FP64 paths, the
+    first `sample32` chains for the FP32 and mixed paths (also against the oracle
+    fed the same states rounded to FP32)."""
     import oracle
     n = int(model.offsets[1] - model.offsets[0])
-    sample = min(sample, model.n_chains)
-    L = sample * n
-    sub = synth.ChainModel(model.axes[:L], model.frames[:L], model.inertias[:L],
-                           model.offsets[:sample + 1].copy(), model.gravity)
+    threads = os.cpu_count() or 1
     f32 = lambda a: a.astype(np.float32).astype(np.float64)
-    ref = oracle.fd(sub, st.q[:L], st.qdot[:L], st.tau[:L], algo="cholesky").reshape(sample, n)
-    ref32 = oracle.fd(sub, f32(st.q[:L]), f32(st.qdot[:L]), f32(st.tau[:L]),
-                      algo="cholesky").reshape(sample, n)
-    res = {"sample_chains": sample, "reference": "FP64 CPU oracle, dense Cholesky",
-           "float_paths_also_vs_states_rounded_to_fp32": {}}
+    K = model.n_chains
+    ref = oracle.fd(model, st.q, st.qdot, st.tau, algo="cholesky",
+                    n_threads=threads).reshape(K, n)
+    k32 = min(sample32, K)
+    L32 = k32 * n
+    sub = synth.ChainModel(model.axes[:L32], model.frames[:L32], model.inertias[:L32],
+                           model.offsets[:k32 + 1].copy(), model.gravity)
+    ref32 = oracle.fd(sub, f32(st.q[:L32]), f32(st.qdot[:L32]), f32(st.tau[:L32]),
+                      algo="cholesky", n_threads=threads).reshape(k32, n)
+    res = {"reference": "FP64 CPU oracle, dense Cholesky", "chains_fp64": K,
+           "chains_float": k32, "float_paths_also_vs_states_rounded_to_fp32": {}}
+
+    def err(got, r):
+        scale = np.maximum(np.abs(r).max(axis=1), 1.0)
+        return float((np.abs(got - r).max(axis=1) / scale).max())
     for k, v in outs.items():
-        got = v[:L].double().cpu().numpy().reshape(sample, n)
-        for r, dst in ((ref, res), (ref32, res["float_paths_also_vs_states_rounded_to_fp32"])):
-            if dst is not res and k.endswith("fp64"):
-                continue
-            scale = np.maximum(np.abs(r).max(axis=1), 1.0)
-            dst[k] = float((np.abs(got - r).max(axis=1) / scale).max())
+        got = v.double().numpy()
+        rows = got.size // n
+        got = got.reshape(rows, n)
+        res[k] = err(got, ref[:rows])
+        if not k.endswith("fp64"):
+            res["float_paths_also_vs_states_rounded_to_fp32"][k] = err(got[:k32], ref32)
     return res
 
 
@@ -591,8 +600,9 @@ def main():
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"}}
 
     # the first chains' results of every path, for the accuracy check of the CPU leg
-    n_acc = min(args.chains, 1024) * args.links
-    acc_outs = {f"{a}_fp64": out[a][:n_acc].cpu() for a in ALGOS}
+    # every chain's FP64 result, the first 4 096 chains' FP32 / mixed results
+    n_acc = min(args.chains, 4096) * args.links
+    acc_outs = {f"{a}_fp64": out[a].cpu() for a in ALGOS}
 
     # CFA with block cyclic reduction in place of OEE (context; not part of the step)
     variants = {}
@@ -603,7 +613,7 @@ def main():
         ms = _time_ms(lambda: fd.solve(batch, q, qd, tau, algo="cfa_cr", team=tcr, out=ocr,
                                        ws=wcr), reps=5, warm=2)
         fl = roofline.flops("cfa_cr", lengths)
-        acc_outs["cfa_cr_fp64"] = ocr[:n_acc].cpu()
+        acc_outs["cfa_cr_fp64"] = ocr.cpu()
         variants["cfa_cr_fp64"] = {"team": tcr, "ms": ms, "solves_per_s": args.chains / (ms * 1e-3),
                                    "tflops": fl / (ms * 1e-3) / 1e12,
                                    "frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
