@@ -641,17 +641,18 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
     if (algo == FD_JSIIA) return fdk::launch_jsiia(k, prec_k, t, s);
     return fdk::launch_abia(k, prec_k, t, s);
   };
-  // 1. qdd (unless given)
+  // 1-2. lambda = M^{-1} qdd_bar with the algorithm's own factorisation: tau_bar;
+  // without a given qdd, FD and this solve share one elimination (MODE_FD2)
   const void *qdd = qddot;
   if (!qdd) {
-    a.mode = fdk::MODE_FD;
+    a.mode = fdk::MODE_FD2;
     a.in3 = tau;
     a.out = qdd_scratch;
+    a.in4 = qddot_bar;
+    a.out4 = tau_bar;
     e = run_fd(a);
     qdd = qdd_scratch;
-  }
-  // 2. lambda = M^{-1} qdd_bar with the algorithm's own factorisation: tau_bar
-  if (e == cudaSuccess) {
+  } else {
     a.mode = fdk::MODE_LINEAR;
     a.in3 = qddot_bar;
     a.out = tau_bar;

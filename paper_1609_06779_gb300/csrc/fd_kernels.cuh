@@ -76,7 +76,7 @@ __device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, c
                                          int mode) {
   static_assert(P >= 8 && P <= 32, "component lanes need a team of 8..32 lanes");
   const int n = pb.n;
-  const bool mode_fd = mode == MODE_FD;
+  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2;
   const int r = tm.r < 6 ? tm.r : 5;
   const bool top = r < 3;
   const int k = top ? r : r - 3;
@@ -183,7 +183,7 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
     }
   }
   const int a = pb.a, b = pb.b;
-  const bool mode_fd = mode == MODE_FD;
+  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2;
   SegOp<T> op;
   se3_identity(op.h);
   // joint transforms and this segment's product h = g_a ... g_{b-1}
@@ -434,7 +434,7 @@ __device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, Out U
 // Z = U_i L_{i+d}^{-T}, and K U_{i-d} = G^T G, K R_{i-d} = G^T g of row i-d.
 template <class TA>
 __device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD, int srcU,
-                                           int srcR) {
+                                           int srcR, int srcR2 = -1) {
   const RowP<TA> row = rowp(wa, n, m);
   TA Dm[15], L[15], inv[5];
 #pragma unroll
@@ -450,6 +450,13 @@ __device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD
   fwd5(L, inv, r);
 #pragma unroll
   for (int k = 0; k < 5; ++k) row[A_GR + k] = r[k];
+  if (srcR2 >= 0) {  // the second right-hand side: g2 = L^{-1} R2
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r[k] = row[srcR2 + k];
+    fwd5(L, inv, r);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) row[A_GR2 + k] = r[k];
+  }
   if (m + d < n) {  // U_m couples row m to m + d; zero beyond
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -470,12 +477,18 @@ __device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD
 //   U_i = -E_i U_{i+d},  E_i = U_i D_{i+d}^{-1},  K_i = U_{i-d}^T D_{i-d}^{-1}.
 template <class TA>
 __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int srcD, int srcU,
-                                        int srcR, TA *Dn, TA *Un, TA *Rn) {
+                                        int srcR, TA *Dn, TA *Un, TA *Rn, int srcR2 = -1,
+                                        TA *Rn2 = nullptr) {
   const RowP<const TA> row = rowp(wa, n, i);
+  const bool two = srcR2 >= 0;
 #pragma unroll
   for (int k = 0; k < 15; ++k) Dn[k] = row[srcD + k];
 #pragma unroll
   for (int k = 0; k < 5; ++k) Rn[k] = row[srcR + k];
+  if (two) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Rn2[k] = row[srcR2 + k];
+  }
 #pragma unroll
   for (int k = 0; k < 25; ++k) Un[k] = TA(0);
   if (i + d < n) {
@@ -505,6 +518,14 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
     for (int r = 0; r < 5; ++r)
 #pragma unroll
       for (int k = 0; k < 5; ++k) Rn[r] -= Z[r][k] * gr[k];  // E_i R_{i+d} = Z g_{i+d}
+    if (two) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) gr[k] = nb[A_GR2 + k];
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Rn2[r] -= Z[r][k] * gr[k];
+    }
     if (i + 2 * d < n) {
 #pragma unroll
       for (int r = 0; r < 5; ++r)
@@ -537,6 +558,14 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
     for (int r = 0; r < 5; ++r)
 #pragma unroll
       for (int k = 0; k < 5; ++k) Rn[r] -= G[k][r] * gr[k];  // K_i R_{i-d} = G^T g
+    if (two) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) gr[k] = pr[A_GR2 + k];
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Rn2[r] -= G[k][r] * gr[k];
+    }
   }
 }
 
@@ -549,7 +578,7 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
 // substitution then solves the rows level by level from the last one down:
 // x_i = D_i^{-1} (R_i - U_{i-d}^T x_{i-d} - U_i x_{i+d}).
 template <class TA, int P>
-__device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n) {
+__device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, bool two) {
   bool bad = false;
   int levels = 0;
   while ((1 << levels) < n) ++levels;
@@ -559,7 +588,7 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n) {
     const int d = 1 << (j - 1);
     for (int t = 2 * tm.r; (t + 1) * d - 1 < n; t += 2 * P) {  // eliminated rows
       const int m = (t + 1) * d - 1;
-      bad |= !oee_factor<TA>(m, d, n, wa, A_D0, A_U0, A_R0);
+      bad |= !oee_factor<TA>(m, d, n, wa, A_D0, A_U0, A_R0, two ? A_R20 : -1);
       if (m - d >= 0) {  // keep the lower coupling for the back substitution
         const RowP<TA> lo = rowp(wa, n, m - d) + A_U0;
         const RowP<TA> row = rowp(wa, n, m);
@@ -570,8 +599,8 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n) {
     tm.sync();
     for (int t = 2 * tm.r + 1; (t + 1) * d - 1 < n; t += 2 * P) {  // kept rows: update in place
       const int i = (t + 1) * d - 1;
-      TA Dn[15], Un[25], Rn[5];
-      oee_row<TA>(i, d, n, wa, A_D0, A_U0, A_R0, Dn, Un, Rn);
+      TA Dn[15], Un[25], Rn[5], Rn2[5];
+      oee_row<TA>(i, d, n, wa, A_D0, A_U0, A_R0, Dn, Un, Rn, two ? A_R20 : -1, Rn2);
       const RowP<TA> row = rowp(wa, n, i);
 #pragma unroll
       for (int k = 0; k < 15; ++k) row[A_D0 + k] = Dn[k];
@@ -579,6 +608,10 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n) {
       for (int k = 0; k < 25; ++k) row[A_U0 + k] = Un[k];
 #pragma unroll
       for (int k = 0; k < 5; ++k) row[A_R0 + k] = Rn[k];
+      if (two) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) row[A_R20 + k] = Rn2[k];
+      }
     }
     tm.sync();
   }
@@ -598,6 +631,14 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n) {
     bwd5(L, inv, r);
 #pragma unroll
     for (int k = 0; k < 5; ++k) row[A_FC + k] = r[k];
+    if (two) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) r[k] = row[A_R20 + k];
+      fwd5(L, inv, r);
+      bwd5(L, inv, r);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) row[A_FC2 + k] = r[k];
+    }
   }
   tm.sync();
   for (int j = levels; j >= 1; --j) {
@@ -605,31 +646,35 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n) {
     for (int t = 2 * tm.r; (t + 1) * d - 1 < n; t += 2 * P) {
       const int i = (t + 1) * d - 1;
       const RowP<TA> row = rowp(wa, n, i);
-      TA r[5], L[15], inv[5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) r[k] = row[A_R0 + k];
-      if (i + d < n) {  // - U_i x_{i+d}
-        const RowP<TA> xn = rowp(wa, n, i + d) + A_FC;
-#pragma unroll
-        for (int rr = 0; rr < 5; ++rr)
-#pragma unroll
-          for (int k = 0; k < 5; ++k) r[rr] -= row[A_U0 + 5 * rr + k] * xn[k];
-      }
-      if (i - d >= 0) {  // - U_{i-d}^T x_{i-d}
-        const RowP<TA> xp = rowp(wa, n, i - d) + A_FC;
-#pragma unroll
-        for (int rr = 0; rr < 5; ++rr)
-#pragma unroll
-          for (int k = 0; k < 5; ++k) r[rr] -= row[A_LO + 5 * k + rr] * xp[k];
-      }
+      TA L[15], inv[5];
 #pragma unroll
       for (int k = 0; k < 15; ++k) L[k] = row[A_L + k];
 #pragma unroll
       for (int k = 0; k < 5; ++k) inv[k] = row[A_LI + k];
-      fwd5(L, inv, r);
-      bwd5(L, inv, r);
+      for (int h = 0; h < (two ? 2 : 1); ++h) {
+        const int fR = h ? A_R20 : A_R0, fX = h ? A_FC2 : A_FC;
+        TA r[5];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) row[A_FC + k] = r[k];
+        for (int k = 0; k < 5; ++k) r[k] = row[fR + k];
+        if (i + d < n) {  // - U_i x_{i+d}
+          const RowP<TA> xn = rowp(wa, n, i + d) + fX;
+#pragma unroll
+          for (int rr = 0; rr < 5; ++rr)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) r[rr] -= row[A_U0 + 5 * rr + k] * xn[k];
+        }
+        if (i - d >= 0) {  // - U_{i-d}^T x_{i-d}
+          const RowP<TA> xp = rowp(wa, n, i - d) + fX;
+#pragma unroll
+          for (int rr = 0; rr < 5; ++rr)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) r[rr] -= row[A_LO + 5 * k + rr] * xp[k];
+        }
+        fwd5(L, inv, r);
+        bwd5(L, inv, r);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) row[fX + k] = r[k];
+      }
     }
     tm.sync();
   }
@@ -637,8 +682,10 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n) {
 }
 
 // Algorithm 1 for one problem; BTD selects SolvBTDSys: 0 = odd-even
-// elimination (Algorithm 2), 1 = block cyclic reduction.
-template <class T, class TA, int P, int BTD>
+// elimination (Algorithm 2), 1 = block cyclic reduction. In MODE_FD2 a second
+// right-hand side (tau_delta := in4) rides along: the blocks D, U and their
+// elimination are shared, only R, F_c and CalcAcc are done twice.
+template <class T, class TA, int P, int BTD, bool TWO>
 __device__ __forceinline__ void cfa_body(const KArgs &A) {
   Team<P> tm;
   Prob<T> pb;
@@ -646,6 +693,9 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
   const int n = pb.n;
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_CFA;
   bool bad = false;
+  constexpr bool two = TWO;  // A.mode == MODE_FD2
+  const T *td2 = two ? static_cast<const T *>(A.in4) + A.state_off[pb.p] : nullptr;
+  T *out2 = two ? static_cast<T *>(A.out4) + A.state_off[pb.p] : nullptr;
 
   // bias torque and tau_delta (Algorithm 1: CalcInvDyn, CalcDiffTorques)
   id_team<T, P>(tm, pb, A.grav, A.mode);
@@ -662,6 +712,7 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     calc_dblock<T, TA>(i > 0 ? &g : nullptr, i > 0 ? rec - REC + REC_JI : nullptr,
                        rec + REC_JI, row + A_D0);
     T yv[6] = {w[W_TD], T(0), T(0), T(0), T(0), T(0)};
+    T y2[3] = {two ? td2[i] : T(0), T(0), T(0)};
     if (i + 1 < n) {
       SE3<T> gn;
       ld_se3(w + NT + W_G, gn);
@@ -671,6 +722,12 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
       yv[0] -= gn.R[0] * tn;
       yv[1] -= gn.R[3] * tn;
       yv[2] -= gn.R[6] * tn;
+      if (two) {
+        const T t2 = td2[i + 1];
+        y2[0] -= gn.R[0] * t2;
+        y2[1] -= gn.R[3] * t2;
+        y2[2] -= gn.R[6] * t2;
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < 25; ++k) row[A_U0 + k] = TA(0);
@@ -682,6 +739,11 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     for (int k = 0; k < 6; ++k)
       z[k] = Ki[s6(k, 0)] * yv[0] + Ki[s6(k, 1)] * yv[1] + Ki[s6(k, 2)] * yv[2];
     stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
+    if (two) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        row[A_Z2 + k] = TA(Ki[s6(k, 0)] * y2[0] + Ki[s6(k, 1)] * y2[1] + Ki[s6(k, 2)] * y2[2]);
+    }
   }
   tm.sync();
   for (int i = tm.r; i < n; i += P) {
@@ -697,12 +759,30 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     }
     const RowP<TA> row = rowp(wa, n, i);
     for (int k = 0; k < 5; ++k) row[A_R0 + k] = TA(-z[k + 1]);
+    if (two) {
+      T z2[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) z2[k] = T(row[A_Z2 + k]);
+      if (i > 0) {
+        SE3<T> g;
+        ld_se3(w + W_G, g);
+        const RowP<TA> rp = rowp(wa, n, i - 1);
+        T zp[6], t[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) zp[k] = T(rp[A_Z2 + k]);
+        adinv(g, zp, t);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) z2[k] -= t[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) row[A_R20 + k] = TA(-z2[k + 1]);
+    }
   }
   tm.sync();
 
   if constexpr (BTD == 1) {
     // SolvBTDSys by block cyclic reduction
-    bad |= cr_solve<TA, P>(tm, wa, n);
+    bad |= cr_solve<TA, P>(tm, wa, n, two);
   } else {
   // SolvBTDSys: odd-even elimination, ceil(log2 n) levels (Algorithm 2)
   int levels = 0;
@@ -712,15 +792,19 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     const int d = 1 << (j - 1);
     const int sD = src ? A_D1 : A_D0, sU = src ? A_U1 : A_U0, sR = src ? A_R1 : A_R0;
     const int tD = src ? A_D0 : A_D1, tU = src ? A_U0 : A_U1, tR = src ? A_R0 : A_R1;
-    for (int m = tm.r; m < n; m += P) bad |= !oee_factor<TA>(m, d, n, wa, sD, sU, sR);
+    const int sR2 = two ? (src ? A_R21 : A_R20) : -1, tR2 = src ? A_R20 : A_R21;
+    for (int m = tm.r; m < n; m += P) bad |= !oee_factor<TA>(m, d, n, wa, sD, sU, sR, sR2);
     tm.sync();
     for (int i = tm.r; i < n; i += P) {
-      TA Dn[15], Un[25], Rn[5];
-      oee_row<TA>(i, d, n, wa, sD, sU, sR, Dn, Un, Rn);
+      TA Dn[15], Un[25], Rn[5], Rn2[5];
+      oee_row<TA>(i, d, n, wa, sD, sU, sR, Dn, Un, Rn, sR2, Rn2);
       const RowP<TA> row = rowp(wa, n, i);
       for (int k = 0; k < 15; ++k) row[tD + k] = Dn[k];
       for (int k = 0; k < 25; ++k) row[tU + k] = Un[k];
       for (int k = 0; k < 5; ++k) row[tR + k] = Rn[k];
+      if (two) {
+        for (int k = 0; k < 5; ++k) row[tR2 + k] = Rn2[k];
+      }
     }
     tm.sync();
     src ^= 1;
@@ -735,6 +819,12 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     fwd5(L, inv, r);
     bwd5(L, inv, r);
     for (int k = 0; k < 5; ++k) row[A_FC + k] = r[k];
+    if (two) {
+      for (int k = 0; k < 5; ++k) r[k] = row[(src ? A_R21 : A_R20) + k];
+      fwd5(L, inv, r);
+      bwd5(L, inv, r);
+      for (int k = 0; k < 5; ++k) row[A_FC2 + k] = r[k];
+    }
   }
   tm.sync();
   }
@@ -760,6 +850,23 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     T z[6];
     sym6_apply(rec + REC_JI, yv, z);
     stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
+    if (two) {
+      T y[6] = {td2[i], T(row[A_FC2]), T(row[A_FC2 + 1]), T(row[A_FC2 + 2]), T(row[A_FC2 + 3]),
+                T(row[A_FC2 + 4])};
+      if (i + 1 < n) {
+        SE3<T> gn;
+        ld_se3(w + NT + W_G, gn);
+        const RowP<TA> rn = rowp(wa, n, i + 1);
+        T Fn[6] = {td2[i + 1], T(rn[A_FC2]), T(rn[A_FC2 + 1]), T(rn[A_FC2 + 2]),
+                   T(rn[A_FC2 + 3]), T(rn[A_FC2 + 4])};
+        T t[6];
+        adinvT(gn, Fn, t);
+        for (int k = 0; k < 6; ++k) y[k] -= t[k];
+      }
+      sym6_apply(rec + REC_JI, y, z);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) row[A_Z2 + k] = TA(z[k]);
+    }
   }
   tm.sync();
   for (int i = tm.r; i < n; i += P) {
@@ -772,6 +879,16 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
     }
     pb.out[i] = qdd;
     if (!finite_t(qdd)) bad = true;
+    if (two) {
+      const RowP<TA> row = rowp(wa, n, i);
+      T x = T(row[A_Z2]);
+      if (i > 0) {
+        const RowP<TA> rp = rowp(wa, n, i - 1);
+        x -= w[W_G + 0] * T(rp[A_Z2]) + w[W_G + 3] * T(rp[A_Z2 + 1]) + w[W_G + 6] * T(rp[A_Z2 + 2]);
+      }
+      out2[i] = x;
+      if (!finite_t(x)) bad = true;
+    }
   }
   const bool any_bad = tm.any(bad);
   if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
@@ -779,12 +896,23 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
 
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(KArgs A) {
-  cfa_body<T, TA, P, 0>(A);
+  cfa_body<T, TA, P, 0, false>(A);
 }
 
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_cr_kernel(KArgs A) {
-  cfa_body<T, TA, P, 1>(A);
+  cfa_body<T, TA, P, 1, false>(A);
+}
+
+// MODE_FD2: forward dynamics and the adjoint's linear solve in one elimination
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa2_kernel(KArgs A) {
+  cfa_body<T, TA, P, 0, true>(A);
+}
+
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_cr2_kernel(KArgs A) {
+  cfa_body<T, TA, P, 1, true>(A);
 }
 
 // ------------------------------------------------------------------ JSIIA
@@ -878,6 +1006,9 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
   const int64_t s0 = A.state_off[pb.p];
   TA *vec = static_cast<TA *>(A.ws_a) + s0 * NA_JSIIA + A.sq_off[pb.p] * NSQ_JSIIA;
   TA *H = vec + n;                                   // h_i = I^c_i e_1, [n][6]
+  TA *vec2 = vec + 7 * static_cast<int64_t>(n);      // MODE_FD2: second right-hand side
+  TA *const vec1 = vec;
+  const bool two = A.mode == MODE_FD2;
   TA *M = vec + static_cast<int64_t>(n) * NA_JSIIA;  // n x n, column-major, lower triangle
   // entry (i, l) of M (and of L) at M[l n + i]: the lanes, on neighbouring rows,
   // touch neighbouring addresses
@@ -886,6 +1017,10 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
 
   id_team<T, P>(tm, pb, A.grav, A.mode);
   for (int i = a; i < b; ++i) vec[i] = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]);
+  if (two) {
+    const T *in4 = static_cast<const T *>(A.in4) + s0;
+    for (int i = a; i < b; ++i) vec2[i] = TA(in4[i]);
+  }
 
   // composite inertias, backward over the links; h_i = column 0 of I^c_i
   auto load_g = [&](int i, SE3<TA> &ga) {
@@ -1045,66 +1180,77 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
     }
     tm.sync();
   }
-  for (int j0 = 0; j0 < n; j0 += NB) {  // L y = b
-    const int jb = min(NB, n - j0);
-    TA y[NB];
-#pragma unroll
-    for (int u = 0; u < NB; ++u) {
-      y[u] = TA(0);
-      if (u < jb) {
-        TA x = vec[j0 + u];
-#pragma unroll
-        for (int w = 0; w < u; ++w) x -= Mat(j0 + u, j0 + w) * y[w];
-        y[u] = x * H[static_cast<int64_t>(j0 + u) * 6];
+  for (int h = 0; h < (two ? 2 : 1); ++h) {
+    TA *vec = h ? vec2 : vec1;
+    for (int j0 = 0; j0 < n; j0 += NB) {  // L y = b
+      const int jb = min(NB, n - j0);
+      TA y[NB];
+  #pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        y[u] = TA(0);
+        if (u < jb) {
+          TA x = vec[j0 + u];
+  #pragma unroll
+          for (int w = 0; w < u; ++w) x -= Mat(j0 + u, j0 + w) * y[w];
+          y[u] = x * H[static_cast<int64_t>(j0 + u) * 6];
+        }
+      }
+      for (int i = j0 + jb + tm.r; i < n; i += P) {
+        TA x = vec[i];
+  #pragma unroll
+        for (int u = 0; u < NB; ++u) x -= Mat(i, j0 + u) * y[u];
+        vec[i] = x;
+      }
+      tm.sync();
+      if (tm.r == 0) {  // after every lane has read this block's right-hand side
+  #pragma unroll
+        for (int u = 0; u < NB; ++u)
+          if (u < jb) vec[j0 + u] = y[u];
       }
     }
-    for (int i = j0 + jb + tm.r; i < n; i += P) {
-      TA x = vec[i];
-#pragma unroll
-      for (int u = 0; u < NB; ++u) x -= Mat(i, j0 + u) * y[u];
-      vec[i] = x;
-    }
     tm.sync();
-    if (tm.r == 0) {  // after every lane has read this block's right-hand side
-#pragma unroll
-      for (int u = 0; u < NB; ++u)
-        if (u < jb) vec[j0 + u] = y[u];
-    }
-  }
-  tm.sync();
-  for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {  // L^T x = y
-    const int jb = min(NB, n - j0);
-    TA x[NB];
-#pragma unroll
-    for (int u = NB - 1; u >= 0; --u) {
-      x[u] = TA(0);
-      if (u < jb) {
-        TA t = vec[j0 + u];
-#pragma unroll
-        for (int w = u + 1; w < NB; ++w)
-          if (w < jb) t -= Mat(j0 + w, j0 + u) * x[w];
-        x[u] = t * H[static_cast<int64_t>(j0 + u) * 6];
+    for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {  // L^T x = y
+      const int jb = min(NB, n - j0);
+      TA x[NB];
+  #pragma unroll
+      for (int u = NB - 1; u >= 0; --u) {
+        x[u] = TA(0);
+        if (u < jb) {
+          TA t = vec[j0 + u];
+  #pragma unroll
+          for (int w = u + 1; w < NB; ++w)
+            if (w < jb) t -= Mat(j0 + w, j0 + u) * x[w];
+          x[u] = t * H[static_cast<int64_t>(j0 + u) * 6];
+        }
+      }
+      for (int i = tm.r; i < j0; i += P) {
+        TA t = vec[i];
+  #pragma unroll
+        for (int u = 0; u < NB; ++u)
+          if (u < jb) t -= Mat(j0 + u, i) * x[u];
+        vec[i] = t;
+      }
+      tm.sync();
+      if (tm.r == 0) {
+  #pragma unroll
+        for (int u = 0; u < NB; ++u)
+          if (u < jb) vec[j0 + u] = x[u];
       }
     }
-    for (int i = tm.r; i < j0; i += P) {
-      TA t = vec[i];
-#pragma unroll
-      for (int u = 0; u < NB; ++u)
-        if (u < jb) t -= Mat(j0 + u, i) * x[u];
-      vec[i] = t;
-    }
     tm.sync();
-    if (tm.r == 0) {
-#pragma unroll
-      for (int u = 0; u < NB; ++u)
-        if (u < jb) vec[j0 + u] = x[u];
-    }
   }
-  tm.sync();
   for (int i = a; i < b; ++i) {
     const T v = T(vec[i]);
     pb.out[i] = v;
     if (!finite_t(v)) bad = true;
+  }
+  if (two) {
+    T *out4 = static_cast<T *>(A.out4) + s0;
+    for (int i = a; i < b; ++i) {
+      const T v = T(vec2[i]);
+      out4[i] = v;
+      if (!finite_t(v)) bad = true;
+    }
   }
   const bool any_bad = tm.any(bad);
   if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
@@ -1117,8 +1263,10 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
 // inertia recursion P_{i-1} = J_{i-1} + X_i^T (P_i - P_i S D_i^{-1} S^T P_i) X_i
 // (serial in i, Section III), the bias-force recursion (backward) and the
 // acceleration recursion (forward) of M^{-1} = [I - S^T Y Pi]^T (S^T J^ S)^{-1}
-// [I - S^T Y Pi]. One thread per problem.
-template <class T, class TA>
+// [I - S^T Y Pi]. One thread per problem. TWO (MODE_FD2): a second right-hand
+// side in4 shares the articulated inertias; its bias force and acceleration pass
+// give M^{-1} in4 in out4.
+template <class T, class TA, bool TWO>
 __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
   Team<1> tm;
   Prob<T> pb;
@@ -1127,6 +1275,9 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_ABIA;
   bool bad = false;
   id_team<T, 1>(tm, pb, A.grav, A.mode);
+  const T *td2 = TWO ? static_cast<const T *>(A.in4) + A.state_off[pb.p] : nullptr;
+  T *out2 = TWO ? static_cast<T *>(A.out4) + A.state_off[pb.p] : nullptr;
+  TA pbias2[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
 
   TA Pm[21], pbias[6];
   if (n > 0) {
@@ -1145,6 +1296,11 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     for (int k = 0; k < 6; ++k) ra[A_H + k] = h[k];
     ra[A_DD] = Dinv;
     ra[A_UU] = u * Dinv;
+    TA u2 = TA(0);
+    if constexpr (TWO) {
+      u2 = TA(td2[i]) - pbias2[0];
+      ra[A_UU2] = u2 * Dinv;
+    }
     if (i == 0) break;
     // Pa = P - h h^T / D, pa = p + h u / D
     TA Pa[21], pa[6], hs[6];
@@ -1152,6 +1308,10 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     for (int r = 0; r < 6; ++r)
       for (int c = r; c < 6; ++c) Pa[s6(r, c)] = Pm[s6(r, c)] - h[r] * hs[c];
     for (int k = 0; k < 6; ++k) pa[k] = pbias[k] + hs[k] * u;
+    TA pa2[6];
+    if constexpr (TWO) {
+      for (int k = 0; k < 6; ++k) pa2[k] = pbias2[k] + hs[k] * u2;
+    }
     SE3<T> g;
     ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
     SE3<TA> ga;
@@ -1161,9 +1321,11 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     for (int k = 0; k < 21; ++k) Pm[k] = TA(J[k]);
     congruence_add(ga, Pa, Pm);
     adinvT(ga, pa, pbias);
+    if constexpr (TWO) adinvT(ga, pa2, pbias2);
   }
   // forward: a' = X_i a_{i-1}, qdd_i = (u_i - h_i . a') / D_i, a_i = a' + e_1 qdd_i
   TA acc[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+  TA acc2[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
   for (int i = 0; i < n; ++i) {
     const TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
     SE3<T> g;
@@ -1179,6 +1341,15 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     const T v = T(qdd);
     pb.out[i] = v;
     if (!finite_t(v)) bad = true;
+    if constexpr (TWO) {
+      adinv(ga, acc2, acc2);
+      TA s2 = TA(0);
+      for (int k = 0; k < 6; ++k) s2 += ra[A_H + k] * acc2[k];
+      const TA x = ra[A_UU2] - s2 * ra[A_DD];
+      acc2[0] += x;
+      out2[i] = T(x);
+      if (!finite_t(T(x))) bad = true;
+    }
   }
   set_status(A.status, pb.p, bad ? 2 : 0);
 }
@@ -1193,7 +1364,7 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
 // forms row r of N X_i = X_i^T N^T. The bias force and the acceleration pass
 // carry one component per lane, as in the component-lane inverse dynamics.
 // Each step's operands are loaded one step ahead (the loop is latency-bound).
-template <class T, class TA, int P>
+template <class T, class TA, int P, bool TWO>
 __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
   static_assert(P >= 8 && P <= 32, "six rows of P need a team of 8..32 lanes");
   __shared__ TA xbuf[128 / P][2][36];
@@ -1210,15 +1381,20 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
   bool bad = false;
   id_team<T, P>(tm, pb, A.grav, A.mode);
   tm.sync();
+  // TWO (MODE_FD2): a second right-hand side in4 rides along (its own bias force
+  // and acceleration pass); M^{-1} in4 goes to out4
+  const T *td2 = TWO ? static_cast<const T *>(A.in4) + A.state_off[pb.p] : nullptr;
+  T *out2 = TWO ? static_cast<T *>(A.out4) + A.state_off[pb.p] : nullptr;
 
   if constexpr (P < 16) {
     // operands of step i: tau_delta_i, g_i, row r of J_{i-1}
-    TA nt_td = TA(0), nt_J[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    TA nt_td = TA(0), nt_td2 = TA(0), nt_J[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
     SE3<T> nt_g;
     se3_identity(nt_g);
     auto fetch = [&](int i) {
       const T *w = pb.wt + static_cast<int64_t>(i) * NT;
       nt_td = TA(w[W_TD]);
+      if (TWO) nt_td2 = TA(td2[i]);
       if (i > 0) {
         ld_se3(w + W_G, nt_g);
         const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
@@ -1226,7 +1402,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
         for (int c = 0; c < 6; ++c) nt_J[c] = TA(J[s6(r, c)]);
       }
     };
-    TA prow[6], pbr = TA(0);  // row r of P_i; component r of the bias force p_i
+    TA prow[6], pbr = TA(0), pbr2 = TA(0);  // row r of P_i; component r of the bias forces
     if (n > 0) {
       const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
   #pragma unroll
@@ -1234,7 +1410,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       fetch(n - 1);
     }
     for (int i = n - 1; i >= 0; --i) {
-      const TA td = nt_td;
+      const TA td = nt_td, tdb = nt_td2;
       SE3<TA> ga;
       TA Jr[6];
   #pragma unroll
@@ -1253,10 +1429,13 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       bad |= !(D > TA(0));
       const TA Dinv = TA(1) / D;
       const TA uD = (td - p0) * Dinv;  // u_i / D_i
+      TA uD2 = TA(0);
+      if constexpr (TWO) uD2 = (tdb - __shfl_sync(tm.mask, pbr2, 0, P)) * Dinv;
       if (tm.r < 6) ra[A_H + tm.r] = prow[0];
       if (tm.r == 0) {
         ra[A_DD] = Dinv;
         ra[A_UU] = uD;
+        if (TWO) ra[A_UU2] = uD2;
       }
       if (i == 0) break;
       // row r of Pa = P - h h^T / D; component r of pa = p + h u / D
@@ -1280,6 +1459,15 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
                         : ga.R[3 * k] * pa[3] + ga.R[3 * k + 1] * pa[4] + ga.R[3 * k + 2] * pa[5];
       const TA fa = __shfl_sync(tm.mask, tb, 3 + ka, P), fb = __shfl_sync(tm.mask, tb, 3 + kb, P);
       pbr = top ? (tb + ga.p[ka] * fb) - ga.p[kb] * fa : tb;
+      if constexpr (TWO) {
+        const TA pb2 = pbr2 + prow[0] * uD2;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pa[c] = __shfl_sync(tm.mask, pb2, c, P);
+        const TA t2 = top ? ga.R[3 * k] * pa[0] + ga.R[3 * k + 1] * pa[1] + ga.R[3 * k + 2] * pa[2]
+                          : ga.R[3 * k] * pa[3] + ga.R[3 * k + 1] * pa[4] + ga.R[3 * k + 2] * pa[5];
+        const TA fa2 = __shfl_sync(tm.mask, t2, 3 + ka, P), fb2 = __shfl_sync(tm.mask, t2, 3 + kb, P);
+        pbr2 = top ? (t2 + ga.p[ka] * fb2) - ga.p[kb] * fa2 : t2;
+      }
       tm.sync();
   #pragma unroll
       for (int c = 0; c < 6; ++c) nrow[c] = x[r * 6 + c];
@@ -1294,7 +1482,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
     // partner): about 15 FP64 operations per lane instead of 24. Lanes 12 and 13
     // carry the bias force p as a seventh column: the same instructions form
     // pa = p + h u / D and X^T pa. Lanes 14.. shadow lane 13 and write nothing.
-    const int L = tm.r < 14 ? tm.r : 13;
+    const int L = tm.r < (TWO ? 16 : 14) ? tm.r : (TWO ? 15 : 13);
     const int cc = L >> 1, hh = L & 1, q0 = 3 * hh;
     const bool colP = cc < 6;
     const int cr = colP ? cc : 5;  // the column whose N row a bias lane reads (unused)
@@ -1312,12 +1500,13 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
         o3[k] = hh == 0 ? t : v[k];
       }
     };
-    TA nt_td = TA(0), nt_J[3] = {TA(0), TA(0), TA(0)};
+    TA nt_td = TA(0), nt_td2 = TA(0), nt_J[3] = {TA(0), TA(0), TA(0)};
     SE3<T> nt_g;
     se3_identity(nt_g);
     auto fetch = [&](int i) {
       const T *w = pb.wt + static_cast<int64_t>(i) * NT;
       nt_td = TA(w[W_TD]);
+      if (TWO) nt_td2 = TA(td2[i]);
       if (i > 0) {
         ld_se3(w + W_G, nt_g);
         const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
@@ -1333,7 +1522,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       fetch(n - 1);
     }
     for (int i = n - 1; i >= 0; --i) {
-      const TA td = nt_td;
+      const TA td = nt_td, tdb = nt_td2;
       SE3<TA> ga;
       TA Jr[3];
 #pragma unroll
@@ -1354,6 +1543,8 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       bad |= !(D > TA(0));
       const TA Dinv = TA(1) / D;
       const TA uD = (td - p0) * Dinv;  // u_i / D_i
+      TA uD2 = TA(0);  // the second right-hand side's bias force rides on lanes 14, 15
+      if constexpr (TWO) uD2 = (tdb - __shfl_sync(tm.mask, pc[0], 14, P)) * Dinv;
       if (tm.r < 2) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) ra[A_H + q0 + k] = pc[k];
@@ -1361,10 +1552,11 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       if (tm.r == 0) {
         ra[A_DD] = Dinv;
         ra[A_UU] = uD;
+        if (TWO) ra[A_UU2] = uD2;
       }
       if (i == 0) break;
       // Pa = P - h h^T / D (column cc); pa = p + h u / D (bias lanes)
-      const TA t = colP ? hc * Dinv : -uD;
+      const TA t = colP ? hc * Dinv : (cc == 6 ? -uD : -uD2);
       TA pa[3], o[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) pa[k] = pc[k] - t * hr[k];
@@ -1393,7 +1585,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
 
   // forward: a' = X_i a_{i-1}, qdd_i = u_i / D_i - (h_i . a') / D_i, a_i = a' + e_1 qdd_i;
   // lane r forms component r of a' (as in the component-lane inverse dynamics)
-  TA nx_h[6], nx_dd = TA(0), nx_ud = TA(0), nx_c[3], nx_p[3];
+  TA nx_h[6], nx_dd = TA(0), nx_ud = TA(0), nx_ud2 = TA(0), nx_c[3], nx_p[3];
   auto fetch_f = [&](int i) {
     const TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
@@ -1401,6 +1593,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
     for (int c = 0; c < 6; ++c) nx_h[c] = ra[A_H + c];
     nx_dd = ra[A_DD];
     nx_ud = ra[A_UU];
+    if (TWO) nx_ud2 = ra[A_UU2];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       nx_c[c] = TA(w[W_G + 3 * c + k]);  // column k of R
@@ -1409,6 +1602,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
   };
   if (n > 0) fetch_f(0);
   TA acc[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+  TA acc2[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
   for (int i = 0; i < n; ++i) {
     TA hh[6], cc[3], pp[3];
 #pragma unroll
@@ -1418,7 +1612,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       cc[c] = nx_c[c];
       pp[c] = nx_p[c];
     }
-    const TA dd = nx_dd, ud = nx_ud;
+    const TA dd = nx_dd, ud = nx_ud, ud2 = nx_ud2;
     if (i + 1 < n) fetch_f(i + 1);
     // (Ad_{g^-1} a)_k = R^T w (k < 3), R^T (v + w x p) (k >= 3)
     TA xv[3];
@@ -1442,6 +1636,27 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
     const T v = T(qdd);
     if ((i & (P - 1)) == tm.r) pb.out[i] = v;
     if (!finite_t(v)) bad = true;
+    if constexpr (TWO) {
+      if (top) {
+        xv[0] = acc2[0];
+        xv[1] = acc2[1];
+        xv[2] = acc2[2];
+      } else {
+        xv[0] = acc2[3] + acc2[1] * pp[2] - acc2[2] * pp[1];
+        xv[1] = acc2[4] + acc2[2] * pp[0] - acc2[0] * pp[2];
+        xv[2] = acc2[5] + acc2[0] * pp[1] - acc2[1] * pp[0];
+      }
+      const TA y2 = cc[0] * xv[0] + cc[1] * xv[1] + cc[2] * xv[2];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc2[c] = __shfl_sync(tm.mask, y2, c, P);
+      TA s2 = TA(0);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) s2 += hh[c] * acc2[c];
+      const TA x2 = ud2 - s2 * dd;
+      acc2[0] += x2;
+      if ((i & (P - 1)) == tm.r) out2[i] = T(x2);
+      if (!finite_t(T(x2))) bad = true;
+    }
   }
   if (tm.r == 0) set_status(A.status, pb.p, bad ? 2 : 0);
 }

@@ -47,18 +47,26 @@ constexpr int A_FC = 110;  // F_c (5)
 constexpr int A_G = 115;   // G = L^{-1} U (row-major 5x5) and g = L^{-1} R of this level
 constexpr int A_GR = 140;
 constexpr int A_LO = 145;  // cyclic reduction: the lower coupling U_{i-d} kept for back substitution
-constexpr int NA_CFA = 170;
+// a second right-hand side (MODE_FD2: the adjoint's M^{-1} w beside FD)
+constexpr int A_R20 = 170;  // R (5), two buffers
+constexpr int A_R21 = 175;
+constexpr int A_GR2 = 180;  // g = L^{-1} R of this level
+constexpr int A_FC2 = 185;  // F_c (5)
+constexpr int A_Z2 = 190;   // J^{-1} (I - Gamma)^T F products (6)
+constexpr int NA_CFA = 196;
 
-// JSIIA: per-link TA entries (right-hand side 1, h_i = I^c_i e_1 6, pad 1) and
-// n*n TA entries (M).
+// JSIIA: per-link TA entries (right-hand side 1, h_i = I^c_i e_1 6, the second
+// right-hand side of MODE_FD2 1) and n*n TA entries (M).
 constexpr int NA_JSIIA = 8;
 constexpr int NSQ_JSIIA = 1;
 
-// ABIA: per-link TA entries: h_i = P_i S_i (6), 1 / D_i (1), u_i / D_i (1).
+// ABIA: per-link TA entries: h_i = P_i S_i (6), 1 / D_i (1), u_i / D_i (1), and
+// u_i / D_i of the second right-hand side (MODE_FD2).
 constexpr int A_H = 0;
 constexpr int A_DD = 6;
 constexpr int A_UU = 7;
-constexpr int NA_ABIA = 8;
+constexpr int A_UU2 = 8;
+constexpr int NA_ABIA = 9;
 
 // Adjoint (reverse inverse dynamics) per-link workspace of T.
 constexpr int J_G = 0;    // g_i (12)
@@ -74,6 +82,8 @@ constexpr int NT_ADJ = 48;
 constexpr int MODE_FD = 0;      // tau_delta = tau - ID(q, qd, 0)
 constexpr int MODE_ID = 1;      // tau = ID(q, qd, qdd)
 constexpr int MODE_LINEAR = 2;  // tau_delta = in3 (solve M x = in3: joint transforms only)
+constexpr int MODE_FD2 = 3;     // MODE_FD into out, and M^{-1} in4 into out4 with the same
+                                // factorisation (the adjoint's linear solve beside FD)
 
 struct KArgs {
   const void *model;         // [L][REC] of T
@@ -96,6 +106,8 @@ struct KArgs {
   const void *lam;  // adjoint: lambda = M^{-1} qdd_bar
   void *out2;       // adjoint: qdot_bar
   void *out3;       // adjoint: mass_bar (or null)
+  const void *in4;  // MODE_FD2: second right-hand side w
+  void *out4;       // MODE_FD2: M^{-1} w
 };
 
 }  // namespace fdk

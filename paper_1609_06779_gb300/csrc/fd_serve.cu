@@ -124,7 +124,6 @@ struct Arena {
   double *ws_r;                                     // [cap][NT_ADJ]  reverse sweep
   double *ws_c;                                     // [cap][NA_CFA]  CFA rows
   double *ws_b;                                     // [cap][NA_ABIA] ABIA
-  double *ws_t2, *ws_c2, *ws_b2;                    // the same for the adjoint's linear solves
   double *hist;                                     // rollout torques
   int64_t *r_hist;                                  // per slot: history start
   int32_t *r_step, *r_steps;                        // per slot: step, total steps
@@ -263,12 +262,11 @@ struct fd_server_s {
   // side streams of a tick: one per CFA team class and one for ABIA; a request's
   // launches (FD, the linear solve of its adjoint, the reverse sweep) stay on one
   // of them, in order, and the classes run concurrently
-  // streams 0..5: FD and reverse sweep per class; 6..11: the same classes' linear
-  // solves of the adjoint (lambda = M^-1 w needs q only, so it runs beside FD on
-  // its own workspaces), joined into the class stream before the reverse sweep
-  static constexpr int kClass = 6, kAux = 2 * kClass;
+  // one side stream per class: FD (with the adjoint's linear solve in the same
+  // elimination for FD+gradient requests) and then the reverse sweep, in order
+  static constexpr int kAux = 6;
   cudaStream_t aux[kAux] = {};
-  cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {}, ev_lin[kClass] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
 
   RangeAlloc slots, recs, hist;
   std::unordered_map<int, Model> models;
@@ -452,7 +450,7 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
   if (e == cudaSuccess) e = cudaEventRecord(S->ev_fork, S->stream);
   for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k)
     e = cudaStreamWaitEvent(S->aux[k], S->ev_fork, 0);
-  auto fd_launch = [&](int algo, int mode, const double *in3, double *out, int p0, int cnt) {
+  auto fd_launch = [&](int algo, int mode, int p0, int cnt) {
     const TeamKind k = algo == FD_CFA ? kTeamCFA : kTeamABIA;
     return over(S, all, p0, cnt, k, [&](int s, int c, int t) {
       fdk::KArgs a = base_args(S);
@@ -461,32 +459,25 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       a.n_problems = c;
       a.q = S->A.q;
       a.qd = S->A.qd;
-      a.in3 = in3;
-      a.out = out;
+      a.in3 = S->A.tau;
+      a.out = S->A.qdd;
+      a.in4 = S->A.w;     // MODE_FD2: lambda = M^-1 w beside qdd
+      a.out4 = S->A.tbar;
       a.mode = mode;
-      a.status = mode == fdk::MODE_FD ? S->d_status + s : nullptr;
+      a.status = S->d_status + s;
       a.team = t;
-      const bool lin = mode == fdk::MODE_LINEAR;
-      cudaStream_t st = S->aux[aux_of(algo != FD_CFA, all[s]->n) + (lin ? fd_server_s::kClass : 0)];
-      if (lin) {
-        a.ws_t = S->A.ws_t2;
-        a.ws_a = algo == FD_CFA ? S->A.ws_c2 : S->A.ws_b2;
-      } else {
-        a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
-      }
+      cudaStream_t st = S->aux[aux_of(algo != FD_CFA, all[s]->n)];
+      a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
       if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, st);
       return fdk::launch_abia(a, 0, t, st);
     });
   };
-  if (e == cudaSuccess)
-    e = fd_launch(FD_CFA, fdk::MODE_FD, S->A.tau, S->A.qdd, gstart[0], gstart[2] - gstart[0]);
-  if (e == cudaSuccess)
-    e = fd_launch(FD_ABIA, fdk::MODE_FD, S->A.tau, S->A.qdd, gstart[2], gstart[4] - gstart[2]);
-  // adjoint of the FD+gradient requests: lambda = M^-1 w, then the reverse sweep
-  if (e == cudaSuccess)
-    e = fd_launch(FD_CFA, fdk::MODE_LINEAR, S->A.w, S->A.tbar, gstart[0], gstart[1] - gstart[0]);
-  if (e == cudaSuccess)
-    e = fd_launch(FD_ABIA, fdk::MODE_LINEAR, S->A.w, S->A.tbar, gstart[2], gstart[3] - gstart[2]);
+  // FD+gradient requests: qdd and lambda = M^-1 w in one elimination (MODE_FD2);
+  // rollouts: qdd
+  if (e == cudaSuccess) e = fd_launch(FD_CFA, fdk::MODE_FD2, gstart[0], gstart[1] - gstart[0]);
+  if (e == cudaSuccess) e = fd_launch(FD_CFA, fdk::MODE_FD, gstart[1], gstart[2] - gstart[1]);
+  if (e == cudaSuccess) e = fd_launch(FD_ABIA, fdk::MODE_FD2, gstart[2], gstart[3] - gstart[2]);
+  if (e == cudaSuccess) e = fd_launch(FD_ABIA, fdk::MODE_FD, gstart[3], gstart[4] - gstart[3]);
   auto reverse = [&](int p0, int cnt, bool abia) {
     return over(S, all, p0, cnt, kTeamReverse, [&](int s, int c, int t) {
       fdk::KArgs a = base_args(S);
@@ -505,10 +496,6 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       return fdk::launch_adjoint_rnea(a, 0, t, S->aux[aux_of(abia, all[s]->n)]);
     });
   };
-  for (int k = 0; k < fd_server_s::kClass && e == cudaSuccess; ++k) {
-    e = cudaEventRecord(S->ev_lin[k], S->aux[fd_server_s::kClass + k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->aux[k], S->ev_lin[k], 0);
-  }
   if (e == cudaSuccess) e = reverse(gstart[0], gstart[1] - gstart[0], false);
   if (e == cudaSuccess) e = reverse(gstart[2], gstart[3] - gstart[2], true);
   for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k) {
@@ -617,7 +604,7 @@ void worker_main(fd_server_s *S) {
 
 size_t per_link_bytes() {
   return 8 * sizeof(double) +
-         (2 * (fdk::NT + fdk::NA_CFA + fdk::NA_ABIA) + fdk::NT_ADJ) * sizeof(double) +
+         (fdk::NT + fdk::NA_CFA + fdk::NA_ABIA + fdk::NT_ADJ) * sizeof(double) +
          sizeof(int64_t) + 2 * sizeof(int32_t) + sizeof(double) +
          2 * sizeof(int32_t) + 3 * sizeof(int64_t);
 }
@@ -629,8 +616,7 @@ void destroy_streams(fd_server_s *S) {
     if (S->aux[k]) cudaStreamDestroy(S->aux[k]);
     if (S->ev_join[k]) cudaEventDestroy(S->ev_join[k]);
   }
-  for (int k = 0; k < fd_server_s::kClass; ++k)
-    if (S->ev_lin[k]) cudaEventDestroy(S->ev_lin[k]);
+
   if (S->ev_fork) cudaEventDestroy(S->ev_fork);
   if (S->stream) cudaStreamDestroy(S->stream);
 }
@@ -678,8 +664,7 @@ fd_status fd_serve_create(int32_t device, size_t mem_budget_bytes, const double 
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_join[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming);
-  for (int k = 0; k < fd_server_s::kClass && e == cudaSuccess; ++k)
-    e = cudaEventCreateWithFlags(&S->ev_lin[k], cudaEventDisableTiming);
+
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -707,9 +692,7 @@ fd_status fd_serve_create(int32_t device, size_t mem_budget_bytes, const double 
   S->A.ws_r = reinterpret_cast<double *>(take(size_t(C) * fdk::NT_ADJ * 8));
   S->A.ws_c = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_CFA * 8));
   S->A.ws_b = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_ABIA * 8));
-  S->A.ws_t2 = reinterpret_cast<double *>(take(size_t(C) * fdk::NT * 8));
-  S->A.ws_c2 = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_CFA * 8));
-  S->A.ws_b2 = reinterpret_cast<double *>(take(size_t(C) * fdk::NA_ABIA * 8));
+
   S->A.r_hist = reinterpret_cast<int64_t *>(take(size_t(C) * 8));
   S->A.r_step = reinterpret_cast<int32_t *>(take(size_t(C) * 4));
   S->A.r_steps = reinterpret_cast<int32_t *>(take(size_t(C) * 4));

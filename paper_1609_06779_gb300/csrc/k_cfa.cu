@@ -9,8 +9,22 @@ cudaError_t launch_cfa_mixed(const KArgs &a, int team, cudaStream_t s);
 cudaError_t launch_cfa_cr_f64(const KArgs &a, int team, cudaStream_t s);
 cudaError_t launch_cfa_cr_f32(const KArgs &a, int team, cudaStream_t s);
 cudaError_t launch_cfa_cr_mixed(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa2_f64(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa2_f32(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa2_mixed(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa_cr2_f64(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa_cr2_f32(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa_cr2_mixed(const KArgs &a, int team, cudaStream_t s);
 
 cudaError_t launch_cfa(const KArgs &a, int prec, int team, cudaStream_t s) {
+  if (a.mode == MODE_FD2) {
+    switch (prec) {
+      case 0: return launch_cfa2_f64(a, team, s);
+      case 1: return launch_cfa2_f32(a, team, s);
+      case 2: return launch_cfa2_mixed(a, team, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (prec) {
     case 0: return launch_cfa_f64(a, team, s);
     case 1: return launch_cfa_f32(a, team, s);
@@ -20,6 +34,14 @@ cudaError_t launch_cfa(const KArgs &a, int prec, int team, cudaStream_t s) {
 }
 
 cudaError_t launch_cfa_cr(const KArgs &a, int prec, int team, cudaStream_t s) {
+  if (a.mode == MODE_FD2) {
+    switch (prec) {
+      case 0: return launch_cfa_cr2_f64(a, team, s);
+      case 1: return launch_cfa_cr2_f32(a, team, s);
+      case 2: return launch_cfa_cr2_mixed(a, team, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (prec) {
     case 0: return launch_cfa_cr_f64(a, team, s);
     case 1: return launch_cfa_cr_f32(a, team, s);

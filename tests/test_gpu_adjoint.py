@@ -89,6 +89,33 @@ def test_adjoint_reuses_forward_result_and_algorithms_agree():
             assert np.abs(x - y).max() <= 1e-8 * max(np.abs(y).max(), 1.0), algo
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_shared_elimination_equals_separate_solves(prec):
+    """Without a given qdd the adjoint solves FD and lambda = M^-1 w in one
+    elimination (two right-hand sides); the results equal a separate FD solve and
+    the adjoint given that qdd (one linear solve) bitwise, for every algorithm
+    and for scan and component-lane teams."""
+    from paper_1609_06779_gb300 import fd
+    model = synth.random_chains([1, 5, 20, 33, 70, 32, 32], seed=61)
+    st = synth.random_states(model.n_links_total, seed=62)
+    w = np.random.default_rng(63).standard_normal(model.n_links_total)
+    cs = fd.ChainSet(model)
+    b = fd.Batch(cs)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    q, qd, tau, wt = t(st.q), t(st.qdot), t(st.tau), t(w)
+    for algo, team in (("abia", 1), ("abia", 8), ("abia", 16), ("jsiia", 2), ("jsiia", 8),
+                       ("cfa", 8), ("cfa", 64), ("cfa_cr", 4)):
+        qdd = fd.solve(b, q, qd, tau, algo=algo, prec=prec, team=team)
+        one = fd.adjoint(b, q, qd, tau, wt, algo=algo, prec=prec, team=team, masses=False)
+        two = fd.adjoint(b, q, qd, tau, wt, qdd=qdd, algo=algo, prec=prec, team=team,
+                         masses=False)
+        for k, (x, y) in enumerate(zip(one, two)):
+            if x is None:
+                continue
+            assert torch.equal(x, y), (algo, team, k)
+
+
 def test_autograd_function_gradcheck_direction():
     """torch.autograd through forward_dynamics: directional derivative of
     <w, qdd> along a random unit direction equals Richardson-extrapolated central
