@@ -669,7 +669,10 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
     r.out3 = mass_bar;
     r.ws_t = region;
     r.status = nullptr;
-    const int tr = algo == FD_ABIA ? resolve_team(b, FD_CFA, prec, 0) : t;
+    // the reverse sweep: component lanes (team 8) for chains of up to 64 links,
+    // else the algorithm's team (ABIA's serial team 1 would scan nothing)
+    const int tr = b->max_links <= 64 ? std::max(t, 8) > 32 ? 32 : std::max(t, 8)
+                   : (algo == FD_ABIA ? resolve_team(b, FD_CFA, prec, 0) : t);
     r.team = tr;
     e = fdk::launch_adjoint_rnea(r, prec == FD_FP64 ? 0 : 1, tr, s);
   }

@@ -56,6 +56,138 @@ __device__ __forceinline__ void dJdm_apply(const T *J, const T *x, T *y) {
   y[5] = -cxw[2] + x[5];
 }
 
+// The same six recursions on component lanes (teams of 8..32, chains up to the
+// inverse dynamics' component-lane length): lanes 0..5 carry the six
+// components; the three forward recursions (V, A, Fbar) run in one serial loop
+// over the links and the three backward ones (F, Abar, Vbar) in another, one
+// transport per recursion per lane per link, while every term that does not
+// recur (joint transforms, f_i, J_i Fbar_i, the Vbar term without Abar, and the
+// gradients) runs one link per lane. Returns after writing the outputs.
+template <class T, int P>
+__device__ __forceinline__ void adjoint_lanes(const Team<P> &tm, const Prob<T> &pb,
+                                              const KArgs &A, const T *lam, T *qbar, T *qdbar,
+                                              T *mbar) {
+  const int n = pb.n;
+  const int r = tm.r < 6 ? tm.r : 5;
+  const bool top = r < 3;
+  const int k = top ? r : r - 3;
+  const int ka = k == 2 ? 0 : k + 1, kb = k == 0 ? 2 : k - 1;  // k+1, k+2 mod 3
+  const bool store = tm.r < 6;
+  auto W = [&](int i) { return pb.wt + static_cast<int64_t>(i) * NT_ADJ; };
+  auto REC_ = [&](int i) { return pb.rec + static_cast<int64_t>(i) * REC; };
+
+  // joint transforms and R^T p, one link per lane
+  for (int i = tm.r; i < n; i += P) {
+    SE3<T> g;
+    joint_transform(REC_(i), pb.q[i], g);
+    st_se3(W(i) + J_G, g);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      W(i)[J_PT + j] = g.R[j] * g.p[0] + g.R[3 + j] * g.p[1] + g.R[6 + j] * g.p[2];
+  }
+  tm.sync();
+
+  // component k of Ad_{g^-1} x: R^T w (top), R^T v + (R^T w) x (R^T p) (bottom)
+  auto fwd_c = [&](const T *x, T c0, T c1, T c2, T pa, T pbk) {
+    const T t = top ? c0 * x[0] + c1 * x[1] + c2 * x[2] : c0 * x[3] + c1 * x[4] + c2 * x[5];
+    const T oa = __shfl_sync(tm.mask, t, ka, P), ob = __shfl_sync(tm.mask, t, kb, P);
+    return top ? t : (t + oa * pbk) - ob * pa;
+  };
+  // component k of Ad_{g^-1}^T y: R n + p x R f (top), R f (bottom)
+  auto bwd_c = [&](const T *y, T c0, T c1, T c2, T pa, T pbk) {
+    const T t = top ? c0 * y[0] + c1 * y[1] + c2 * y[2] : c0 * y[3] + c1 * y[4] + c2 * y[5];
+    const T fa = __shfl_sync(tm.mask, t, 3 + ka, P), fb = __shfl_sync(tm.mask, t, 3 + kb, P);
+    return top ? (t + pa * fb) - pbk * fa : t;
+  };
+  auto gather = [&](T v, T *full) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) full[j] = __shfl_sync(tm.mask, v, j, P);
+  };
+
+  // forward: V (Eq. 2a), A (Eq. 2b at qdd = in3), Fbar_i = X_i Fbar_{i-1} + e_1 lambda_i
+  {
+    T V[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T Ac[6] = {T(0), T(0), T(0), T(-A.grav[0]), T(-A.grav[1]), T(-A.grav[2])};
+    T Fb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    for (int i = 0; i < n; ++i) {
+      T *w = W(i);
+      const T c0 = w[J_G + k], c1 = w[J_G + 3 + k], c2 = w[J_G + 6 + k];
+      const T pa = w[J_PT + ka], pbk = w[J_PT + kb];
+      const T qdi = pb.qd[i];
+      T y = fwd_c(V, c0, c1, c2, pa, pbk) + (r == 0 ? qdi : T(0));
+      gather(y, V);
+      if (store) w[J_V + r] = y;
+      const T cv = r == 1 ? V[2] : (r == 2 ? -V[1] : (r == 4 ? V[5] : (r == 5 ? -V[4] : T(0))));
+      y = fwd_c(Ac, c0, c1, c2, pa, pbk) + cv * qdi + (r == 0 ? pb.in3[i] : T(0));
+      gather(y, Ac);
+      if (store) w[J_A + r] = y;
+      y = fwd_c(Fb, c0, c1, c2, pa, pbk) + (r == 0 ? lam[i] : T(0));
+      gather(y, Fb);
+      if (store) w[J_FB + r] = y;
+    }
+  }
+  tm.sync();
+
+  // terms that do not recur, one link per lane: f_i (into J_F), J_i Fbar_i (into
+  // J_AB), ad_{Fbar_i}^T (J_i V_i) - J_i ad_{V_i} Fbar_i (into J_VB)
+  for (int i = tm.r; i < n; i += P) {
+    T *w = W(i);
+    const T *J = REC_(i) + REC_J;
+    T V[6], Ai[6], Fb[6], JV[6], t1[6], t2[6], t3[6];
+    ldv<T, 6>(w + J_V, V);
+    ldv<T, 6>(w + J_A, Ai);
+    ldv<T, 6>(w + J_FB, Fb);
+    sym6_apply(J, V, JV);
+    adT_apply(V, JV, t1);
+    sym6_apply(J, Ai, t2);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) t2[j] -= t1[j];
+    stv<T, 6>(w + J_F, t2);  // f_i
+    sym6_apply(J, Fb, t2);
+    stv<T, 6>(w + J_AB, t2);  // J_i Fbar_i
+    adT_apply(Fb, JV, t1);    // ad_{Fbar}^T (J V)
+    ad_apply(V, Fb, t2);      // ad_V Fbar
+    sym6_apply(J, t2, t3);    // J ad_V Fbar
+#pragma unroll
+    for (int j = 0; j < 6; ++j) t1[j] -= t3[j];
+    stv<T, 6>(w + J_VB, t1);
+  }
+  tm.sync();
+
+  // backward: F_i = X_{i+1}^T F_{i+1} + f_i, Abar_i = X_{i+1}^T Abar_{i+1} + J_i Fbar_i,
+  // Vbar_i = X_{i+1}^T Vbar_{i+1} + (the Vbar term) - qd_i ad_{e_1}^T Abar_i
+  {
+    T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T Ab[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T Vb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    for (int i = n - 1; i >= 0; --i) {
+      T *w = W(i);
+      T yF = w[J_F + r], yA = w[J_AB + r], yV = w[J_VB + r];
+      if (i + 1 < n) {
+        const T *wn = W(i + 1);
+        const T c0 = wn[J_G + 3 * k], c1 = wn[J_G + 3 * k + 1], c2 = wn[J_G + 3 * k + 2];
+        const T pa = wn[J_G + 9 + ka], pbk = wn[J_G + 9 + kb];
+        yF += bwd_c(F, c0, c1, c2, pa, pbk);
+        yA += bwd_c(Ab, c0, c1, c2, pa, pbk);
+        yV += bwd_c(Vb, c0, c1, c2, pa, pbk);
+      }
+      gather(yF, F);
+      gather(yA, Ab);
+      // - qd ad_{e_1}^T Abar = qd (0, -n_z, n_y; 0, -f_z, f_y)
+      const T qdi = pb.qd[i];
+      const T ca = r == 1 ? -Ab[2] : (r == 2 ? Ab[1] : (r == 4 ? -Ab[5] : (r == 5 ? Ab[4] : T(0))));
+      yV += qdi * ca;
+      gather(yV, Vb);
+      if (store) {
+        w[J_F + r] = yF;
+        w[J_AB + r] = yA;
+        w[J_VB + r] = yV;
+      }
+    }
+  }
+  tm.sync();
+}
+
 template <class T, int P>
 __global__ void __launch_bounds__(block_for<P>()) adjoint_rnea_kernel(KArgs A) {
   Team<P> tm;
@@ -69,7 +201,11 @@ __global__ void __launch_bounds__(block_for<P>()) adjoint_rnea_kernel(KArgs A) {
   T *mbar = A.out3 ? static_cast<T *>(A.out3) + s0 : nullptr;
   auto W = [&](int i) { return pb.wt + static_cast<int64_t>(i) * NT_ADJ; };
   auto REC_ = [&](int i) { return pb.rec + static_cast<int64_t>(i) * REC; };
-
+  bool lanes = false;
+  if constexpr (P >= 8 && P <= 32) lanes = pb.n <= lanes_id_max_links<P>();
+  if (lanes) {
+    adjoint_lanes<T, P>(tm, pb, A, lam, qbar, qdbar, mbar);
+  } else {
   SegOp<T> op;
   se3_identity(op.h);
   for (int i = a; i < b; ++i) {
@@ -193,8 +329,10 @@ __global__ void __launch_bounds__(block_for<P>()) adjoint_rnea_kernel(KArgs A) {
     l[4] = t1[4] - t3[4] - qdi * Ab[5];
     l[5] = t1[5] - t3[5] + qdi * Ab[4];
   });
+  }
 
-  for (int i = a; i < b; ++i) {
+  const int g0 = lanes ? tm.r : a, g1 = lanes ? pb.n : b, gs = lanes ? P : 1;
+  for (int i = g0; i < g1; i += gs) {
     const T *w = W(i);
     T V[6], Ai[6], F[6], Fb[6], Ab[6], Vb[6];
     ldv<T, 6>(w + J_V, V);

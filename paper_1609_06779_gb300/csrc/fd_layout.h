@@ -76,7 +76,8 @@ constexpr int J_F = 24;   // F_i
 constexpr int J_FB = 30;  // Fbar_i (f_i before the force pass)
 constexpr int J_AB = 36;  // Abar_i
 constexpr int J_VB = 42;  // Vbar_i
-constexpr int NT_ADJ = 48;
+constexpr int J_PT = 48;  // R^T p of g_i (component-lane sweeps)
+constexpr int NT_ADJ = 52;
 
 // id_team modes (a zero-initialised KArgs means forward dynamics)
 constexpr int MODE_FD = 0;      // tau_delta = tau - ID(q, qd, 0)
