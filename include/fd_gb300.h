@@ -237,8 +237,8 @@ fd_status fd_solve_adjoint(fd_batch_t batch, const void *q, const void *qdot, co
  * qddot (output) are device arrays of the chain set's total link count, packed
  * in chain order, double for FD_FP64 and float for FD_FP32 / FD_MIXED. team and
  * status as for fd_solve_batch. Limits: at most 65 536 chains, and the CFA
- * workspace of all links must fit in 32 MiB - 256 KiB (FD_FP64: 1 184 bytes per
- * link, about 28 000 links; FD_FP32 / FD_MIXED: about 31 000 links); larger sets
+ * workspace of all links must fit in 32 MiB - 256 KiB (FD_FP64: 1 824 bytes per
+ * link, about 18 000 links; FD_MIXED about 19 000; FD_FP32 about 36 000); larger sets
  * return FD_ERR_INVALID_ARG with the sizes in fd_last_error().
  *
  * The first call on a device looks up the array's device address with

@@ -14,8 +14,9 @@
 namespace {
 
 // 32 MiB per device: a 256 KiB problem -> chain map (identity) followed by the
-// CFA workspace. At FP64 the workspace needs 1 184 bytes per link (about 28 000
-// links); at FP32 / mixed 128 + 928 bytes per link (about 31 000 links).
+// CFA workspace. At FP64 the workspace needs 32 x 8 + 196 x 8 = 1 824 bytes per
+// link (about 18 000 links); mixed 32 x 4 + 196 x 8 = 1 696 (about 19 000);
+// FP32 32 x 4 + 196 x 4 = 912 (about 36 000).
 constexpr size_t kScratchBytes = size_t(32) << 20;
 constexpr int kMaxProblems = 1 << 16;
 constexpr size_t kMapBytes = size_t(kMaxProblems) * sizeof(int32_t);
