@@ -175,7 +175,7 @@ __device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, c
 // Leaves g_i, V_i, f_i in the workspace.
 template <class T, int P>
 __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, const double *grav,
-                                        int mode) {
+                                        int mode, bool skip_force = false) {
   if constexpr (P >= 8 && P <= 32) {
     if (pb.n <= lanes_id_max_links<P>()) {
       id_lanes<T, P>(tm, pb, grav, mode);
@@ -259,7 +259,9 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
     stv<T, 6>(w + W_F, JA);
   }
 
-  // ---- force: F_i = Ad_{g_{i+1}^{-1}}^T F_{i+1} + f_i, F_n = 0 (Eq. 2c), tau = S^T F (2d)
+  // ---- force: F_i = Ad_{g_{i+1}^{-1}}^T F_{i+1} + f_i, F_n = 0 (Eq. 2c), tau = S^T F (2d);
+  // skip_force (serial schedule only) leaves f_i in W_F for the caller's own backward loop
+  if (P == 1 && skip_force) return;
   T y[6];
   if (P > 1) {
     for (int k = 0; k < 6; ++k) y[k] = T(0);
@@ -1276,23 +1278,40 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
   const int n = pb.n;
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_ABIA;
   bool bad = false;
-  id_team<T, 1>(tm, pb, A.grav, A.mode);
+  // inverse dynamics up to f_i; its force pass runs inside the backward loop below,
+  // beside the articulated-inertia step of the same link (two independent
+  // recursions sharing g_i)
+  const bool linear = A.mode == MODE_LINEAR;
+  id_team<T, 1>(tm, pb, A.grav, A.mode, true);
   const T *td2 = TWO ? static_cast<const T *>(A.in4) + A.state_off[pb.p] : nullptr;
   T *out2 = TWO ? static_cast<T *>(A.out4) + A.state_off[pb.p] : nullptr;
   TA pbias2[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
 
   TA Pm[21], pbias[6];
+  T Fy[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};  // force recursion F_{i+1} transported
   if (n > 0) {
     const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
     for (int k = 0; k < 21; ++k) Pm[k] = TA(J[k]);
   }
   for (int k = 0; k < 6; ++k) pbias[k] = TA(0);
   for (int i = n - 1; i >= 0; --i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    SE3<T> g;
+    ld_se3(w + W_G, g);
+    // tau_delta_i: the force pass F_i = X_{i+1}^T F_{i+1} + f_i, tau_i = F_i[0]
+    T tdi;
+    if (linear) {
+      tdi = w[W_TD];
+    } else {
+      for (int k = 0; k < 6; ++k) Fy[k] += w[W_F + k];
+      tdi = pb.in3[i] - Fy[0];
+      adinvT(g, Fy, Fy);
+    }
     TA *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
     TA h[6];
     for (int k = 0; k < 6; ++k) h[k] = Pm[s6(0, k)];
     const TA D = h[0];
-    const TA u = TA(pb.wt[static_cast<int64_t>(i) * NT + W_TD]) - pbias[0];
+    const TA u = TA(tdi) - pbias[0];
     bad |= !(D > TA(0));
     const TA Dinv = TA(1) / D;
     for (int k = 0; k < 6; ++k) ra[A_H + k] = h[k];
@@ -1314,8 +1333,6 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     if constexpr (TWO) {
       for (int k = 0; k < 6; ++k) pa2[k] = pbias2[k] + hs[k] * u2;
     }
-    SE3<T> g;
-    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
     SE3<TA> ga;
     for (int c = 0; c < 9; ++c) ga.R[c] = TA(g.R[c]);
     for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
