@@ -591,7 +591,7 @@ def main():
     hbm_gbs = alg_bytes / (per_algo_ms[dom] / 1e3) / 1e9
     roof = {"bound": "alu", "achieved": rl[dom]["tflops"], "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": rl[dom]["frac"], "traffic": traffic,
-            "kernel": f"{dom}_kernel<double,double,{teams[dom]}>",
+            "kernel": f"{dom}_kernel, team {teams[dom]}, FP64",
             "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s), not measured",
             "algorithmic_flops_per_launch": roofline.flops(dom, lengths),
             "algorithmic_bytes_per_launch": alg_bytes,

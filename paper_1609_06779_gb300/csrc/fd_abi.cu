@@ -696,8 +696,13 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
   int cap = 1;
   while (cap < b->max_links && cap < 256) cap *= 2;
   std::vector<int> cand;
-  for (int t = 1; t <= cap; t *= 2)
-    if (algo != FD_ABIA || fdk::abia_team_ok(t)) cand.push_back(t);
+  if (algo == FD_ABIA) {
+    // ABIA's lane teams spread each step's 6x6 update over 6 or 12 lanes, which
+    // pays even for chains shorter than the team
+    for (int t : {1, 8, 16, 32}) cand.push_back(t);
+  } else {
+    for (int t = 1; t <= cap; t *= 2) cand.push_back(t);
+  }
   if (b->n_problems == 0 || b->n_state_links == 0) {
     if (best_team) *best_team = 1;
     return FD_OK;
