@@ -618,6 +618,24 @@ def main():
                                    "tflops": fl / (ms * 1e-3) / 1e12,
                                    "frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
         del wcr, ocr
+        # inverse dynamics alone (fd_inverse_dynamics, the scans of Eq. 2a-2d) and the
+        # adjoint (FD and M^-1 w in one elimination, then the reverse sweep) of CFA
+        for team in (8,):
+            wid = fd.workspace(batch, None, "fp64", team, dev)
+            oid = torch.empty_like(q)
+            ms = _time_ms(lambda: fd.inverse_dynamics(batch, q, qd, out["cfa"], team=team,
+                                                      out=oid, ws=wid), reps=5, warm=2)
+            fl = roofline.flops("id", lengths)
+            variants["inverse_dynamics_fp64"] = {"team": team, "ms": ms,
+                                                 "solves_per_s": args.chains / (ms * 1e-3),
+                                                 "tflops": fl / (ms * 1e-3) / 1e12}
+            del wid, oid
+        wb = torch.randn_like(q)
+        ms = _time_ms(lambda: fd.adjoint(batch, q, qd, tau, wb, algo="cfa", team=teams["cfa"],
+                                         masses=False), reps=3, warm=1)
+        variants["adjoint_cfa_fp64"] = {"team": teams["cfa"], "ms": ms,
+                                        "solves_per_s": args.chains / (ms * 1e-3)}
+        del wb
     # FP32 and mixed variants of each algorithm (context; not part of the step)
     if rank == 0:
         q32, qd32, tau32 = (x.float() for x in (q, qd, tau))
