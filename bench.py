@@ -636,6 +636,25 @@ def main():
         variants["adjoint_cfa_fp64"] = {"team": teams["cfa"], "ms": ms,
                                         "solves_per_s": args.chains / (ms * 1e-3)}
         del wb
+        # the step's three launches on three streams forked from and joined to the
+        # launching stream: the GPU fills one kernel's tail with the others' blocks
+        side = [torch.cuda.Stream(dev) for _ in ALGOS]
+
+        def step3():
+            fork = torch.cuda.Event()
+            fork.record(stream)
+            for s, a in zip(side, ALGOS):
+                s.wait_event(fork)
+                fd.solve(batch, q, qd, tau, algo=a, prec="fp64", team=teams[a], out=out[a],
+                         ws=ws[a], stream=s)
+            for s in side:
+                join = torch.cuda.Event()
+                join.record(s)
+                stream.wait_event(join)
+
+        ms = _time_ms(step3, reps=5, warm=2)
+        variants["step_three_streams_fp64"] = {"ms": ms,
+                                               "solves_per_s": 3 * args.chains / (ms * 1e-3)}
     # FP32 and mixed variants of each algorithm (context; not part of the step)
     if rank == 0:
         q32, qd32, tau32 = (x.float() for x in (q, qd, tau))

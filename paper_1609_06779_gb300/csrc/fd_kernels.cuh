@@ -167,6 +167,131 @@ __device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, c
 }
 
 
+// Eq. 2a-2c for a team of two: the angular half of every twist, acceleration and
+// force on lane 0, the linear half on lane 1, one half-transport per lane per link
+// (nine rotation products, and the cross-product term with the other half taken
+// by shuffle), against a whole transport per link on each lane for the scans at
+// this team size. Joint transforms and f_i, which do not recur, run one link per
+// lane. Same outputs as the scans (W_G, W_TD; V_i in W_V, f_i in W_F), visible to
+// both lanes on return.
+template <class T, int P>
+__device__ __forceinline__ void id_pair(const Team<P> &tm, const Prob<T> &pb, const double *grav,
+                                        int mode) {
+  static_assert(P == 2, "the component pair is a team of two lanes");
+  const int n = pb.n;
+  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2;
+  const bool h = tm.r != 0;  // false: components 0..2, true: 3..5
+  auto xch = [&](T v) { return __shfl_xor_sync(tm.mask, v, 1); };
+
+  // joint transforms and R^T p, one link per lane
+  for (int i = tm.r; i < n; i += P) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    SE3<T> g;
+    joint_transform(pb.rec + static_cast<int64_t>(i) * REC, pb.q[i], g);
+    st_se3(w + W_G, g);
+    if (mode == MODE_LINEAR) {
+      w[W_TD] = pb.in3[i];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        w[W_PT + j] = g.R[j] * g.p[0] + g.R[3 + j] * g.p[1] + g.R[6 + j] * g.p[2];
+    }
+  }
+  tm.sync();
+  if (mode == MODE_LINEAR) return;
+
+  // twist V_i (Eq. 2a) and acceleration Vd_i (Eq. 2b), forward; Vd_i parks in W_F.
+  // (Ad_{g^-1} x) = (R^T w; R^T v + R^T w x R^T p): this lane's half of R^T x, and on
+  // the linear lane the cross product with the angular lane's half.
+  T x[3] = {T(0), T(0), T(0)};                                   // this lane's half of V
+  T ax[3] = {h ? T(-grav[0]) : T(0), h ? T(-grav[1]) : T(0), h ? T(-grav[2]) : T(0)};
+  for (int i = 0; i < n; ++i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    T R[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = w[W_G + k];
+    const T pt0 = h ? w[W_PT] : T(0), pt1 = h ? w[W_PT + 1] : T(0), pt2 = h ? w[W_PT + 2] : T(0);
+    const T qdi = pb.qd[i];
+    // twist
+    T t[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = R[k] * x[0] + R[3 + k] * x[1] + R[6 + k] * x[2];
+    T o[3];  // the angular lane's R^T w on the linear lane
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = xch(t[k]);
+    x[0] = ((h ? t[0] : t[0] + qdi) + o[1] * pt2) - o[2] * pt1;
+    x[1] = (t[1] + o[2] * pt0) - o[0] * pt2;
+    x[2] = (t[2] + o[0] * pt1) - o[1] * pt0;
+    // the whole V_i for the acceleration's ad_{V_i} e_1 qd_i = (0, w_z, -w_y; 0, v_z, -v_y) qd_i
+    const T v1 = x[1], v2 = x[2];
+    if (tm.r < 2) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w[W_V + (h ? 3 : 0) + k] = x[k];
+    }
+    // acceleration
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = R[k] * ax[0] + R[3 + k] * ax[1] + R[6 + k] * ax[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = xch(t[k]);
+    const T a0 = (!h && !mode_fd) ? pb.in3[i] : T(0);
+    ax[0] = ((t[0] + a0) + o[1] * pt2) - o[2] * pt1;
+    ax[1] = ((t[1] + o[2] * pt0) - o[0] * pt2) + v2 * qdi;
+    ax[2] = ((t[2] + o[0] * pt1) - o[1] * pt0) - v1 * qdi;
+    if (tm.r < 2) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w[W_F + (h ? 3 : 0) + k] = ax[k];
+    }
+  }
+  tm.sync();
+
+  // f_i = J_i Vd_i - ad_{V_i}^T J_i V_i, one link per lane
+  for (int i = tm.r; i < n; i += P) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+    T Vi[6], Ai[6], JV[6], f[6];
+    ldv<T, 6>(w + W_V, Vi);
+    ldv<T, 6>(w + W_F, Ai);
+    sym6_apply(rec + REC_J, Vi, JV);
+    adT_apply(Vi, JV, f);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) f[j] = -f[j];
+    sym6_apply_add(rec + REC_J, Ai, f);
+    stv<T, 6>(w + W_F, f);
+  }
+  tm.sync();
+
+  // force F_i = Ad_{g_{i+1}^{-1}}^T F_{i+1} + f_i (Eq. 2c), backward; tau_i = F_i[0] (2d).
+  // (Ad_{g^-1}^T y) = (R n + p x R f; R f): this lane's half of R y, and on the
+  // angular lane the cross product with the linear lane's half.
+  T y[3] = {T(0), T(0), T(0)};
+  for (int i = n - 1; i >= 0; --i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    T f[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = w[W_F + (h ? 3 : 0) + k];
+    if (i + 1 < n) {
+      const T *wn = w + NT;
+      T R[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) R[k] = wn[W_G + k];
+      const T p0 = h ? T(0) : wn[W_G + 9], p1 = h ? T(0) : wn[W_G + 10], p2 = h ? T(0) : wn[W_G + 11];
+      T t[3], o[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t[k] = R[3 * k] * y[0] + R[3 * k + 1] * y[1] + R[3 * k + 2] * y[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o[k] = xch(t[k]);  // R f on the angular lane
+      y[0] = (((t[0] + p1 * o[2]) - p2 * o[1])) + f[0];
+      y[1] = (((t[1] + p2 * o[0]) - p0 * o[2])) + f[1];
+      y[2] = (((t[2] + p0 * o[1]) - p1 * o[0])) + f[2];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) y[k] = f[k];
+    }
+    if (tm.r == 0) w[W_TD] = mode_fd ? pb.in3[i] - y[0] : y[0];
+  }
+  tm.sync();
+}
+
 // Eq. 2a-2d for one problem: the twist and acceleration recursions (forward,
 // block lower bi-diagonal) and the force recursion (backward, block upper
 // bi-diagonal), each as a segmented scan over SE(3)-affine operators.
@@ -181,6 +306,10 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
       id_lanes<T, P>(tm, pb, grav, mode);
       return;
     }
+  }
+  if constexpr (P == 2) {
+    id_pair<T, P>(tm, pb, grav, mode);
+    return;
   }
   const int a = pb.a, b = pb.b;
   const bool mode_fd = mode == MODE_FD || mode == MODE_FD2;
@@ -983,6 +1112,146 @@ __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, T
     for (int c = r; c < 3; ++c) Out[s6(3 + r, 3 + c)] += Cp[r][c];
 }
 
+// The same congruence X^T P X + J on a pair of lanes (h = lane & 1), both holding
+// the whole P: lane 0 rotates A and rows 0, 1 of B, lane 1 rotates C and rows 2, 1
+// of B; they swap halves with shuffles, each forms its rows of B'' and three
+// entries of the top-left block and of C' + J_C, and they swap those. Both lanes
+// end with the whole result in Out: about 117 operations on each lane instead of
+// 201 on one. J is the link's packed inertia (added at the end, since B'' and the
+// top-left block use the bare rotated blocks). Lanes pick their operands with
+// selects, never by a lane-dependent register index.
+template <class TA, class T, int P>
+__device__ __forceinline__ void congruence_pair(const Team<P> &tm, const SE3<TA> &g,
+                                                const TA *P6, const T *J, TA *Out) {
+  const bool h = (tm.r & 1) != 0;
+  const TA *R = g.R, *p = g.p;
+  auto xch = [&](TA v) { return __shfl_xor_sync(tm.mask, v, 1); };
+  // S' = R S R^T of this lane's symmetric block (A or C), upper triangle
+  TA S[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S[k][c] = h ? P6[s6(3 + k, 3 + c)] : P6[s6(k, c)];
+  TA RS[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      RS[r][c] = R[3 * r] * S[0][c] + R[3 * r + 1] * S[1][c] + R[3 * r + 2] * S[2][c];
+  TA Sp[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = r; c < 3; ++c)
+      Sp[r][c] = RS[r][0] * R[3 * c] + RS[r][1] * R[3 * c + 1] + RS[r][2] * R[3 * c + 2];
+  // rows a = (h ? 2 : 0) and 1 of B' = R B R^T
+  TA Ra[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Ra[k] = h ? R[6 + k] : R[k];
+  TA RBa[3], RBb[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    RBa[c] = Ra[0] * P6[s6(0, 3 + c)] + Ra[1] * P6[s6(1, 3 + c)] + Ra[2] * P6[s6(2, 3 + c)];
+    RBb[c] = R[3] * P6[s6(0, 3 + c)] + R[4] * P6[s6(1, 3 + c)] + R[5] * P6[s6(2, 3 + c)];
+  }
+  TA Bpa[3], Bp1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Bpa[c] = RBa[0] * R[3 * c] + RBa[1] * R[3 * c + 1] + RBa[2] * R[3 * c + 2];
+    Bp1[c] = RBb[0] * R[3 * c] + RBb[1] * R[3 * c + 1] + RBb[2] * R[3 * c + 2];
+  }
+  // swap: A', C' and B' whole on both lanes
+  TA Ap[3][3], Cp[3][3], Bp[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = r; c < 3; ++c) {
+      const TA o = xch(Sp[r][c]);
+      Ap[r][c] = h ? o : Sp[r][c];
+      Cp[r][c] = h ? Sp[r][c] : o;
+      Ap[c][r] = Ap[r][c];
+      Cp[c][r] = Cp[r][c];
+    }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const TA o = xch(Bpa[c]);
+    Bp[0][c] = h ? o : Bpa[c];
+    Bp[1][c] = Bp1[c];
+    Bp[2][c] = h ? Bpa[c] : o;
+  }
+  // rows a and 1 of B'' = B' + p^ C', (p^ C')_rc = p_{r+1} C'_{r+2,c} - p_{r+2} C'_{r+1,c}
+  const TA pu = h ? p[0] : p[1], pv = h ? p[1] : p[2];
+  TA Bqa[3], Bq1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const TA xa = h ? Cp[1][c] : Cp[2][c], xb = h ? Cp[0][c] : Cp[1][c];
+    Bqa[c] = (Bpa[c] + pu * xa) - pv * xb;
+    Bq1[c] = (Bp1[c] + p[2] * Cp[0][c]) - p[0] * Cp[2][c];
+  }
+  TA Bq[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const TA o = xch(Bqa[c]);
+    Bq[0][c] = h ? o : Bqa[c];
+    Bq[1][c] = Bq1[c];
+    Bq[2][c] = h ? Bqa[c] : o;
+  }
+  // this lane's entries of the upper triangles of the top-left block and of C:
+  // lane 0 (0,0) (0,1) (0,2), lane 1 (1,1) (1,2) (2,2);
+  // top left (r, c) = A'_rc + (p x b'_r)_c + (p x b''_c)_r + J_rc
+  TA tl[3], cn[3], bn[3], b1[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int ra = 0, ca = e, rb = e == 2 ? 2 : 1, cb = e == 0 ? 1 : 2;
+    const TA a_rc = h ? Ap[rb][cb] : Ap[ra][ca];
+    // (p x b'_r)_c = p_{c+1} B'_{r,c+2} - p_{c+2} B'_{r,c+1}
+    const TA q1 = h ? p[(cb + 1) % 3] : p[(ca + 1) % 3], q2 = h ? p[(cb + 2) % 3] : p[(ca + 2) % 3];
+    const TA y2 = h ? Bp[rb][(cb + 2) % 3] : Bp[ra][(ca + 2) % 3];
+    const TA y1 = h ? Bp[rb][(cb + 1) % 3] : Bp[ra][(ca + 1) % 3];
+    // (p x b''_c)_r = p_{r+1} B''_{c,r+2} - p_{r+2} B''_{c,r+1}
+    const TA s1 = h ? p[(rb + 1) % 3] : p[(ra + 1) % 3], s2 = h ? p[(rb + 2) % 3] : p[(ra + 2) % 3];
+    const TA z2 = h ? Bq[cb][(rb + 2) % 3] : Bq[ca][(ra + 2) % 3];
+    const TA z1 = h ? Bq[cb][(rb + 1) % 3] : Bq[ca][(ra + 1) % 3];
+    const int r = h ? rb : ra, c = h ? cb : ca;
+    TA t = a_rc + TA(J[s6(r, c)]);
+    t += q1 * y2 - q2 * y1;
+    t += s1 * z2 - s2 * z1;
+    tl[e] = t;
+    cn[e] = (h ? Cp[rb][cb] : Cp[ra][ca]) + TA(J[s6(3 + r, 3 + c)]);
+  }
+  const int a = h ? 2 : 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    bn[c] = Bqa[c] + TA(J[s6(a, 3 + c)]);
+    b1[c] = Bq1[c] + TA(J[s6(1, 3 + c)]);
+  }
+  // swap the entries and assemble the whole result on both lanes
+  TA to[3], co[3], bo[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    to[e] = xch(tl[e]);
+    co[e] = xch(cn[e]);
+    bo[e] = xch(bn[e]);
+  }
+  Out[s6(0, 0)] = h ? to[0] : tl[0];
+  Out[s6(0, 1)] = h ? to[1] : tl[1];
+  Out[s6(0, 2)] = h ? to[2] : tl[2];
+  Out[s6(1, 1)] = h ? tl[0] : to[0];
+  Out[s6(1, 2)] = h ? tl[1] : to[1];
+  Out[s6(2, 2)] = h ? tl[2] : to[2];
+  Out[s6(3, 3)] = h ? co[0] : cn[0];
+  Out[s6(3, 4)] = h ? co[1] : cn[1];
+  Out[s6(3, 5)] = h ? co[2] : cn[2];
+  Out[s6(4, 4)] = h ? cn[0] : co[0];
+  Out[s6(4, 5)] = h ? cn[1] : co[1];
+  Out[s6(5, 5)] = h ? cn[2] : co[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Out[s6(0, 3 + c)] = h ? bo[c] : bn[c];
+    Out[s6(1, 3 + c)] = b1[c];
+    Out[s6(2, 3 + c)] = h ? bn[c] : bo[c];
+  }
+}
 
 // JSIIA (Section II-C): M by the unit-acceleration inverse dynamics of every
 // column, its Cholesky factor, two triangular solves.
@@ -995,8 +1264,8 @@ __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, T
 //   M[i][k] = e_1^T F_i = (X_{k+1}^T ... X_i^T h_i)[0],  h_i = I^c_i e_1:
 // one SE(3) transport per entry of the lower triangle. The composite recursion
 // runs on six lanes (row r of I^c on lane r, the congruence as two transports
-// per lane through a shared-memory transpose) for teams of 8 and more, on one
-// lane for smaller teams.
+// per lane through a shared-memory transpose) for teams of 8 and more, on a pair
+// of lanes for teams of 2 and 4, on one lane alone.
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel(KArgs A) {
   constexpr int NXB = P >= 8 ? block_for<P>() / P : 1;
@@ -1068,8 +1337,30 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
         for (int c = 0; c < 6; ++c) prow[c] = Jr[c] + orow[c];
       }
     }
-  } else {
+  } else if constexpr (P >= 2) {
+    // teams of 2 and 4: the congruence on a pair of lanes (lanes 2, 3 of a team of
+    // 4 repeat lanes 0, 1 and write nothing)
     tm.sync();
+    TA Pm[21];
+    if (n > 0) {
+      const T *J = pb.rec + static_cast<int64_t>(n - 1) * REC + REC_J;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) Pm[k] = TA(J[k]);
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      if (tm.r == 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) H[static_cast<int64_t>(i) * 6 + c] = Pm[s6(0, c)];
+      }
+      if (i == 0) break;
+      SE3<TA> ga;
+      load_g(i, ga);
+      TA Pn[21];
+      congruence_pair<TA, T, P>(tm, ga, Pm, pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J, Pn);
+#pragma unroll
+      for (int k = 0; k < 21; ++k) Pm[k] = Pn[k];
+    }
+  } else {
     if (tm.r == 0) {
       TA Pm[21];
       if (n > 0) {

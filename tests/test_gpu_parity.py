@@ -80,7 +80,7 @@ def test_fd_fp32_parity_short_chains(prec, algo):
     model = synth.random_chains([1, 2, 4, 7, 7, 7, 8] * 8, seed=11)
     st = synth.random_states(model.n_links_total, seed=12)
     ref = oracle.fd(model, st.q, st.qdot, st.tau)
-    for team in ([1, 8, 32] if algo == "abia" else [1, 8]):
+    for team in ([1, 8, 32] if algo == "abia" else [1, 2, 8]):
         got, status = _run(model, st, algo, prec, team)
         assert (status == 0).all()
         err = _rel_err(got, ref, model.offsets)
