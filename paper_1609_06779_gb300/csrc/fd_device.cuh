@@ -408,8 +408,10 @@ __device__ __forceinline__ void team_scan_bwd(const Team<P> &tm, SegOp<T> op, T 
 
 // ------------------------------------------------------------- 5x5 SolvSys
 
-// Cholesky D = L L^T of a packed symmetric 5x5 (lower triangle). Writes L and
-// the reciprocals of its diagonal. Returns false if a pivot is not positive.
+// Cholesky D = L L^T of a packed symmetric 5x5 (lower triangle). Writes the
+// strict lower triangle of L, the reciprocals of its diagonal into inv and (the
+// same reciprocals) into L's diagonal slots. Returns false if a pivot is not
+// positive.
 template <class T>
 __device__ __forceinline__ bool chol5(const T *D, T *L, T *inv) {
   bool ok = true;
@@ -420,7 +422,7 @@ __device__ __forceinline__ bool chol5(const T *D, T *L, T *inv) {
     for (int k = 0; k < j; ++k) d -= L[l5(j, k)] * L[l5(j, k)];
     ok = ok && (d > T(0));
     const T r = d > T(0) ? rsqrt_t(d) : T(0);
-    L[l5(j, j)] = d * r;
+    L[l5(j, j)] = r;  // the diagonal sqrt(d) itself is never read: the solves take 1 / L_jj
     inv[j] = r;
 #pragma unroll
     for (int i = j + 1; i < 5; ++i) {

@@ -664,8 +664,8 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
         for (int c = 0; c < 5; ++c) {
           TA s = TA(0);
 #pragma unroll
-          for (int k = 0; k < 5; ++k) s += Z[r][k] * nb[A_G + 5 * k + c];
-          Un[5 * r + c] = -s;  // U_i <- -E_i U_{i+d} = -Z G_{i+d}
+          for (int k = 0; k < 5; ++k) s -= Z[r][k] * nb[A_G + 5 * k + c];
+          Un[5 * r + c] = s;  // U_i <- -E_i U_{i+d} = -Z G_{i+d}
         }
     }
   }
@@ -1055,7 +1055,12 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_cr2_kern
 //   X^T P X = [[A' + B' p^T + p^ B''^T, B''], [B''^T, C']],  B'' = B' + p^ C',
 // where (B' p^T)_rc = (p x b'_r)_c and (p^ B''^T)_rc = (p x b''_c)_r for the rows
 // b'_r, b''_c: about 200 fused operations instead of twelve 6-vector transports.
-template <class TA>
+//
+// ZERO0: row and column 0 of P are zero and never read (the articulated inertia
+// Pa = P - P S D^{-1} S^T P has Pa S = 0 with S = e_1), which drops the first
+// column of A from R A, the first row of B from R B and the first column of R A
+// from A' (36 fewer operations).
+template <class TA, bool ZERO0 = false>
 __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, TA *Out) {
   const TA *R = g.R, *p = g.p;
   TA RA[3][3], RB[3][3], RC[3][3];  // R A, R B, R C
@@ -1063,9 +1068,14 @@ __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, T
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      RA[r][c] = R[3 * r] * P6[s6(0, c)] + R[3 * r + 1] * P6[s6(1, c)] + R[3 * r + 2] * P6[s6(2, c)];
-      RB[r][c] = R[3 * r] * P6[s6(0, 3 + c)] + R[3 * r + 1] * P6[s6(1, 3 + c)] +
-                 R[3 * r + 2] * P6[s6(2, 3 + c)];
+      if constexpr (ZERO0) {
+        RA[r][c] = c == 0 ? TA(0) : R[3 * r + 1] * P6[s6(1, c)] + R[3 * r + 2] * P6[s6(2, c)];
+        RB[r][c] = R[3 * r + 1] * P6[s6(1, 3 + c)] + R[3 * r + 2] * P6[s6(2, 3 + c)];
+      } else {
+        RA[r][c] = R[3 * r] * P6[s6(0, c)] + R[3 * r + 1] * P6[s6(1, c)] + R[3 * r + 2] * P6[s6(2, c)];
+        RB[r][c] = R[3 * r] * P6[s6(0, 3 + c)] + R[3 * r + 1] * P6[s6(1, 3 + c)] +
+                   R[3 * r + 2] * P6[s6(2, 3 + c)];
+      }
       RC[r][c] = R[3 * r] * P6[s6(3, 3 + c)] + R[3 * r + 1] * P6[s6(4, 3 + c)] +
                  R[3 * r + 2] * P6[s6(5, 3 + c)];
     }
@@ -1097,7 +1107,10 @@ __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, T
     for (int c = r; c < 3; ++c) {
       const int c1 = (c + 1) % 3, c2 = (c + 2) % 3, r1 = (r + 1) % 3, r2 = (r + 2) % 3;
       TA t = Out[s6(r, c)];
-      t += RA[r][0] * R[3 * c] + RA[r][1] * R[3 * c + 1] + RA[r][2] * R[3 * c + 2];
+      if constexpr (ZERO0)
+        t += RA[r][1] * R[3 * c + 1] + RA[r][2] * R[3 * c + 2];
+      else
+        t += RA[r][0] * R[3 * c] + RA[r][1] * R[3 * c + 1] + RA[r][2] * R[3 * c + 2];
       t += p[c1] * Bp[r][c2] - p[c2] * Bp[r][c1];
       t += p[r1] * Bq[c][r2] - p[r2] * Bq[c][r1];
       Out[s6(r, c)] = t;
@@ -1111,6 +1124,7 @@ __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, T
 #pragma unroll
     for (int c = r; c < 3; ++c) Out[s6(3 + r, 3 + c)] += Cp[r][c];
 }
+
 
 // The same congruence X^T P X + J on a pair of lanes (h = lane & 1), both holding
 // the whole P: lane 0 rotates A and rows 0, 1 of B, lane 1 rotates C and rows 2, 1
@@ -1425,7 +1439,7 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
         for (int w = 0; w < u; ++w) d -= Ld[u][w] * Ld[u][w];
         bad |= !(d > TA(0));
         const TA r = d > TA(0) ? rsqrt_t(d) : TA(0);
-        Ld[u][u] = d * r;
+        Ld[u][u] = r;  // L_jj itself is never read: the panel and the solves take 1 / L_jj
         rinv[u] = r;
 #pragma unroll
         for (int v = u + 1; v < NB; ++v) {
@@ -1562,7 +1576,7 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
 // side in4 shares the articulated inertias; its bias force and acceleration pass
 // give M^{-1} in4 in out4.
 template <class T, class TA, bool TWO>
-__global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
+__global__ void __launch_bounds__(128, TWO ? 3 : 4) abia_kernel(KArgs A) {
   Team<1> tm;
   Prob<T> pb;
   if (!load_problem<T, 1>(A, tm, pb, NT)) return;
@@ -1614,10 +1628,10 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
       ra[A_UU2] = u2 * Dinv;
     }
     if (i == 0) break;
-    // Pa = P - h h^T / D, pa = p + h u / D
+    // Pa = P - h h^T / D (row and column 0 vanish: Pa e_1 = 0), pa = p + h u / D
     TA Pa[21], pa[6], hs[6];
     for (int k = 0; k < 6; ++k) hs[k] = h[k] * Dinv;
-    for (int r = 0; r < 6; ++r)
+    for (int r = 1; r < 6; ++r)
       for (int c = r; c < 6; ++c) Pa[s6(r, c)] = Pm[s6(r, c)] - h[r] * hs[c];
     for (int k = 0; k < 6; ++k) pa[k] = pbias[k] + hs[k] * u;
     TA pa2[6];
@@ -1629,7 +1643,7 @@ __global__ void __launch_bounds__(128) abia_kernel(KArgs A) {
     for (int c = 0; c < 3; ++c) ga.p[c] = TA(g.p[c]);
     const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
     for (int k = 0; k < 21; ++k) Pm[k] = TA(J[k]);
-    congruence_add(ga, Pa, Pm);
+    congruence_add<TA, true>(ga, Pa, Pm);
     adinvT(ga, pa, pbias);
     if constexpr (TWO) adinvT(ga, pa2, pbias2);
   }

@@ -30,12 +30,16 @@ def id_flops(n: int) -> int:
 # X^T P X + J in rotated 3x3 blocks (R A, R B, R C 135; B' 45; C' 30;
 # B'' = B' + p^ C' 36; top-left block with its cross terms 84; + J 15)
 CONG_BLOCKS = 345
+# the same with row and column 0 of P zero (the articulated inertia, Pa S = 0):
+# R A 18 and R B 27 instead of 45 each, A' 24 instead of 36
+CONG_BLOCKS_ART = CONG_BLOCKS - 57
 
 
 def abia_flops(n: int) -> int:
-    """ID + articulated-inertia recursion (Pa 63 + 1, pa 18, congruence with J
-    in blocks 345, bias transport 42) for n-1 links + forward pass 56."""
-    per_abi = 64 + 18 + CONG_BLOCKS + ADJ
+    """ID + articulated-inertia recursion (Pa on its 15 nonzero entries 45 + 1,
+    pa 18, congruence with J in blocks and the zero row and column of Pa 288, bias
+    transport 42) for n-1 links + forward pass 56."""
+    per_abi = 46 + 18 + CONG_BLOCKS_ART + ADJ
     return id_flops(n) + max(n - 1, 0) * per_abi + n * (ADJ + 14)
 
 
