@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fd_layout.h"
 
 namespace fdk {
@@ -132,6 +134,19 @@ __device__ __forceinline__ void adT_apply(const T *V, const T *x, T *y) {
   cross3(V, x + 3, c);
   y[0] = -a[0] - b[0]; y[1] = -a[1] - b[1]; y[2] = -a[2] - b[2];
   y[3] = -c[0]; y[4] = -c[1]; y[5] = -c[2];
+}
+
+// y -= ad_V^T x, i.e. y += (w x n + v x f; w x f) for V = (w; v), x = (n; f),
+// accumulated in fused multiply-adds (no separate negations)
+template <class T>
+__device__ __forceinline__ void adT_sub(const T *V, const T *x, T *y) {
+  const T *w = V, *v = V + 3, *n = x, *f = x + 3;
+  y[0] = (((y[0] + w[1] * n[2]) - w[2] * n[1]) + v[1] * f[2]) - v[2] * f[1];
+  y[1] = (((y[1] + w[2] * n[0]) - w[0] * n[2]) + v[2] * f[0]) - v[0] * f[2];
+  y[2] = (((y[2] + w[0] * n[1]) - w[1] * n[0]) + v[0] * f[1]) - v[1] * f[0];
+  y[3] = (y[3] + w[1] * f[2]) - w[2] * f[1];
+  y[4] = (y[4] + w[2] * f[0]) - w[0] * f[2];
+  y[5] = (y[5] + w[0] * f[1]) - w[1] * f[0];
 }
 
 // y = K x, K packed symmetric 6x6

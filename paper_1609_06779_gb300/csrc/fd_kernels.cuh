@@ -137,10 +137,8 @@ __device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, c
     ldv<T, 6>(w + W_V, Vi);
     ldv<T, 6>(w + W_F, Ai);
     sym6_apply(rec + REC_J, Vi, JV);
-    adT_apply(Vi, JV, f);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) f[j] = -f[j];
-    sym6_apply_add(rec + REC_J, Ai, f);
+    sym6_apply(rec + REC_J, Ai, f);
+    adT_sub(Vi, JV, f);
     stv<T, 6>(w + W_F, f);
   }
   tm.sync();
@@ -252,10 +250,8 @@ __device__ __forceinline__ void id_pair(const Team<P> &tm, const Prob<T> &pb, co
     ldv<T, 6>(w + W_V, Vi);
     ldv<T, 6>(w + W_F, Ai);
     sym6_apply(rec + REC_J, Vi, JV);
-    adT_apply(Vi, JV, f);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) f[j] = -f[j];
-    sym6_apply_add(rec + REC_J, Ai, f);
+    sym6_apply(rec + REC_J, Ai, f);
+    adT_sub(Vi, JV, f);
     stv<T, 6>(w + W_F, f);
   }
   tm.sync();
@@ -382,9 +378,8 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
     T V[6], JV[6], JA[6];
     ldv<T, 6>(w + W_V, V);
     sym6_apply(rec + REC_J, V, JV);
-    adT_apply(V, JV, JA);
-    for (int k = 0; k < 6; ++k) JA[k] = -JA[k];
-    sym6_apply_add(rec + REC_J, x, JA);  // J Vd - ad_V^T J V
+    sym6_apply(rec + REC_J, x, JA);
+    adT_sub(V, JV, JA);  // J Vd - ad_V^T J V
     stv<T, 6>(w + W_F, JA);
   }
 
@@ -446,6 +441,16 @@ __device__ __forceinline__ RowP<E> rowp(E *wa, int n, int i) {
 
 // (X K X^T)[1..5][1..5] + Kd[1..5][1..5] into packed lower 5x5, X = Ad_{g^{-1}},
 // K, Kd packed symmetric 6x6 (T_ii of Algorithm 1's CalcA, W_i^T T_ii W_i).
+// acc + (a0 b0 + a1 b1 + a2 b2): one chain of fused multiply-adds from acc when the
+// products are in the accumulation type, else the sum in T added in TA
+template <class T, class TA>
+__device__ __forceinline__ TA add_dot3(TA acc, T a0, T b0, T a1, T b1, T a2, T b2) {
+  if constexpr (std::is_same<T, TA>::value)
+    return ((acc + a0 * b0) + a1 * b1) + a2 * b2;
+  else
+    return acc + TA(a0 * b0 + a1 * b1 + a2 * b2);
+}
+
 template <class T, class TA, class Out>
 __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, const T *Kself,
                                             Out D) {
@@ -484,8 +489,8 @@ __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, con
       for (int c = 0; c <= r; ++c) {
         const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
         T t = C[r][c];
-        t -= p[r1] * B[r2][c] - p[r2] * B[r1][c];   // (p x b_c)_r
-        t += Bt[c1][r] * p[c2] - Bt[c2][r] * p[c1];  // (bt_r x p)_c
+        t = (t - p[r1] * B[r2][c]) + p[r2] * B[r1][c];   // - (p x b_c)_r
+        t = (t + Bt[c1][r] * p[c2]) - Bt[c2][r] * p[c1];  // + (bt_r x p)_c
         Cs[r][c] = t;
         Cs[c][r] = t;
       }
@@ -500,7 +505,8 @@ __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, con
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b <= a; ++b)
-        acc[l5(a, b)] += TA(R[1 + a] * AR[0][b] + R[4 + a] * AR[1][b] + R[7 + a] * AR[2][b]);
+        acc[l5(a, b)] = add_dot3<T, TA>(acc[l5(a, b)], R[1 + a], AR[0][b], R[4 + a], AR[1][b],
+                                        R[7 + a], AR[2][b]);
     // off-diagonal rows 1..2 of R^T Bt R, as rows 3..5 x columns 1..2 of D
     T RB[2][3];  // (R^T Bt)_{a,:} for a = 1, 2
 #pragma unroll
@@ -512,8 +518,8 @@ __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, con
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b)
-        acc[l5(2 + b, a)] +=
-            TA(RB[a][0] * R[b] + RB[a][1] * R[3 + b] + RB[a][2] * R[6 + b]);
+        acc[l5(2 + b, a)] = add_dot3<T, TA>(acc[l5(2 + b, a)], RB[a][0], R[b], RB[a][1],
+                                            R[3 + b], RB[a][2], R[6 + b]);
     // bottom-right R^T Cs R
     T RC[3][3];  // R^T Cs
 #pragma unroll
@@ -525,8 +531,8 @@ __device__ __forceinline__ void calc_dblock(const SE3<T> *g, const T *Kprev, con
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b <= a; ++b)
-        acc[l5(2 + a, 2 + b)] +=
-            TA(RC[a][0] * R[b] + RC[a][1] * R[3 + b] + RC[a][2] * R[6 + b]);
+        acc[l5(2 + a, 2 + b)] = add_dot3<T, TA>(acc[l5(2 + a, 2 + b)], RC[a][0], R[b], RC[a][1],
+                                                R[3 + b], RC[a][2], R[6 + b]);
   }
 #pragma unroll
   for (int k = 0; k < 15; ++k) D[k] = acc[k];
@@ -544,17 +550,17 @@ __device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, Out U
     if (j < 3) {
 #pragma unroll
       for (int r = 0; r < 5; ++r)
-        U[5 * r + c] = TA(-(Ki[s6(r + 1, 0)] * R[j] + Ki[s6(r + 1, 1)] * R[3 + j] +
-                            Ki[s6(r + 1, 2)] * R[6 + j]));
+        U[5 * r + c] = TA(-Ki[s6(r + 1, 0)] * R[j] - Ki[s6(r + 1, 1)] * R[3 + j] -
+                          Ki[s6(r + 1, 2)] * R[6 + j]);
     } else {
       const int m = j - 3;
       const T x0 = R[m], x1 = R[3 + m], x2 = R[6 + m];
       const T w0 = p[1] * x2 - p[2] * x1, w1 = p[2] * x0 - p[0] * x2, w2 = p[0] * x1 - p[1] * x0;
 #pragma unroll
       for (int r = 0; r < 5; ++r)
-        U[5 * r + c] = TA(-(Ki[s6(r + 1, 0)] * w0 + Ki[s6(r + 1, 1)] * w1 +
-                            Ki[s6(r + 1, 2)] * w2 + Ki[s6(r + 1, 3)] * x0 +
-                            Ki[s6(r + 1, 4)] * x1 + Ki[s6(r + 1, 5)] * x2));
+        U[5 * r + c] = TA(-Ki[s6(r + 1, 0)] * w0 - Ki[s6(r + 1, 1)] * w1 -
+                          Ki[s6(r + 1, 2)] * w2 - Ki[s6(r + 1, 3)] * x0 -
+                          Ki[s6(r + 1, 4)] * x1 - Ki[s6(r + 1, 5)] * x2);
     }
   }
 }
@@ -878,35 +884,31 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
   }
   tm.sync();
   for (int i = tm.r; i < n; i += P) {
+    // R_i = -(z_i - Ad_{g_i^{-1}} z_{i-1}), components 1..5
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    T z[6];
+    T z[6], t[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     ldv<T, 6>(w + W_Z, z);
+    SE3<T> g;
     if (i > 0) {
-      SE3<T> g;
       ld_se3(w + W_G, g);
-      T t[6];
       adinv(g, w - NT + W_Z, t);
-      for (int k = 0; k < 6; ++k) z[k] -= t[k];
     }
     const RowP<TA> row = rowp(wa, n, i);
-    for (int k = 0; k < 5; ++k) row[A_R0 + k] = TA(-z[k + 1]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) row[A_R0 + k] = TA(t[k + 1] - z[k + 1]);
     if (two) {
-      T z2[6];
+      T z2[6], t2[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
       for (int k = 0; k < 6; ++k) z2[k] = T(row[A_Z2 + k]);
       if (i > 0) {
-        SE3<T> g;
-        ld_se3(w + W_G, g);
         const RowP<TA> rp = rowp(wa, n, i - 1);
-        T zp[6], t[6];
+        T zp[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) zp[k] = T(rp[A_Z2 + k]);
-        adinv(g, zp, t);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) z2[k] -= t[k];
+        adinv(g, zp, t2);
       }
 #pragma unroll
-      for (int k = 0; k < 5; ++k) row[A_R20 + k] = TA(-z2[k + 1]);
+      for (int k = 0; k < 5; ++k) row[A_R20 + k] = TA(t2[k + 1] - z2[k + 1]);
     }
   }
   tm.sync();
@@ -1106,13 +1108,12 @@ __device__ __forceinline__ void congruence_add(const SE3<TA> &g, const TA *P6, T
 #pragma unroll
     for (int c = r; c < 3; ++c) {
       const int c1 = (c + 1) % 3, c2 = (c + 2) % 3, r1 = (r + 1) % 3, r2 = (r + 2) % 3;
+      // one chain of fused multiply-adds from Out's entry (no separate additions)
       TA t = Out[s6(r, c)];
-      if constexpr (ZERO0)
-        t += RA[r][1] * R[3 * c + 1] + RA[r][2] * R[3 * c + 2];
-      else
-        t += RA[r][0] * R[3 * c] + RA[r][1] * R[3 * c + 1] + RA[r][2] * R[3 * c + 2];
-      t += p[c1] * Bp[r][c2] - p[c2] * Bp[r][c1];
-      t += p[r1] * Bq[c][r2] - p[r2] * Bq[c][r1];
+      if constexpr (!ZERO0) t = t + RA[r][0] * R[3 * c];
+      t = (t + RA[r][1] * R[3 * c + 1]) + RA[r][2] * R[3 * c + 2];
+      t = (t + p[c1] * Bp[r][c2]) - p[c2] * Bp[r][c1];
+      t = (t + p[r1] * Bq[c][r2]) - p[r2] * Bq[c][r1];
       Out[s6(r, c)] = t;
     }
 #pragma unroll
@@ -1228,8 +1229,8 @@ __device__ __forceinline__ void congruence_pair(const Team<P> &tm, const SE3<TA>
     const TA z1 = h ? Bq[cb][(rb + 1) % 3] : Bq[ca][(ra + 1) % 3];
     const int r = h ? rb : ra, c = h ? cb : ca;
     TA t = a_rc + TA(J[s6(r, c)]);
-    t += q1 * y2 - q2 * y1;
-    t += s1 * z2 - s2 * z1;
+    t = (t + q1 * y2) - q2 * y1;
+    t = (t + s1 * z2) - s2 * z1;
     tl[e] = t;
     cn[e] = (h ? Cp[rb][cb] : Cp[ra][ca]) + TA(J[s6(3 + r, 3 + c)]);
   }
