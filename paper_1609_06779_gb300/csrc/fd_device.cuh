@@ -24,6 +24,14 @@ __device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sinco
 __device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+// x > 0 for a pivot, tested on the bit pattern (an integer compare, not an FP64
+// one): true for positive numbers and +inf, also for a NaN with a clear sign bit,
+// which the kernels' final finiteness check then reports
+__device__ __forceinline__ bool pos_t(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool pos_t(float x) { return __float_as_int(x) > 0; }
+// 1 / x rounded to nearest (the same value as the IEEE division 1 / x)
+__device__ __forceinline__ double rcp_t(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
 
 // ------------------------------------------------------------------ indexing
 
@@ -435,8 +443,8 @@ __device__ __forceinline__ bool chol5(const T *D, T *L, T *inv) {
     T d = D[l5(j, j)];
 #pragma unroll
     for (int k = 0; k < j; ++k) d -= L[l5(j, k)] * L[l5(j, k)];
-    ok = ok && (d > T(0));
-    const T r = d > T(0) ? rsqrt_t(d) : T(0);
+    ok = ok && pos_t(d);
+    const T r = rsqrt_t(d);  // inf or NaN for a non-positive pivot, flagged by ok
     L[l5(j, j)] = r;  // the diagonal sqrt(d) itself is never read: the solves take 1 / L_jj
     inv[j] = r;
 #pragma unroll

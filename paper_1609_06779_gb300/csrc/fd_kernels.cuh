@@ -545,23 +545,18 @@ template <class T, class TA, class Out>
 __device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, Out U) {
   const T *R = gn.R, *p = gn.p;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    const int j = c + 1;
-    if (j < 3) {
+  for (int r = 0; r < 5; ++r) {
+    const T k0 = Ki[s6(r + 1, 0)], k1 = Ki[s6(r + 1, 1)], k2 = Ki[s6(r + 1, 2)];
 #pragma unroll
-      for (int r = 0; r < 5; ++r)
-        U[5 * r + c] = TA(-Ki[s6(r + 1, 0)] * R[j] - Ki[s6(r + 1, 1)] * R[3 + j] -
-                          Ki[s6(r + 1, 2)] * R[6 + j]);
-    } else {
-      const int m = j - 3;
-      const T x0 = R[m], x1 = R[3 + m], x2 = R[6 + m];
-      const T w0 = p[1] * x2 - p[2] * x1, w1 = p[2] * x0 - p[0] * x2, w2 = p[0] * x1 - p[1] * x0;
+    for (int j = 1; j < 3; ++j)
+      U[5 * r + j - 1] = TA(-k0 * R[j] - k1 * R[3 + j] - k2 * R[6 + j]);
+    // columns 3..5: k_top . (p x x) + k_bot . x = (k_top x p + k_bot) . x, x = R_{:,m}
+    const T a0 = (Ki[s6(r + 1, 3)] + k1 * p[2]) - k2 * p[1];
+    const T a1 = (Ki[s6(r + 1, 4)] + k2 * p[0]) - k0 * p[2];
+    const T a2 = (Ki[s6(r + 1, 5)] + k0 * p[1]) - k1 * p[0];
 #pragma unroll
-      for (int r = 0; r < 5; ++r)
-        U[5 * r + c] = TA(-Ki[s6(r + 1, 0)] * w0 - Ki[s6(r + 1, 1)] * w1 -
-                          Ki[s6(r + 1, 2)] * w2 - Ki[s6(r + 1, 3)] * x0 -
-                          Ki[s6(r + 1, 4)] * x1 - Ki[s6(r + 1, 5)] * x2);
-    }
+    for (int m = 0; m < 3; ++m)
+      U[5 * r + 2 + m] = TA(-a0 * R[m] - a1 * R[3 + m] - a2 * R[6 + m]);
   }
 }
 
@@ -1438,8 +1433,8 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
         TA d = Ld[u][u];
 #pragma unroll
         for (int w = 0; w < u; ++w) d -= Ld[u][w] * Ld[u][w];
-        bad |= !(d > TA(0));
-        const TA r = d > TA(0) ? rsqrt_t(d) : TA(0);
+        bad |= !pos_t(d);
+        const TA r = rsqrt_t(d);  // inf or NaN for a non-positive pivot, flagged by bad
         Ld[u][u] = r;  // L_jj itself is never read: the panel and the solves take 1 / L_jj
         rinv[u] = r;
 #pragma unroll
@@ -1618,8 +1613,8 @@ __global__ void __launch_bounds__(128, TWO ? 3 : 4) abia_kernel(KArgs A) {
     for (int k = 0; k < 6; ++k) h[k] = Pm[s6(0, k)];
     const TA D = h[0];
     const TA u = TA(tdi) - pbias[0];
-    bad |= !(D > TA(0));
-    const TA Dinv = TA(1) / D;
+    bad |= !pos_t(D);
+    const TA Dinv = rcp_t(D);
     for (int k = 0; k < 6; ++k) ra[A_H + k] = h[k];
     ra[A_DD] = Dinv;
     ra[A_UU] = u * Dinv;
@@ -1751,8 +1746,8 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       for (int c = 0; c < 6; ++c) h[c] = __shfl_sync(tm.mask, prow[c], 0, P);
       const TA p0 = __shfl_sync(tm.mask, pbr, 0, P);
       const TA D = h[0];
-      bad |= !(D > TA(0));
-      const TA Dinv = TA(1) / D;
+      bad |= !pos_t(D);
+      const TA Dinv = rcp_t(D);
       const TA uD = (td - p0) * Dinv;  // u_i / D_i
       TA uD2 = TA(0);
       if constexpr (TWO) uD2 = (tdb - __shfl_sync(tm.mask, pbr2, 0, P)) * Dinv;
@@ -1865,8 +1860,8 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       TA hr[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) hr[k] = __shfl_sync(tm.mask, pc[k], hh, P);
-      bad |= !(D > TA(0));
-      const TA Dinv = TA(1) / D;
+      bad |= !pos_t(D);
+      const TA Dinv = rcp_t(D);
       const TA uD = (td - p0) * Dinv;  // u_i / D_i
       TA uD2 = TA(0);  // the second right-hand side's bias force rides on lanes 14, 15
       if constexpr (TWO) uD2 = (tdb - __shfl_sync(tm.mask, pc[0], 14, P)) * Dinv;

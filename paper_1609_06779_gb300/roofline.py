@@ -75,13 +75,14 @@ def oee_flops(n: int) -> int:
 # R^T Bt 30 + its 6 entries 36, R^T Cs 45 + its 6 entries 36 (each entry with its
 # addition into K_self)
 D_BLOCKS = 36 + 48 + 48 + 66 + 81
-# U_i: columns 1, 2 of Ad^T have three nonzeros (5 rows x 5 flops), columns 3..5
-# six after one cross product (9 + 5 rows x 11 flops)
-U_BLOCK = 2 * 25 + 3 * (9 + 55)
+# U_i: columns 1, 2 of Ad^T have three nonzeros (5 rows x 5 flops); columns 3..5
+# are (p x x; x), and k_top . (p x x) + k_bot . x = (k_top x p + k_bot) . x (per
+# row 12 for that vector, then 5 per column)
+U_BLOCK = 2 * 25 + 5 * (12 + 3 * 5)
 
 
 def cfa_flops(n: int) -> int:
-    """ID + A blocks (D in rotated blocks 279; U 242: rows 1..5 of J^{-1} times
+    """ID + A blocks (D in rotated blocks 279; U 185: rows 1..5 of J^{-1} times
     the sparse columns of Ad^T) + R = -B tau (J^{-1} on three nonzero components
     30 + 6, one transport 42) + OEE + CalcAcc (120)."""
     return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 78) + oee_flops(n) + n * 120

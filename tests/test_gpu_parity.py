@@ -120,6 +120,30 @@ def test_shared_model_batch_cfg_small():
         assert _rel_err(got, ref, so).max() < 1e-10, algo
 
 
+def test_nonfinite_input_flags_only_its_problem():
+    """A NaN or infinite torque, or a NaN joint angle, makes that problem's status
+    nonzero; the other problems of the same launch solve as usual."""
+    model = synth.random_chains([7, 32, 5, 32, 9], seed=31)
+    st = synth.random_states(model.n_links_total, seed=32)
+    ref = oracle.fd(model, st.q, st.qdot, st.tau)
+    off = model.offsets
+    bad = synth.States(st.q.copy(), st.qdot.copy(), st.tau.copy())
+    bad.tau[off[1] + 3] = np.nan
+    bad.tau[off[2]] = np.inf
+    bad.q[off[4] + 8] = np.nan
+    clean = [0, 3]
+    for algo in ("abia", "jsiia", "cfa", "cfa_cr"):
+        for prec, team in (("fp64", 1), ("fp64", 2), ("fp64", 8), ("mixed", 8), ("fp32", 1)):
+            if algo == "abia" and team == 2:
+                continue
+            got, status = _run(model, bad, algo, prec, team)
+            assert list(status != 0) == [False, True, True, False, True], (algo, prec, team, status)
+            err = _rel_err(got, ref, off)[clean]
+            assert np.isfinite(err).all(), (algo, prec, team, err)
+            if prec != "fp32":  # FP32 CFA on 32 links is at the 1e-2 level
+                assert err.max() < (1e-10 if prec == "fp64" else 1e-3), (algo, prec, team, err)
+
+
 def test_all_algorithms_and_teams_agree():
     model = synth.random_chains([32] * 64, seed=21)
     st = synth.random_states(model.n_links_total, seed=22)
