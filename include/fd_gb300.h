@@ -140,9 +140,10 @@ fd_status fd_batch_info(fd_batch_t batch, int32_t *n_problems, int64_t *n_state_
  * scans across warps through shared memory). FD_ABIA keeps its articulated-
  * inertia recursion serial over the links (the paper notes it cannot be
  * parallelised beyond a constant factor, Section III) and takes that constant
- * factor: team 1 runs one thread per problem, teams 8, 16 and 32 spread the
- * six rows of each step's 6x6 update over six lanes and run inverse dynamics
- * as a scan; other sizes return FD_ERR_UNSUPPORTED.
+ * factor: team 1 runs one thread per problem, teams 8, 16 and 32 spread each
+ * step's 6x6 update over six (team 8) or twelve lanes and run inverse dynamics
+ * on component lanes (chains of up to 64 links) or as a scan; other sizes
+ * return FD_ERR_UNSUPPORTED.
  */
 
 /* Bytes of device workspace fd_solve_batch / fd_inverse_dynamics need for
