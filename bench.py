@@ -131,10 +131,14 @@ def measured_hbm_gbs():
 
 
 def csrc_sha() -> str:
+    """Hash of the sources the forward-dynamics kernels are compiled from (their
+    headers and launch units), so a traffic record stays valid only for them."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1609_06779_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+        if f in ("fd_layout.h", "fd_device.cuh", "fd_kernels.cuh", "fd_launch.h") or (
+                f.startswith(("k_abia", "k_jsiia", "k_cfa")) and f.endswith(".cu")):
+            h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -22,13 +22,6 @@
 
 namespace fdk {
 
-// ad_{e_1} x = (e_1 x w; e_1 x v)
-template <class T>
-__device__ __forceinline__ void ad_e1(const T *x, T *y) {
-  y[0] = T(0); y[1] = -x[2]; y[2] = x[1];
-  y[3] = T(0); y[4] = -x[5]; y[5] = x[4];
-}
-
 template <class T>
 __device__ __forceinline__ T dot6(const T *a, const T *b) {
   T s = T(0);
@@ -138,19 +131,15 @@ __device__ __forceinline__ void adjoint_lanes(const Team<P> &tm, const Prob<T> &
     ldv<T, 6>(w + J_A, Ai);
     ldv<T, 6>(w + J_FB, Fb);
     sym6_apply(J, V, JV);
-    adT_apply(V, JV, t1);
     sym6_apply(J, Ai, t2);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) t2[j] -= t1[j];
-    stv<T, 6>(w + J_F, t2);  // f_i
+    adT_sub(V, JV, t2);
+    stv<T, 6>(w + J_F, t2);   // f_i = J A - ad_V^T J V
     sym6_apply(J, Fb, t2);
     stv<T, 6>(w + J_AB, t2);  // J_i Fbar_i
-    adT_apply(Fb, JV, t1);    // ad_{Fbar}^T (J V)
-    ad_apply(V, Fb, t2);      // ad_V Fbar
-    sym6_apply(J, t2, t3);    // J ad_V Fbar
-#pragma unroll
-    for (int j = 0; j < 6; ++j) t1[j] -= t3[j];
-    stv<T, 6>(w + J_VB, t1);
+    ad_apply(V, Fb, t1);      // ad_V Fbar
+    sym6_apply(J, t1, t3);    // J ad_V Fbar
+    adT_sub(Fb, JV, t3);      // minus the Vbar term: J ad_V Fbar - ad_{Fbar}^T (J V)
+    stv<T, 6>(w + J_VB, t3);
   }
   tm.sync();
 
@@ -162,14 +151,17 @@ __device__ __forceinline__ void adjoint_lanes(const Team<P> &tm, const Prob<T> &
     T Vb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     for (int i = n - 1; i >= 0; --i) {
       T *w = W(i);
-      T yF = w[J_F + r], yA = w[J_AB + r], yV = w[J_VB + r];
+      T yF = w[J_F + r], yA = w[J_AB + r], yV;
+      const T nv = w[J_VB + r];  // minus the Vbar term
       if (i + 1 < n) {
         const T *wn = W(i + 1);
         const T c0 = wn[J_G + 3 * k], c1 = wn[J_G + 3 * k + 1], c2 = wn[J_G + 3 * k + 2];
         const T pa = wn[J_G + 9 + ka], pbk = wn[J_G + 9 + kb];
         yF += bwd_c(F, c0, c1, c2, pa, pbk);
         yA += bwd_c(Ab, c0, c1, c2, pa, pbk);
-        yV += bwd_c(Vb, c0, c1, c2, pa, pbk);
+        yV = bwd_c(Vb, c0, c1, c2, pa, pbk) - nv;
+      } else {
+        yV = -nv;
       }
       gather(yF, F);
       gather(yA, Ab);
@@ -295,8 +287,7 @@ __global__ void __launch_bounds__(block_for<P>()) adjoint_rnea_kernel(KArgs A) {
     ldv<T, 6>(W(i) + J_A, Ai);
     sym6_apply(REC_(i) + REC_J, Ai, JA);
     sym6_apply(REC_(i) + REC_J, V, JV);
-    adT_apply(V, JV, c);
-    for (int k = 0; k < 6; ++k) JA[k] -= c[k];
+    adT_sub(V, JV, JA);
     stv<T, 6>(W(i) + J_FB, JA);
   }
   bwd(J_F, [&](int i, T *l) { ldv<T, 6>(W(i) + J_FB, l); });
@@ -342,20 +333,20 @@ __global__ void __launch_bounds__(block_for<P>()) adjoint_rnea_kernel(KArgs A) {
     ldv<T, 6>(w + J_AB, Ab);
     ldv<T, 6>(w + J_VB, Vb);
     const T qdi = pb.qd[i];
-    // ad_V e_1 = (0, w_z, -w_y; 0, v_z, -v_y)
-    const T adVe1[6] = {T(0), V[2], -V[1], T(0), V[5], -V[4]};
-    const T g_qd = Vb[0] + dot6(adVe1, Ab);
-    T t[6], u[6];
-    ad_e1(V, t);
-    T g_q = dot6(Vb, t);
-    for (int k = 0; k < 6; ++k) u[k] = Ai[k] - qdi * adVe1[k];
-    ad_e1(u, t);
-    g_q += dot6(Ab, t);
-    ad_e1(Fb, t);
-    g_q += dot6(t, F);
+    // with ad_V e_1 = (0, w_z, -w_y; 0, v_z, -v_y) and ad_{e_1} x = (0, -x_2, x_1;
+    // 0, -x_5, x_4), written out without the zero entries:
+    // -g_qd = -Vbar_0 - (ad_V e_1) . Abar
+    const T m_gqd = (((-Vb[0] - V[2] * Ab[1]) + V[1] * Ab[2]) - V[5] * Ab[4]) + V[4] * Ab[5];
+    // u = A - qd ad_V e_1 (components 1, 2, 4, 5; 0 and 3 are A's)
+    const T u1 = Ai[1] - qdi * V[2], u2 = Ai[2] + qdi * V[1];
+    const T u4 = Ai[4] - qdi * V[5], u5 = Ai[5] + qdi * V[4];
+    // g_q = Vbar . ad_{e_1} V + Abar . ad_{e_1} u + (ad_{e_1} Fbar) . F
+    T g_q = ((-Vb[1] * V[2] + Vb[2] * V[1]) - Vb[4] * V[5]) + Vb[5] * V[4];
+    g_q = (((g_q - Ab[1] * u2) + Ab[2] * u1) - Ab[4] * u5) + Ab[5] * u4;
+    g_q = (((g_q - F[1] * Fb[2]) + F[2] * Fb[1]) - F[4] * Fb[5]) + F[5] * Fb[4];
     // x_bar = -(d ID / d x)^T lambda; d ID / d q carries the minus of dX/dq
     qbar[i] = g_q;
-    qdbar[i] = -g_qd;
+    qdbar[i] = m_gqd;
     if (mbar) {
       T JmA[6], JmV[6], adVFb[6];
       dJdm_apply(REC_(i) + REC_J, Ai, JmA);
