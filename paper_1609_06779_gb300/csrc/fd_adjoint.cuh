@@ -80,17 +80,19 @@ __device__ __forceinline__ void adjoint_lanes(const Team<P> &tm, const Prob<T> &
   }
   tm.sync();
 
-  // component k of Ad_{g^-1} x: R^T w (top), R^T v + (R^T w) x (R^T p) (bottom)
+  // component k of Ad_{g^-1} x: R^T w (top), R^T v + (R^T w) x (R^T p) (bottom).
+  // Every lane runs the same FP64 instructions: operands are picked by selects and
+  // the callers pass pa = pbk = 0 on the lanes that take no cross product.
   auto fwd_c = [&](const T *x, T c0, T c1, T c2, T pa, T pbk) {
-    const T t = top ? c0 * x[0] + c1 * x[1] + c2 * x[2] : c0 * x[3] + c1 * x[4] + c2 * x[5];
+    const T t = c0 * (top ? x[0] : x[3]) + c1 * (top ? x[1] : x[4]) + c2 * (top ? x[2] : x[5]);
     const T oa = __shfl_sync(tm.mask, t, ka, P), ob = __shfl_sync(tm.mask, t, kb, P);
-    return top ? t : (t + oa * pbk) - ob * pa;
+    return (t + oa * pbk) - ob * pa;
   };
   // component k of Ad_{g^-1}^T y: R n + p x R f (top), R f (bottom)
   auto bwd_c = [&](const T *y, T c0, T c1, T c2, T pa, T pbk) {
-    const T t = top ? c0 * y[0] + c1 * y[1] + c2 * y[2] : c0 * y[3] + c1 * y[4] + c2 * y[5];
+    const T t = c0 * (top ? y[0] : y[3]) + c1 * (top ? y[1] : y[4]) + c2 * (top ? y[2] : y[5]);
     const T fa = __shfl_sync(tm.mask, t, 3 + ka, P), fb = __shfl_sync(tm.mask, t, 3 + kb, P);
-    return top ? (t + pa * fb) - pbk * fa : t;
+    return (t + pa * fb) - pbk * fa;
   };
   auto gather = [&](T v, T *full) {
 #pragma unroll
@@ -105,12 +107,13 @@ __device__ __forceinline__ void adjoint_lanes(const Team<P> &tm, const Prob<T> &
     for (int i = 0; i < n; ++i) {
       T *w = W(i);
       const T c0 = w[J_G + k], c1 = w[J_G + 3 + k], c2 = w[J_G + 6 + k];
-      const T pa = w[J_PT + ka], pbk = w[J_PT + kb];
+      const T pa = top ? T(0) : w[J_PT + ka], pbk = top ? T(0) : w[J_PT + kb];
       const T qdi = pb.qd[i];
       T y = fwd_c(V, c0, c1, c2, pa, pbk) + (r == 0 ? qdi : T(0));
       gather(y, V);
       if (store) w[J_V + r] = y;
-      const T cv = r == 1 ? V[2] : (r == 2 ? -V[1] : (r == 4 ? V[5] : (r == 5 ? -V[4] : T(0))));
+      const T cv = neg_if(r == 1 ? V[2] : (r == 2 ? V[1] : (r == 4 ? V[5] : (r == 5 ? V[4] : T(0)))),
+                          r == 2 || r == 5);
       y = fwd_c(Ac, c0, c1, c2, pa, pbk) + cv * qdi + (r == 0 ? pb.in3[i] : T(0));
       gather(y, Ac);
       if (store) w[J_A + r] = y;
@@ -156,7 +159,7 @@ __device__ __forceinline__ void adjoint_lanes(const Team<P> &tm, const Prob<T> &
       if (i + 1 < n) {
         const T *wn = W(i + 1);
         const T c0 = wn[J_G + 3 * k], c1 = wn[J_G + 3 * k + 1], c2 = wn[J_G + 3 * k + 2];
-        const T pa = wn[J_G + 9 + ka], pbk = wn[J_G + 9 + kb];
+        const T pa = top ? wn[J_G + 9 + ka] : T(0), pbk = top ? wn[J_G + 9 + kb] : T(0);
         yF += bwd_c(F, c0, c1, c2, pa, pbk);
         yA += bwd_c(Ab, c0, c1, c2, pa, pbk);
         yV = bwd_c(Vb, c0, c1, c2, pa, pbk) - nv;
@@ -167,7 +170,8 @@ __device__ __forceinline__ void adjoint_lanes(const Team<P> &tm, const Prob<T> &
       gather(yA, Ab);
       // - qd ad_{e_1}^T Abar = qd (0, -n_z, n_y; 0, -f_z, f_y)
       const T qdi = pb.qd[i];
-      const T ca = r == 1 ? -Ab[2] : (r == 2 ? Ab[1] : (r == 4 ? -Ab[5] : (r == 5 ? Ab[4] : T(0))));
+      const T ca = neg_if(r == 1 ? Ab[2] : (r == 2 ? Ab[1] : (r == 4 ? Ab[5] : (r == 5 ? Ab[4] : T(0)))),
+                          r == 1 || r == 4);
       yV += qdi * ca;
       gather(yV, Vb);
       if (store) {

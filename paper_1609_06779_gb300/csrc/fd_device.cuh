@@ -29,6 +29,15 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 // which the kernels' final finiteness check then reports
 __device__ __forceinline__ bool pos_t(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool pos_t(float x) { return __float_as_int(x) > 0; }
+// -x if f, else x: the sign bit flipped by an integer operation
+__device__ __forceinline__ double neg_if(double x, bool f) {
+  return __longlong_as_double(static_cast<long long>(
+      static_cast<unsigned long long>(__double_as_longlong(x)) ^ (static_cast<unsigned long long>(f) << 63)));
+}
+__device__ __forceinline__ float neg_if(float x, bool f) {
+  return __int_as_float(static_cast<int>(static_cast<unsigned>(__float_as_int(x)) ^
+                                         (static_cast<unsigned>(f) << 31)));
+}
 // 1 / x rounded to nearest (the same value as the IEEE division 1 / x)
 __device__ __forceinline__ double rcp_t(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }

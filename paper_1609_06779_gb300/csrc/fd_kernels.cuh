@@ -105,24 +105,27 @@ __device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, c
   T Ac[6] = {T(0), T(0), T(0), T(-grav[0]), T(-grav[1]), T(-grav[2])};
   for (int i = 0; i < n; ++i) {
     T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    // every lane runs the same FP64 instructions: operands are picked by selects
+    // and the cross-product coefficients are zero on the angular lanes
     const T c0 = w[W_G + k], c1 = w[W_G + 3 + k], c2 = w[W_G + 6 + k];
-    const T pa = w[W_PT + ka], pbk = w[W_PT + kb];
+    const T pa = top ? T(0) : w[W_PT + ka], pbk = top ? T(0) : w[W_PT + kb];
     const T qdi = pb.qd[i];
     const T e0 = (r == 0) ? qdi : T(0);
     // twist
-    T t = top ? c0 * V[0] + c1 * V[1] + c2 * V[2] : c0 * V[3] + c1 * V[4] + c2 * V[5];
+    T t = c0 * (top ? V[0] : V[3]) + c1 * (top ? V[1] : V[4]) + c2 * (top ? V[2] : V[5]);
     T oa = __shfl_sync(tm.mask, t, ka, P), ob = __shfl_sync(tm.mask, t, kb, P);
-    T y = top ? t + e0 : t + oa * pbk - ob * pa;
+    T y = ((t + e0) + oa * pbk) - ob * pa;
 #pragma unroll
     for (int j = 0; j < 6; ++j) V[j] = __shfl_sync(tm.mask, y, j, P);
     if (store) w[W_V + r] = y;
     // acceleration: + ad_{V_i} e_1 qd_i = (0, w_z, -w_y; 0, v_z, -v_y) qd_i (+ e_1 qdd_i)
-    const T cv = r == 1 ? V[2] : (r == 2 ? -V[1] : (r == 4 ? V[5] : (r == 5 ? -V[4] : T(0))));
+    const T cv = neg_if(r == 1 ? V[2] : (r == 2 ? V[1] : (r == 4 ? V[5] : (r == 5 ? V[4] : T(0)))),
+                        r == 2 || r == 5);
     const T a0 = (r == 0 && !mode_fd) ? pb.in3[i] : T(0);
-    t = top ? c0 * Ac[0] + c1 * Ac[1] + c2 * Ac[2] : c0 * Ac[3] + c1 * Ac[4] + c2 * Ac[5];
+    t = c0 * (top ? Ac[0] : Ac[3]) + c1 * (top ? Ac[1] : Ac[4]) + c2 * (top ? Ac[2] : Ac[5]);
     oa = __shfl_sync(tm.mask, t, ka, P);
     ob = __shfl_sync(tm.mask, t, kb, P);
-    y = top ? (t + a0) + cv * qdi : ((t + oa * pbk) - ob * pa) + cv * qdi;
+    y = (((t + a0) + oa * pbk) - ob * pa) + cv * qdi;
 #pragma unroll
     for (int j = 0; j < 6; ++j) Ac[j] = __shfl_sync(tm.mask, y, j, P);
     if (store) w[W_F + r] = y;
@@ -152,10 +155,11 @@ __device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, c
     if (i + 1 < n) {
       const T *wn = w + NT;
       const T c0 = wn[W_G + 3 * k], c1 = wn[W_G + 3 * k + 1], c2 = wn[W_G + 3 * k + 2];
-      const T pa = wn[W_G + 9 + ka], pbk = wn[W_G + 9 + kb];
-      const T t = top ? c0 * F[0] + c1 * F[1] + c2 * F[2] : c0 * F[3] + c1 * F[4] + c2 * F[5];
+      // the cross product only on the angular lanes (coefficients zero on the others)
+      const T pa = top ? wn[W_G + 9 + ka] : T(0), pbk = top ? wn[W_G + 9 + kb] : T(0);
+      const T t = c0 * (top ? F[0] : F[3]) + c1 * (top ? F[1] : F[4]) + c2 * (top ? F[2] : F[5]);
       const T fa = __shfl_sync(tm.mask, t, 3 + ka, P), fb = __shfl_sync(tm.mask, t, 3 + kb, P);
-      y = top ? ((t + pa * fb) - pbk * fa) + fi : t + fi;
+      y = ((t + pa * fb) - pbk * fa) + fi;
     }
 #pragma unroll
     for (int j = 0; j < 6; ++j) F[j] = __shfl_sync(tm.mask, y, j, P);
@@ -1709,14 +1713,22 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
   if constexpr (P < 16) {
     // operands of step i: tau_delta_i, g_i, row r of J_{i-1}
     TA nt_td = TA(0), nt_td2 = TA(0), nt_J[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    // g_i, and this lane's row k of R with p_{k+1}, p_{k+2} (zero on the linear
+    // lanes, which take no cross product in X^T), read by lane-dependent offsets
+    // from memory rather than by lane-dependent register indices
     SE3<T> nt_g;
     se3_identity(nt_g);
+    TA nt_rk[3] = {TA(0), TA(0), TA(0)}, nt_pka = TA(0), nt_pkb = TA(0);
     auto fetch = [&](int i) {
       const T *w = pb.wt + static_cast<int64_t>(i) * NT;
       nt_td = TA(w[W_TD]);
       if (TWO) nt_td2 = TA(td2[i]);
       if (i > 0) {
         ld_se3(w + W_G, nt_g);
+  #pragma unroll
+        for (int c = 0; c < 3; ++c) nt_rk[c] = TA(w[W_G + 3 * k + c]);
+        nt_pka = top ? TA(w[W_G + 9 + ka]) : TA(0);
+        nt_pkb = top ? TA(w[W_G + 9 + kb]) : TA(0);
         const T *J = pb.rec + static_cast<int64_t>(i - 1) * REC + REC_J;
   #pragma unroll
         for (int c = 0; c < 6; ++c) nt_J[c] = TA(J[s6(r, c)]);
@@ -1731,6 +1743,7 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
     }
     for (int i = n - 1; i >= 0; --i) {
       const TA td = nt_td, tdb = nt_td2;
+      const TA rk0 = nt_rk[0], rk1 = nt_rk[1], rk2 = nt_rk[2], pka = nt_pka, pkb = nt_pkb;
       SE3<TA> ga;
       TA Jr[6];
   #pragma unroll
@@ -1775,18 +1788,18 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
       TA pa[6];
   #pragma unroll
       for (int c = 0; c < 6; ++c) pa[c] = __shfl_sync(tm.mask, par_b, c, P);
-      const TA tb = top ? ga.R[3 * k] * pa[0] + ga.R[3 * k + 1] * pa[1] + ga.R[3 * k + 2] * pa[2]
-                        : ga.R[3 * k] * pa[3] + ga.R[3 * k + 1] * pa[4] + ga.R[3 * k + 2] * pa[5];
+      const TA tb = rk0 * (top ? pa[0] : pa[3]) + rk1 * (top ? pa[1] : pa[4]) +
+                    rk2 * (top ? pa[2] : pa[5]);
       const TA fa = __shfl_sync(tm.mask, tb, 3 + ka, P), fb = __shfl_sync(tm.mask, tb, 3 + kb, P);
-      pbr = top ? (tb + ga.p[ka] * fb) - ga.p[kb] * fa : tb;
+      pbr = (tb + pka * fb) - pkb * fa;
       if constexpr (TWO) {
         const TA pb2 = pbr2 + prow[0] * uD2;
 #pragma unroll
         for (int c = 0; c < 6; ++c) pa[c] = __shfl_sync(tm.mask, pb2, c, P);
-        const TA t2 = top ? ga.R[3 * k] * pa[0] + ga.R[3 * k + 1] * pa[1] + ga.R[3 * k + 2] * pa[2]
-                          : ga.R[3 * k] * pa[3] + ga.R[3 * k + 1] * pa[4] + ga.R[3 * k + 2] * pa[5];
+        const TA t2 = rk0 * (top ? pa[0] : pa[3]) + rk1 * (top ? pa[1] : pa[4]) +
+                      rk2 * (top ? pa[2] : pa[5]);
         const TA fa2 = __shfl_sync(tm.mask, t2, 3 + ka, P), fb2 = __shfl_sync(tm.mask, t2, 3 + kb, P);
-        pbr2 = top ? (t2 + ga.p[ka] * fb2) - ga.p[kb] * fa2 : t2;
+        pbr2 = (t2 + pka * fb2) - pkb * fa2;
       }
       tm.sync();
   #pragma unroll
