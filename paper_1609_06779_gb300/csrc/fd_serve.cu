@@ -90,6 +90,7 @@ struct Model {
 struct Req {
   uint64_t ticket = 0;
   int kind = 0, algo = 0, model = 0, n = 0, steps = 1, step = 0;
+  int adv = 0;  // rollout steps this tick
   int64_t mrec = 0;  // first record of the model (stable while the request holds it)
   double dt = 0.0;
   std::vector<double> q, qd, tau, w;  // tau: n (FD+grad) or steps x n (rollout)
@@ -140,12 +141,32 @@ int team_for(TeamKind k, int n) {
   if (k == kTeamABIA) return n <= 64 ? 8 : 16;
   return n <= 32 ? 8 : (n <= 64 ? 16 : (n <= 128 ? 32 : 64));
 }
+// Rollouts by length class, by algorithm and chain length only. A tick lasts
+// about as long as its longest chains' serial recursions (an ABIA step costs a
+// few microseconds per link on its critical lane), so the rollouts of a shorter
+// class take several steps in that time, about 160 link-steps per tick for ABIA:
+// each step is the same FD launch and Euler step as alone, on the class's own
+// side stream. The per-size baseline takes one step per tick.
+int roll_class(int algo, int n) {
+  if (algo == FD_ABIA) return n <= 20 ? 0 : (n <= 40 ? 1 : (n <= 64 ? 2 : 3));
+  return n <= 32 ? 0 : (n <= 64 ? 1 : (n <= 128 ? 2 : 3));
+}
+int substeps(int algo, int n) {
+  static const int kAbia[4] = {8, 4, 2, 1}, kCfa[4] = {4, 2, 1, 1};
+  return (algo == FD_ABIA ? kAbia : kCfa)[roll_class(algo, n)];
+}
 // side stream of a request, by algorithm and chain length only (its FD, adjoint
 // solve and reverse sweep launches all go there, in order): CFA length classes
 // on streams 0..3, ABIA up to 64 links on 4, longer ABIA on 5
 int aux_of(bool abia, int n) {
   if (abia) return n <= 64 ? 4 : 5;
   return n <= 32 ? 0 : (n <= 64 ? 1 : (n <= 128 ? 2 : 3));
+}
+// side stream of a rollout's steps: ABIA rollouts of up to 20 and 40 links on
+// streams 6 and 7, the others on their FD stream (behind its FD+gradient work)
+int roll_aux(int algo, int n) {
+  if (algo == FD_ABIA && n <= 40) return n <= 20 ? 6 : 7;
+  return aux_of(algo == FD_ABIA, n);
 }
 
 __global__ void scatter_kernel(const double *stage, const UpDesc *d, int nd, Arena A) {
@@ -259,12 +280,11 @@ struct fd_server_s {
   OutDesc *h_outd = nullptr;
   size_t c_prob = 0, c_moff = 0, c_soff = 0, c_stage = 0, c_out = 0, c_up = 0, c_outd = 0;
   cudaStream_t stream = nullptr;
-  // side streams of a tick: one per CFA team class and one for ABIA; a request's
-  // launches (FD, the linear solve of its adjoint, the reverse sweep) stay on one
-  // of them, in order, and the classes run concurrently
-  // one side stream per class: FD (with the adjoint's linear solve in the same
-  // elimination for FD+gradient requests) and then the reverse sweep, in order
-  static constexpr int kAux = 6;
+  // side streams of a tick, one per length class (four CFA, two ABIA, and two
+  // more for short ABIA rollouts); a request's launches (FD with its adjoint's
+  // linear solve in the same elimination, the reverse sweep, or a rollout's
+  // steps) stay on one of them, in order, and the classes run concurrently
+  static constexpr int kAux = 8;
   cudaStream_t aux[kAux] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
 
@@ -414,18 +434,30 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
 
   // 2. problem order: [CFA FD+grad | CFA rollout | ABIA FD+grad | ABIA rollout],
   // each sorted by length (the per-size mode launches one kernel per length)
+  // (rollouts: within a team class, by the steps they take this tick, so that the
+  // k-th step of the tick covers a prefix of the class)
+  const bool per_size = (S->flags & FD_SERVE_PER_SIZE) != 0;
   std::vector<Req *> groups[4];
   for (Req *r : act) {
     const bool first = r->step == 0;
     const int g = (r->algo == FD_CFA ? 0 : 2) + (r->kind == FD_REQ_ROLLOUT ? 1 : 0);
     if (r->kind == FD_REQ_FD_GRAD && !first) continue;  // finished last tick
+    r->adv = r->kind == FD_REQ_ROLLOUT
+                 ? std::min(per_size ? 1 : substeps(r->algo, r->n), r->steps - r->step)
+                 : 1;
     groups[g].push_back(r);
   }
   std::vector<Req *> all;
   int gstart[5] = {0, 0, 0, 0, 0};
   for (int g = 0; g < 4; ++g) {
-    std::stable_sort(groups[g].begin(), groups[g].end(),
-                     [](const Req *x, const Req *y) { return x->n > y->n; });
+    const int algo = g < 2 ? FD_CFA : FD_ABIA;
+    std::stable_sort(groups[g].begin(), groups[g].end(), [&](const Req *x, const Req *y) {
+      if (per_size || (g & 1) == 0) return x->n > y->n;
+      const int cx = roll_class(algo, x->n), cy = roll_class(algo, y->n);
+      if (cx != cy) return cx > cy;
+      if (x->adv != y->adv) return x->adv > y->adv;
+      return x->n > y->n;
+    });
     gstart[g] = static_cast<int>(all.size());
     all.insert(all.end(), groups[g].begin(), groups[g].end());
   }
@@ -450,34 +482,62 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
   if (e == cudaSuccess) e = cudaEventRecord(S->ev_fork, S->stream);
   for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k)
     e = cudaStreamWaitEvent(S->aux[k], S->ev_fork, 0);
+  auto fd_range = [&](int algo, int mode, int s, int c, int t, cudaStream_t st) {
+    fdk::KArgs a = base_args(S);
+    a.prob_chain = S->d_prob + s;
+    a.state_off = S->d_soff + s;
+    a.n_problems = c;
+    a.q = S->A.q;
+    a.qd = S->A.qd;
+    a.in3 = S->A.tau;
+    a.out = S->A.qdd;
+    a.in4 = S->A.w;     // MODE_FD2: lambda = M^-1 w beside qdd
+    a.out4 = S->A.tbar;
+    a.mode = mode;
+    a.status = S->d_status + s;
+    a.team = t;
+    a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
+    if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, st);
+    return fdk::launch_abia(a, 0, t, st);
+  };
   auto fd_launch = [&](int algo, int mode, int p0, int cnt) {
     const TeamKind k = algo == FD_CFA ? kTeamCFA : kTeamABIA;
     return over(S, all, p0, cnt, k, [&](int s, int c, int t) {
-      fdk::KArgs a = base_args(S);
-      a.prob_chain = S->d_prob + s;
-      a.state_off = S->d_soff + s;
-      a.n_problems = c;
-      a.q = S->A.q;
-      a.qd = S->A.qd;
-      a.in3 = S->A.tau;
-      a.out = S->A.qdd;
-      a.in4 = S->A.w;     // MODE_FD2: lambda = M^-1 w beside qdd
-      a.out4 = S->A.tbar;
-      a.mode = mode;
-      a.status = S->d_status + s;
-      a.team = t;
-      cudaStream_t st = S->aux[aux_of(algo != FD_CFA, all[s]->n)];
-      a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
-      if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, st);
-      return fdk::launch_abia(a, 0, t, st);
+      return fd_range(algo, mode, s, c, t, S->aux[aux_of(algo != FD_CFA, all[s]->n)]);
     });
   };
-  // FD+gradient requests: qdd and lambda = M^-1 w in one elimination (MODE_FD2);
-  // rollouts: qdd
+  // rollouts: per team class, step j of the tick (FD, then one semi-implicit Euler
+  // step) over the class's requests that take more than j steps, a prefix of it;
+  // all on the class's side stream, in order
+  auto roll_launch = [&](int algo, int p0, int cnt) -> cudaError_t {
+    const TeamKind k = algo == FD_CFA ? kTeamCFA : kTeamABIA;
+    int s = p0;
+    while (s < p0 + cnt) {
+      const int rc = roll_class(algo, all[s]->n);
+      int e2 = s + 1;
+      while (e2 < p0 + cnt &&
+             (per_size ? all[e2]->n == all[s]->n : roll_class(algo, all[e2]->n) == rc))
+        ++e2;
+      const int c = e2 - s, t = team_for(k, all[s]->n);
+      cudaStream_t st = S->aux[roll_aux(algo, all[s]->n)];
+      for (int j = 0; j < all[s]->adv; ++j) {
+        int cj = 0;
+        while (cj < c && all[s + cj]->adv > j) ++cj;
+        S->launches += 2;
+        cudaError_t err = fd_range(algo, fdk::MODE_FD, s, cj, t, st);
+        if (err != cudaSuccess) return err;
+        rollout_step_kernel<<<(cj + 3) / 4, 128, 0, st>>>(S->d_prob + s, S->d_moff,
+                                                          S->d_soff + s, cj, S->A);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+      }
+      s = e2;
+    }
+    return cudaSuccess;
+  };
+  // FD+gradient requests: qdd and lambda = M^-1 w in one elimination (MODE_FD2)
   if (e == cudaSuccess) e = fd_launch(FD_CFA, fdk::MODE_FD2, gstart[0], gstart[1] - gstart[0]);
-  if (e == cudaSuccess) e = fd_launch(FD_CFA, fdk::MODE_FD, gstart[1], gstart[2] - gstart[1]);
   if (e == cudaSuccess) e = fd_launch(FD_ABIA, fdk::MODE_FD2, gstart[2], gstart[3] - gstart[2]);
-  if (e == cudaSuccess) e = fd_launch(FD_ABIA, fdk::MODE_FD, gstart[3], gstart[4] - gstart[3]);
   auto reverse = [&](int p0, int cnt, bool abia) {
     return over(S, all, p0, cnt, kTeamReverse, [&](int s, int c, int t) {
       fdk::KArgs a = base_args(S);
@@ -498,27 +558,22 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
   };
   if (e == cudaSuccess) e = reverse(gstart[0], gstart[1] - gstart[0], false);
   if (e == cudaSuccess) e = reverse(gstart[2], gstart[3] - gstart[2], true);
+  // rollouts: their steps of this tick, queued behind the FD+gradient work of the
+  // same side stream
+  if (e == cudaSuccess) e = roll_launch(FD_CFA, gstart[1], gstart[2] - gstart[1]);
+  if (e == cudaSuccess) e = roll_launch(FD_ABIA, gstart[3], gstart[4] - gstart[3]);
   for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k) {
     e = cudaEventRecord(S->ev_join[k], S->aux[k]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->stream, S->ev_join[k], 0);
   }
 
-  // 4. which requests finish this tick; rollouts advance one step
+  // 4. which requests finish this tick (rollouts advanced on their side streams)
   std::vector<Req *> done;
   for (int g = 0; g < 4; ++g)
     for (int p = gstart[g]; p < gstart[g + 1]; ++p) {
       Req *r = all[p];
-      if (r->kind == FD_REQ_FD_GRAD || r->step + 1 >= r->steps) done.push_back(r);
+      if (r->kind == FD_REQ_FD_GRAD || r->step + r->adv >= r->steps) done.push_back(r);
     }
-  auto roll = [&](int p0, int cnt) {
-    if (cnt <= 0) return cudaSuccess;
-    ++S->launches;
-    rollout_step_kernel<<<(cnt + 3) / 4, 128, 0, S->stream>>>(S->d_prob + p0, S->d_moff,
-                                                                S->d_soff + p0, cnt, S->A);
-    return cudaGetLastError();
-  };
-  if (e == cudaSuccess) e = roll(gstart[1], gstart[2] - gstart[1]);
-  if (e == cudaSuccess) e = roll(gstart[3], gstart[4] - gstart[3]);
 
   // 5. gather the finished requests' results into one download
   int64_t out_len = 0;
@@ -559,8 +614,8 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
   S->ticks += 1;
   S->busy_s += t1 - t0;
   for (Req *r : all) {
-    S->link_solves += r->n;
-    if (r->kind == FD_REQ_ROLLOUT) r->step += 1;
+    S->link_solves += static_cast<double>(r->n) * r->adv;
+    if (r->kind == FD_REQ_ROLLOUT) r->step += r->adv;
   }
   for (size_t k = 0; k < done.size(); ++k) {
     Req *r = done[k];
