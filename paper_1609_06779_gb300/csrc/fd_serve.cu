@@ -132,13 +132,17 @@ struct Arena {
 };
 
 // Teams depend on a request's algorithm and chain length only, so its arithmetic
-// does not depend on the mix. CFA and the reverse sweep take about one lane per
-// four links (8..64): long chains bound a tick's latency, and a small team
-// leaves a 256-link chain's OEE levels serial on eight lanes. ABIA takes 8 up to
-// 64 links and 16 (its twelve-lane step) beyond.
+// does not depend on the mix. They are chosen for latency, since a tick lasts as
+// long as its longest chains' solves: CFA takes about one lane per two links
+// beyond 32 (8, 32, 64, 128: a 256-link chain's FD in 0.46 ms on 128 lanes
+// against 0.82 ms on 64, measured in batches of 48), ABIA 16 up to 64 links and
+// 32 beyond (its twelve-lane step: 64 links 0.31 against 0.42 ms on 8 lanes, 256
+// links 0.84 against 0.95 ms on 16), the reverse sweep about one lane per four
+// links (8..64).
 enum TeamKind { kTeamCFA, kTeamReverse, kTeamABIA };
 int team_for(TeamKind k, int n) {
-  if (k == kTeamABIA) return n <= 64 ? 8 : 16;
+  if (k == kTeamABIA) return n <= 64 ? 16 : 32;
+  if (k == kTeamCFA) return n <= 32 ? 8 : (n <= 64 ? 32 : (n <= 128 ? 64 : 128));
   return n <= 32 ? 8 : (n <= 64 ? 16 : (n <= 128 ? 32 : 64));
 }
 // Rollouts by length class, by algorithm and chain length only. A tick lasts

@@ -126,7 +126,9 @@ def test_served_results_agree_with_the_batch_api_and_oracle():
         m = models[r["model"]]
         cs = fd.ChainSet(m)
         b = fd.Batch(cs)
-        team = 8 if (r["algo"] == "abia" or m.n_links_total <= 32) else 16  # the server's rule
+        n = m.n_links_total  # the server's rule
+        team = (16 if n <= 64 else 32) if r["algo"] == "abia" else (
+            8 if n <= 32 else (32 if n <= 64 else (64 if n <= 128 else 128)))
         if r["kind"] == "grad":
             ref = oracle.fd(m, r["q"], r["qd"], r["tau"])
             assert np.abs(res["qddot"] - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1.0)
