@@ -258,13 +258,15 @@ fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const void *qdot,
  * A server owns one device allocation of mem_budget_bytes (its memory budget)
  * and a worker thread. Chain models are registered once and stay resident.
  * Requests name a model and carry their state; they are admitted in arrival
- * order as link slots and memory free up, and every tick the worker runs one
- * forward-dynamics launch per algorithm over all admitted requests ("continuous
- * batching": requests arriving while others are on the GPU join the next tick),
- * the adjoint over new FD+gradient requests and one integration step over the
- * rollouts. Not in the paper (its experiments solve fixed groups); built on the
- * same kernels as fd_solve_batch and fd_solve_adjoint, FP64 only, with a fixed
- * team per algorithm so a request's arithmetic does not depend on the mix.
+ * order as link slots and memory free up, and every tick the worker runs the
+ * forward dynamics of all admitted requests, one launch per algorithm and length
+ * class ("continuous batching": requests arriving while others are on the GPU
+ * join the next tick), the adjoint over new FD+gradient requests, and the
+ * rollouts' integration steps (one per tick for the longest chains, several for
+ * shorter ones, by length class). Not in the paper (its experiments solve fixed
+ * groups); built on the same kernels as fd_solve_batch and fd_solve_adjoint,
+ * FP64 only, with teams and steps per tick set by a request's algorithm and
+ * chain length alone, so its arithmetic does not depend on the mix.
  */
 typedef struct fd_server_s *fd_server_t;
 
