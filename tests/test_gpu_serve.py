@@ -149,6 +149,38 @@ def test_served_results_agree_with_the_batch_api_and_oracle():
     srv.close()
 
 
+def test_rollouts_over_several_ticks_follow_the_euler_loop():
+    """Rollouts longer than a tick's steps (shorter chains take several steps per
+    tick, the longest one) end where a semi-implicit Euler loop over the oracle
+    does, for every length class and both algorithms."""
+    from paper_1609_06779_gb300 import fd
+    rng = np.random.default_rng(9)
+    lengths = [6, 18, 30, 50, 90]
+    models = [synth.random_chains([n], seed=900 + k) for k, n in enumerate(lengths)]
+    srv = fd.Server(budget_bytes=128 << 20)
+    ids = [srv.add_model(m) for m in models]
+    reqs = []
+    for k, n in enumerate(lengths):
+        for algo in ("abia", "cfa"):
+            st = synth.random_states(n, seed=9000 + 10 * k + len(reqs))
+            steps = 23 if algo == "abia" else 11
+            reqs.append(dict(kind="rollout", model=k, q=st.q, qd=st.qdot,
+                             taus=rng.standard_normal((steps, n)) * 10, dt=1e-3, algo=algo))
+    out = _run(srv, ids, reqs)
+    for r, res in zip(reqs, out):
+        m = models[r["model"]]
+        q, qd = r["q"].copy(), r["qd"].copy()
+        for tau in r["taus"]:
+            qdd = oracle.fd(m, q, qd, tau)
+            qd = qd + r["dt"] * qdd
+            q = q + r["dt"] * qd
+        assert res["status"] == 0 and res["steps_done"] == len(r["taus"])
+        np.testing.assert_allclose(res["q"], q, rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(res["qdot"], qd, rtol=1e-9, atol=1e-9)
+        np.testing.assert_allclose(res["qddot"], qdd, rtol=1e-9, atol=1e-9)
+    srv.close()
+
+
 def test_admission_under_a_small_budget_and_timeouts():
     from paper_1609_06779_gb300 import fd
     srv = fd.Server(budget_bytes=16 << 20)       # a few thousand link slots
