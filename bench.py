@@ -657,8 +657,11 @@ def main():
                 stream.wait_event(join)
 
         ms = _time_ms(step3, reps=5, warm=2)
+        torch.cuda.synchronize()
+        same3 = all(torch.equal(out[a].cpu(), acc_outs[f"{a}_fp64"]) for a in ALGOS)
         variants["step_three_streams_fp64"] = {"ms": ms,
-                                               "solves_per_s": 3 * args.chains / (ms * 1e-3)}
+                                               "solves_per_s": 3 * args.chains / (ms * 1e-3),
+                                               "results_equal_device_step": same3}
     # FP32 and mixed variants of each algorithm (context; not part of the step)
     if rank == 0:
         q32, qd32, tau32 = (x.float() for x in (q, qd, tau))
