@@ -1292,6 +1292,7 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
   TA *vec = static_cast<TA *>(A.ws_a) + s0 * NA_JSIIA + A.sq_off[pb.p] * NSQ_JSIIA;
   TA *H = vec + n;                                   // h_i = I^c_i e_1, [n][6]
   TA *vec2 = vec + 7 * static_cast<int64_t>(n);      // MODE_FD2: second right-hand side
+  TA *Sb = vec + 8 * static_cast<int64_t>(n);        // teams of 1..4: s_i, [n][6]
   TA *const vec1 = vec;
   const bool two = A.mode == MODE_FD2;
   TA *M = vec + static_cast<int64_t>(n) * NA_JSIIA;  // n x n, column-major, lower triangle
@@ -1396,20 +1397,79 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
   }
   tm.sync();
 
-  // lower triangle, row by row: row i costs i transports, so lanes take rows in
-  // snake order (round t: t P + r, then t P + P - 1 - r) to balance the work
-  for (int t = 0; t * P < n; ++t) {
-    const int i = t * P + ((t & 1) ? (P - 1 - tm.r) : tm.r);
-    if (i >= n) continue;
-    TA z[6];
+  // lower triangle, row by row: row i costs i transports (or dot products), so
+  // lanes take rows in snake order (round t: t P + r, then t P + P - 1 - r) to
+  // balance the work
+  if constexpr (P <= 4) {
+    // Teams of up to four lanes pair vectors in the base frame instead: with
+    // s_k = Ad_{g_0k} e_1 (joint k's axis as a base-frame twist) and
+    // F_i = Ad_{g_0i^{-1}}^T h_i (the composite force h_i in base coordinates),
+    // M[i][k] = s_k . F_i, the same power pairing as in frame k: one 6-term dot
+    // product per entry instead of one SE(3) transport. Every lane runs the
+    // forward kinematics g_0i = g_0,i-1 g_{i-1,i}; lane r forms s_i and F_i for
+    // the links i = r mod P (F_i over h_i).
+    SE3<TA> g0;
+    se3_identity(g0);
+    for (int i = 0; i < n; ++i) {
+      SE3<TA> gi;
+      load_g(i, gi);
+      SE3<TA> t;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) z[c] = H[static_cast<int64_t>(i) * 6 + c];
-    Mat(i, i) = z[0];
-    for (int j = i; j >= 1; --j) {
-      SE3<TA> ga;
-      load_g(j, ga);
-      adinvT(ga, z, z);
-      Mat(i, j - 1) = z[0];
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          t.R[3 * a + b] = (g0.R[3 * a] * gi.R[b] + g0.R[3 * a + 1] * gi.R[3 + b]) +
+                           g0.R[3 * a + 2] * gi.R[6 + b];
+        t.p[a] = ((g0.p[a] + g0.R[3 * a] * gi.p[0]) + g0.R[3 * a + 1] * gi.p[1]) +
+                 g0.R[3 * a + 2] * gi.p[2];
+      }
+      g0 = t;
+      if ((i & (P - 1)) == tm.r) {
+        const TA ax = g0.R[0], ay = g0.R[3], az = g0.R[6];  // R_0i e_1
+        TA *sv = Sb + static_cast<int64_t>(i) * 6;
+        sv[0] = ax;
+        sv[1] = ay;
+        sv[2] = az;
+        sv[3] = g0.p[1] * az - g0.p[2] * ay;  // p_0i x R_0i e_1
+        sv[4] = g0.p[2] * ax - g0.p[0] * az;
+        sv[5] = g0.p[0] * ay - g0.p[1] * ax;
+        TA *hv = H + static_cast<int64_t>(i) * 6;
+        TA h[6], f[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) h[c] = hv[c];
+        Mat(i, i) = h[0];
+        adinvT(g0, h, f);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) hv[c] = f[c];
+      }
+    }
+    tm.sync();
+    for (int t = 0; t * P < n; ++t) {
+      const int i = t * P + ((t & 1) ? (P - 1 - tm.r) : tm.r);
+      if (i >= n) continue;
+      TA f[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) f[c] = H[static_cast<int64_t>(i) * 6 + c];
+      for (int k = 0; k < i; ++k) {
+        const TA *sv = Sb + static_cast<int64_t>(k) * 6;
+        Mat(i, k) = (((((sv[0] * f[0] + sv[1] * f[1]) + sv[2] * f[2]) + sv[3] * f[3]) +
+                      sv[4] * f[4]) + sv[5] * f[5]);
+      }
+    }
+  } else {
+    for (int t = 0; t * P < n; ++t) {
+      const int i = t * P + ((t & 1) ? (P - 1 - tm.r) : tm.r);
+      if (i >= n) continue;
+      TA z[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) z[c] = H[static_cast<int64_t>(i) * 6 + c];
+      Mat(i, i) = z[0];
+      for (int j = i; j >= 1; --j) {
+        SE3<TA> ga;
+        load_g(j, ga);
+        adinvT(ga, z, z);
+        Mat(i, j - 1) = z[0];
+      }
     }
   }
   tm.sync();

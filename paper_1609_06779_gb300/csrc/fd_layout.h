@@ -56,8 +56,9 @@ constexpr int A_Z2 = 190;   // J^{-1} (I - Gamma)^T F products (6)
 constexpr int NA_CFA = 196;
 
 // JSIIA: per-link TA entries (right-hand side 1, h_i = I^c_i e_1 6, the second
-// right-hand side of MODE_FD2 1) and n*n TA entries (M).
-constexpr int NA_JSIIA = 8;
+// right-hand side of MODE_FD2 1, joint i's axis as a base-frame twist s_i 6) and
+// n*n TA entries (M).
+constexpr int NA_JSIIA = 14;
 constexpr int NSQ_JSIIA = 1;
 
 // ABIA: per-link TA entries: h_i = P_i S_i (6), 1 / D_i (1), u_i / D_i (1), and

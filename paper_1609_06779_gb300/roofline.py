@@ -45,10 +45,12 @@ def abia_flops(n: int) -> int:
 
 def jsiia_flops(n: int) -> int:
     """ID + the composite inertias of the unit-acceleration columns (n - 1
-    congruences X^T I X: 12 transports, + J 21) + one transport per entry below
-    the diagonal of M + Cholesky n^3/3 + two triangular solves 2 n^2."""
+    congruences X^T I X: 12 transports, + J 21) + the entries of M below the
+    diagonal as base-frame pairings (per link: forward kinematics 63, the joint
+    axis as a base-frame twist 9, the composite force to the base frame 42; per
+    entry a 6-term dot product 11) + Cholesky n^3/3 + two triangular solves 2 n^2."""
     composite = max(n - 1, 0) * (12 * ADJ + 21)
-    entries = ADJ * n * (n - 1) // 2
+    entries = n * (63 + 9 + ADJ) + 11 * n * (n - 1) // 2
     return id_flops(n) + composite + entries + (n ** 3) // 3 + 2 * n * n
 
 
