@@ -1400,14 +1400,17 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
   // lower triangle, row by row: row i costs i transports (or dot products), so
   // lanes take rows in snake order (round t: t P + r, then t P + P - 1 - r) to
   // balance the work
-  if constexpr (P <= 4) {
+  if constexpr (P <= 4 && std::is_same<T, double>::value) {
     // Teams of up to four lanes pair vectors in the base frame instead: with
     // s_k = Ad_{g_0k} e_1 (joint k's axis as a base-frame twist) and
     // F_i = Ad_{g_0i^{-1}}^T h_i (the composite force h_i in base coordinates),
     // M[i][k] = s_k . F_i, the same power pairing as in frame k: one 6-term dot
     // product per entry instead of one SE(3) transport. Every lane runs the
     // forward kinematics g_0i = g_0,i-1 g_{i-1,i}; lane r forms s_i and F_i for
-    // the links i = r mod P (F_i over h_i).
+    // the links i = r mod P (F_i over h_i). The base-frame terms grow with the
+    // distance from the base and cancel in the pairing, which costs digits in
+    // proportion: FP64 only (with joint transforms rounded to FP32, the mixed
+    // mode's entries would lose about two digits).
     SE3<TA> g0;
     se3_identity(g0);
     for (int i = 0; i < n; ++i) {
