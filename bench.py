@@ -14,6 +14,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -553,8 +554,7 @@ def main():
         step()
     torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    clk = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                              else ".", f".clocks_rank{rank}.csv"), local)
+    clk = Clocks(os.path.join(tempfile.gettempdir(), f"fd_bench_clocks_{os.getpid()}.csv"), local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()

@@ -54,8 +54,10 @@ typedef enum fd_algo {
 typedef enum fd_prec {
   FD_FP64 = 0,  /* states and all arithmetic in double */
   FD_FP32 = 1,  /* states and all arithmetic in float */
-  FD_MIXED = 2  /* float states and arithmetic; the OEE elimination, the
-                   articulated-inertia recursion and the JSIIA Cholesky in double */
+  FD_MIXED = 2  /* float states, joint transforms and inverse dynamics (the bias
+                   torque); in double: CFA's blocks of A, R = -B tau_delta, the OEE
+                   elimination and CalcAcc (from the double model copy), the
+                   articulated-inertia recursion and the JSIIA Cholesky */
 } fd_prec;
 
 typedef enum fd_status {
@@ -236,18 +238,21 @@ fd_status fd_solve_adjoint(fd_batch_t batch, const void *q, const void *qdot, co
  *
  * Problem p is chain p of `chain` (no batch plan); q, qdot, tau (inputs) and
  * qddot (output) are device arrays of the chain set's total link count, packed
- * in chain order, double for FD_FP64 and float for FD_FP32 / FD_MIXED. team and
- * status as for fd_solve_batch. Limits: at most 65 536 chains, and the CFA
- * workspace of all links must fit in 32 MiB - 256 KiB (FD_FP64: 1 824 bytes per
- * link, about 18 000 links; FD_MIXED about 19 000; FD_FP32 about 36 000); larger sets
- * return FD_ERR_INVALID_ARG with the sizes in fd_last_error().
+ * in chain order, double for FD_FP64 and float for FD_FP32 / FD_MIXED. team: 0
+ * or a power of two from 1 to 256, as for fd_solve_batch (team 0 takes the
+ * default fd_solve_batch uses for a batch plan that was not autotuned); the
+ * result equals fd_solve_batch's at the same team bit for bit. status as for
+ * fd_solve_batch. Limit: the CFA workspace of all links must fit in 32 MiB
+ * (FD_FP64: 1 824 bytes per link, about 18 000 links; FD_MIXED about 19 000;
+ * FD_FP32 about 36 000); larger sets return FD_ERR_INVALID_ARG with the sizes
+ * in fd_last_error().
  *
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress and copies a constant problem map into it (synchronous);
- * make that first call before any stream capture. Every call shares the one
- * array and leaves its contents behind; nothing in it has to start at zero, but
- * calls whose kernels overlap on the GPU (other streams, other host threads)
- * race on it and must be serialised by the caller.
+ * cudaGetSymbolAddress (host side only; nothing is copied to the device); make
+ * that first call before any stream capture. Every call shares the one array
+ * and leaves its contents behind; nothing in it has to start at zero, but calls
+ * whose kernels overlap on the GPU (other streams, other host threads) race on
+ * it and must be serialised by the caller.
  */
 fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const void *qdot,
                               const void *tau, void *qddot, fd_prec prec, int32_t team,

@@ -216,6 +216,25 @@ fd_status fdk_pack_chain(int64_t first, int64_t n, const double *joint_axes,
 // translation units.
 fd_status fdk_fail(fd_status st, const char *msg) { return fail(st, "%s", msg); }
 
+int fdk_default_team(int32_t algo, int64_t n_problems, int32_t max_links) {
+  // ABIA: one thread per problem once a warp per FP64 unit (152 SMs x 4) is
+  // busy with 32 problems each; below that, spread each step over a team of 8
+  if (algo == FD_ABIA) return n_problems > 152 * 4 * 8 ? 1 : 8;
+  // about four resident warps' worth of lanes per FP64 unit of the GPU
+  // (152 SMs x 2048 threads), but no more lanes than links and at most 256
+  const long long want = 152LL * 2048;
+  long long per = n_problems > 0 ? want / n_problems : 1;
+  int p = pow2_floor(std::max<long long>(per, 1));
+  int cap = 1;
+  while (cap < max_links && cap < 256) cap *= 2;
+  return std::min(p, cap);
+}
+
+bool fdk_valid_team(int t) {
+  return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32 || t == 64 || t == 128 ||
+         t == 256;
+}
+
 extern "C" {
 
 const char *fd_last_error(void) { return g_err.c_str(); }
@@ -447,17 +466,7 @@ int resolve_team(const fd_batch_s *b, int32_t algo, fd_prec prec, int32_t team) 
   if (team > 0) return team;
   const int tuned = (algo >= 0 && algo < 4 && prec >= 0 && prec < 3) ? b->tuned[algo][prec] : 0;
   if (tuned > 0) return tuned;
-  // ABIA: one thread per problem once a warp per FP64 unit (152 SMs x 4) is
-  // busy with 32 problems each; below that, spread each step over a team of 8
-  if (algo == FD_ABIA) return b->n_problems > 152 * 4 * 8 ? 1 : 8;
-  // about four resident warps' worth of lanes per FP64 unit of the GPU
-  // (152 SMs x 2048 threads), but no more lanes than links and at most 256
-  const long long want = 152LL * 2048;
-  long long per = b->n_problems > 0 ? want / b->n_problems : 1;
-  int p = pow2_floor(std::max<long long>(per, 1));
-  int cap = 1;
-  while (cap < b->max_links && cap < 256) cap *= 2;
-  return std::min(p, cap);
+  return fdk_default_team(algo, b->n_problems, b->max_links);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -479,10 +488,7 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int /*team: no l
   return w;
 }
 
-bool valid_team(int t) {
-  return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32 || t == 64 || t == 128 ||
-         t == 256;
-}
+bool valid_team(int t) { return fdk_valid_team(t); }
 
 }  // namespace
 
@@ -520,6 +526,7 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   const int prec_k = prec == FD_FP64 ? 0 : (prec == FD_FP32 || algo == -1 ? 1 : 2);
   fdk::KArgs a{};
   a.model = prec == FD_FP64 ? b->chain->d_model64 : b->chain->d_model32;
+  a.model64 = b->chain->d_model64;
   a.model_off = b->chain->d_off;
   a.prob_chain = b->d_prob_chain;
   a.state_off = b->d_state_off;
@@ -616,6 +623,7 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
 
   fdk::KArgs a{};
   a.model = prec == FD_FP64 ? b->chain->d_model64 : b->chain->d_model32;
+  a.model64 = b->chain->d_model64;
   a.model_off = b->chain->d_off;
   a.prob_chain = b->d_prob_chain;
   a.state_off = b->d_state_off;

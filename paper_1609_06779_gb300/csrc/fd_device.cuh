@@ -213,12 +213,13 @@ __device__ __forceinline__ void joint_transform(const T *rec, T q, SE3<T> &g) {
 
 // ------------------------------------------------------------ load / store
 
-template <class T>
-__device__ __forceinline__ void ld_se3(const T *src, SE3<T> &g) {
+// (converting when the stored type S differs from the arithmetic type T)
+template <class S, class T>
+__device__ __forceinline__ void ld_se3(const S *src, SE3<T> &g) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) g.R[k] = src[k];
+  for (int k = 0; k < 9; ++k) g.R[k] = T(src[k]);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) g.p[k] = src[9 + k];
+  for (int k = 0; k < 3; ++k) g.p[k] = T(src[9 + k]);
 }
 template <class T>
 __device__ __forceinline__ void st_se3(T *dst, const SE3<T> &g) {

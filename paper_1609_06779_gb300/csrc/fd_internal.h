@@ -37,6 +37,13 @@ struct fd_batch_s {
 // Sets the calling thread's fd_last_error message and returns st.
 fd_status fdk_fail(fd_status st, const char *msg);
 
+// The team size used when a caller passes team 0 and nothing was autotuned: a
+// size that fills the GPU for n_problems problems of up to max_links links.
+int fdk_default_team(int32_t algo, int64_t n_problems, int32_t max_links);
+
+// Team sizes the kernels are built for: powers of two from 1 to 256.
+bool fdk_valid_team(int t);
+
 // Packs one chain's model records in canonical link frames (see fd_abi.cu).
 fd_status fdk_pack_chain(int64_t first, int64_t n, const double *joint_axes,
                          const double *link_frames, const double *spatial_inertias, double *rec,

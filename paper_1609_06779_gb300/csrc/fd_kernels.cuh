@@ -18,6 +18,7 @@ struct Prob {
   int n;          // links
   int a, b;       // this lane's segment [a, b)
   const T *rec;   // model records of the chain
+  int64_t m0;     // the chain's first record in the arena
   const T *q, *qd, *in3;
   T *out;
   T *wt;          // T workspace of the problem [n][NT]
@@ -29,7 +30,7 @@ __device__ __forceinline__ bool load_problem(const KArgs &A, const Team<P> &tm, 
   const long long team = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) / P;
   if (team >= A.n_problems) return false;
   const int p = A.order ? A.order[team] : static_cast<int>(team);
-  const int c = A.prob_chain[p];
+  const int c = A.prob_chain ? A.prob_chain[p] : p;  // no map: problem p is chain p
   const int64_t m0 = A.model_off[c];
   const int n = static_cast<int>(A.model_off[c + 1] - m0);
   const int64_t s0 = A.state_off[p];
@@ -39,6 +40,7 @@ __device__ __forceinline__ bool load_problem(const KArgs &A, const Team<P> &tm, 
   pb.a = min(tm.r * S, n);
   pb.b = min(pb.a + S, n);
   pb.rec = static_cast<const T *>(A.model) + m0 * REC;
+  pb.m0 = m0;
   pb.q = static_cast<const T *>(A.q) + s0;
   pb.qd = static_cast<const T *>(A.qd) + s0;
   pb.in3 = static_cast<const T *>(A.in3) + s0;
@@ -76,7 +78,8 @@ __device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, c
                                          int mode) {
   static_assert(P >= 8 && P <= 32, "component lanes need a team of 8..32 lanes");
   const int n = pb.n;
-  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2;
+  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2 || mode == MODE_RES;
+  const T *qdd_in = mode == MODE_ID ? pb.in3 : (mode == MODE_RES ? pb.out : nullptr);
   const int r = tm.r < 6 ? tm.r : 5;
   const bool top = r < 3;
   const int k = top ? r : r - 3;
@@ -121,7 +124,7 @@ __device__ __forceinline__ void id_lanes(const Team<P> &tm, const Prob<T> &pb, c
     // acceleration: + ad_{V_i} e_1 qd_i = (0, w_z, -w_y; 0, v_z, -v_y) qd_i (+ e_1 qdd_i)
     const T cv = neg_if(r == 1 ? V[2] : (r == 2 ? V[1] : (r == 4 ? V[5] : (r == 5 ? V[4] : T(0)))),
                         r == 2 || r == 5);
-    const T a0 = (r == 0 && !mode_fd) ? pb.in3[i] : T(0);
+    const T a0 = (r == 0 && qdd_in) ? qdd_in[i] : T(0);
     t = c0 * (top ? Ac[0] : Ac[3]) + c1 * (top ? Ac[1] : Ac[4]) + c2 * (top ? Ac[2] : Ac[5]);
     oa = __shfl_sync(tm.mask, t, ka, P);
     ob = __shfl_sync(tm.mask, t, kb, P);
@@ -181,7 +184,8 @@ __device__ __forceinline__ void id_pair(const Team<P> &tm, const Prob<T> &pb, co
                                         int mode) {
   static_assert(P == 2, "the component pair is a team of two lanes");
   const int n = pb.n;
-  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2;
+  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2 || mode == MODE_RES;
+  const T *qdd_in = mode == MODE_ID ? pb.in3 : (mode == MODE_RES ? pb.out : nullptr);
   const bool h = tm.r != 0;  // false: components 0..2, true: 3..5
   auto xch = [&](T v) { return __shfl_xor_sync(tm.mask, v, 1); };
 
@@ -235,7 +239,7 @@ __device__ __forceinline__ void id_pair(const Team<P> &tm, const Prob<T> &pb, co
     for (int k = 0; k < 3; ++k) t[k] = R[k] * ax[0] + R[3 + k] * ax[1] + R[6 + k] * ax[2];
 #pragma unroll
     for (int k = 0; k < 3; ++k) o[k] = xch(t[k]);
-    const T a0 = (!h && !mode_fd) ? pb.in3[i] : T(0);
+    const T a0 = (!h && qdd_in) ? qdd_in[i] : T(0);
     ax[0] = ((t[0] + a0) + o[1] * pt2) - o[2] * pt1;
     ax[1] = ((t[1] + o[2] * pt0) - o[0] * pt2) + v2 * qdi;
     ax[2] = ((t[2] + o[0] * pt1) - o[1] * pt0) - v1 * qdi;
@@ -295,8 +299,9 @@ __device__ __forceinline__ void id_pair(const Team<P> &tm, const Prob<T> &pb, co
 // Eq. 2a-2d for one problem: the twist and acceleration recursions (forward,
 // block lower bi-diagonal) and the force recursion (backward, block upper
 // bi-diagonal), each as a segmented scan over SE(3)-affine operators.
-//   mode_fd = true:  qdd = 0 and gravity; writes tau_delta_i = tau_i - tau_bias_i
-//   mode_fd = false: qdd = in3;           writes tau_i
+//   MODE_FD, MODE_FD2: qdd = 0 and gravity; writes tau_delta_i = tau_i - tau_bias_i
+//   MODE_ID:           qdd = in3;           writes tau_i
+//   MODE_RES:          qdd = out;           writes the residual tau_i - ID_i(q, qd, out)
 // Leaves g_i, V_i, f_i in the workspace.
 template <class T, int P>
 __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, const double *grav,
@@ -312,7 +317,8 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
     return;
   }
   const int a = pb.a, b = pb.b;
-  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2;
+  const bool mode_fd = mode == MODE_FD || mode == MODE_FD2 || mode == MODE_RES;
+  const T *qdd_in = mode == MODE_ID ? pb.in3 : (mode == MODE_RES ? pb.out : nullptr);
   SegOp<T> op;
   se3_identity(op.h);
   // joint transforms and this segment's product h = g_a ... g_{b-1}
@@ -365,7 +371,7 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
     xx[2] -= V[1] * qdi;
     xx[4] += V[5] * qdi;
     xx[5] -= V[4] * qdi;
-    if (!mode_fd) xx[0] += pb.in3[i];
+    if (qdd_in) xx[0] += qdd_in[i];
   };
   if (P > 1) {
     for (int k = 0; k < 6; ++k) x[k] = T(0);
@@ -833,33 +839,58 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
   const T *td2 = two ? static_cast<const T *>(A.in4) + A.state_off[pb.p] : nullptr;
   T *out2 = two ? static_cast<T *>(A.out4) + A.state_off[pb.p] : nullptr;
 
-  // bias torque and tau_delta (Algorithm 1: CalcInvDyn, CalcDiffTorques)
-  id_team<T, P>(tm, pb, A.grav, A.mode);
+  // Single precision only: one refinement step. Algorithm 2 finishes every row
+  // with a full Schur complement of A, which in FP32 cancels down to about
+  // cond(A) eps32 relative accuracy; a second pass solves M d = tau - ID(q, qd,
+  // qdd) with the same algorithm (a Newton step on the inverse dynamics, Eq. 2,
+  // whose residual is exact to the inverse dynamics' own rounding) and adds d.
+  constexpr bool refine = std::is_same<T, float>::value && std::is_same<TA, float>::value && !TWO;
+  const int passes = (refine && A.mode == MODE_FD) ? 2 : 1;
+  for (int pass = 0; pass < passes; ++pass) {
+  // bias torque and tau_delta (Algorithm 1: CalcInvDyn, CalcDiffTorques); on the
+  // refinement pass the residual tau - ID(q, qd, qdd) of the first pass's qdd
+  id_team<T, P>(tm, pb, A.grav, pass ? MODE_RES : A.mode);
   tm.sync();
+
+  // CalcA, R = -B tau_delta and CalcAcc run in the accumulation type TA on the
+  // model record of that type. Under mixed precision (float T, double TA) that is
+  // the FP64 record: the blocks of A, B and C are then formed in FP64 from one set
+  // of joint transforms, so M^{-1} = C - B^T A^{-1} B holds to FP64 rounding and
+  // only the FP32 inverse dynamics (tau_delta) and joint transforms perturb the
+  // problem. The products z = J^{-1} (...) live in the T workspace when T = TA and
+  // in the row's G slot (free before the elimination and after it) otherwise.
+  constexpr bool same = std::is_same<T, TA>::value;
+  const TA *recA;
+  if constexpr (same) recA = pb.rec;
+  else recA = static_cast<const TA *>(A.model64) + pb.m0 * REC;
+  auto zst = [&](int i) -> RowP<TA> {
+    if constexpr (same) return RowP<TA>{pb.wt + static_cast<int64_t>(i) * NT + W_Z, 1};
+    else return rowp(wa, n, i) + A_G;
+  };
 
   // CalcA: D_i, U_i; R = -B tau_delta applied as -W^T (I-Gamma) J^{-1} (I-Gamma)^T S tau_delta.
   // From here on lanes take rows round robin (neighbouring rows on neighbouring lanes).
   for (int i = tm.r; i < n; i += P) {
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+    const TA *rec = recA + static_cast<int64_t>(i) * REC;
     const RowP<TA> row = rowp(wa, n, i);
-    SE3<T> g;
+    SE3<TA> g;
     ld_se3(w + W_G, g);
-    calc_dblock<T, TA>(i > 0 ? &g : nullptr, i > 0 ? rec - REC + REC_JI : nullptr,
-                       rec + REC_JI, row + A_D0);
-    T yv[6] = {w[W_TD], T(0), T(0), T(0), T(0), T(0)};
-    T y2[3] = {two ? td2[i] : T(0), T(0), T(0)};
+    calc_dblock<TA, TA>(i > 0 ? &g : nullptr, i > 0 ? rec - REC + REC_JI : nullptr,
+                        rec + REC_JI, row + A_D0);
+    TA yv[6] = {TA(w[W_TD]), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    TA y2[3] = {two ? TA(td2[i]) : TA(0), TA(0), TA(0)};
     if (i + 1 < n) {
-      SE3<T> gn;
+      SE3<TA> gn;
       ld_se3(w + NT + W_G, gn);
-      calc_ublock<T, TA>(gn, rec + REC_JI, row + A_U0);
-      const T tn = w[NT + W_TD];
+      calc_ublock<TA, TA>(gn, rec + REC_JI, row + A_U0);
+      const TA tn = TA(w[NT + W_TD]);
       // Ad_{g_{i+1}^{-1}}^T (e_1 t) = (t R e_1; 0)
       yv[0] -= gn.R[0] * tn;
       yv[1] -= gn.R[3] * tn;
       yv[2] -= gn.R[6] * tn;
       if (two) {
-        const T t2 = td2[i + 1];
+        const TA t2 = TA(td2[i + 1]);
         y2[0] -= gn.R[0] * t2;
         y2[1] -= gn.R[3] * t2;
         y2[2] -= gn.R[6] * t2;
@@ -869,45 +900,50 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
       for (int k = 0; k < 25; ++k) row[A_U0 + k] = TA(0);
     }
     // z = J^{-1} y with y = (y_0, y_1, y_2, 0, 0, 0): columns 0..2 only
-    const T *Ki = rec + REC_JI;
-    T z[6];
+    const TA *Ki = rec + REC_JI;
+    const RowP<TA> zs = zst(i);
 #pragma unroll
     for (int k = 0; k < 6; ++k)
-      z[k] = Ki[s6(k, 0)] * yv[0] + Ki[s6(k, 1)] * yv[1] + Ki[s6(k, 2)] * yv[2];
-    stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
+      zs[k] = Ki[s6(k, 0)] * yv[0] + Ki[s6(k, 1)] * yv[1] + Ki[s6(k, 2)] * yv[2];
     if (two) {
 #pragma unroll
       for (int k = 0; k < 6; ++k)
-        row[A_Z2 + k] = TA(Ki[s6(k, 0)] * y2[0] + Ki[s6(k, 1)] * y2[1] + Ki[s6(k, 2)] * y2[2]);
+        row[A_Z2 + k] = Ki[s6(k, 0)] * y2[0] + Ki[s6(k, 1)] * y2[1] + Ki[s6(k, 2)] * y2[2];
     }
   }
   tm.sync();
   for (int i = tm.r; i < n; i += P) {
     // R_i = -(z_i - Ad_{g_i^{-1}} z_{i-1}), components 1..5
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    T z[6], t[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    ldv<T, 6>(w + W_Z, z);
-    SE3<T> g;
+    TA z[6], t[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    const RowP<TA> zs = zst(i);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) z[k] = zs[k];
+    SE3<TA> g;
     if (i > 0) {
       ld_se3(w + W_G, g);
-      adinv(g, w - NT + W_Z, t);
+      const RowP<TA> zq = zst(i - 1);
+      TA zp[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) zp[k] = zq[k];
+      adinv(g, zp, t);
     }
     const RowP<TA> row = rowp(wa, n, i);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) row[A_R0 + k] = TA(t[k + 1] - z[k + 1]);
+    for (int k = 0; k < 5; ++k) row[A_R0 + k] = t[k + 1] - z[k + 1];
     if (two) {
-      T z2[6], t2[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+      TA z2[6], t2[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
 #pragma unroll
-      for (int k = 0; k < 6; ++k) z2[k] = T(row[A_Z2 + k]);
+      for (int k = 0; k < 6; ++k) z2[k] = row[A_Z2 + k];
       if (i > 0) {
         const RowP<TA> rp = rowp(wa, n, i - 1);
-        T zp[6];
+        TA zp[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) zp[k] = T(rp[A_Z2 + k]);
+        for (int k = 0; k < 6; ++k) zp[k] = rp[A_Z2 + k];
         adinv(g, zp, t2);
       }
 #pragma unroll
-      for (int k = 0; k < 5; ++k) row[A_R20 + k] = TA(t2[k + 1] - z2[k + 1]);
+      for (int k = 0; k < 5; ++k) row[A_R20 + k] = t2[k + 1] - z2[k + 1];
     }
   }
   tm.sync();
@@ -962,66 +998,70 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
   }
 
   // CalcAcc: qdd = C tau_delta + B^T F_c = S^T (I-Gamma) J^{-1} (I-Gamma)^T F,
-  // F_i = S tau_delta_i + W F_c,i (Eq. force-decomposition-global)
+  // F_i = S tau_delta_i + W F_c,i (Eq. force-decomposition-global), in TA
   for (int i = tm.r; i < n; i += P) {
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+    const TA *rec = recA + static_cast<int64_t>(i) * REC;
     const RowP<TA> row = rowp(wa, n, i);
-    T yv[6] = {w[W_TD], T(row[A_FC]), T(row[A_FC + 1]), T(row[A_FC + 2]), T(row[A_FC + 3]),
-               T(row[A_FC + 4])};
+    TA yv[6] = {TA(w[W_TD]), row[A_FC], row[A_FC + 1], row[A_FC + 2], row[A_FC + 3],
+                row[A_FC + 4]};
+    SE3<TA> gn;
     if (i + 1 < n) {
-      SE3<T> gn;
       ld_se3(w + NT + W_G, gn);
       const RowP<TA> rn = rowp(wa, n, i + 1);
-      T Fn[6] = {w[NT + W_TD], T(rn[A_FC]), T(rn[A_FC + 1]), T(rn[A_FC + 2]), T(rn[A_FC + 3]),
-                 T(rn[A_FC + 4])};
-      T t[6];
+      TA Fn[6] = {TA(w[NT + W_TD]), rn[A_FC], rn[A_FC + 1], rn[A_FC + 2], rn[A_FC + 3],
+                  rn[A_FC + 4]};
+      TA t[6];
       adinvT(gn, Fn, t);
       for (int k = 0; k < 6; ++k) yv[k] -= t[k];
     }
-    T z[6];
+    TA z[6];
     sym6_apply(rec + REC_JI, yv, z);
-    stv<T, 6>(pb.wt + static_cast<int64_t>(i) * NT + W_Z, z);
+    const RowP<TA> zs = zst(i);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) zs[k] = z[k];
     if (two) {
-      T y[6] = {td2[i], T(row[A_FC2]), T(row[A_FC2 + 1]), T(row[A_FC2 + 2]), T(row[A_FC2 + 3]),
-                T(row[A_FC2 + 4])};
+      TA y[6] = {TA(td2[i]), row[A_FC2], row[A_FC2 + 1], row[A_FC2 + 2], row[A_FC2 + 3],
+                 row[A_FC2 + 4]};
       if (i + 1 < n) {
-        SE3<T> gn;
-        ld_se3(w + NT + W_G, gn);
         const RowP<TA> rn = rowp(wa, n, i + 1);
-        T Fn[6] = {td2[i + 1], T(rn[A_FC2]), T(rn[A_FC2 + 1]), T(rn[A_FC2 + 2]),
-                   T(rn[A_FC2 + 3]), T(rn[A_FC2 + 4])};
-        T t[6];
+        TA Fn[6] = {TA(td2[i + 1]), rn[A_FC2], rn[A_FC2 + 1], rn[A_FC2 + 2], rn[A_FC2 + 3],
+                    rn[A_FC2 + 4]};
+        TA t[6];
         adinvT(gn, Fn, t);
         for (int k = 0; k < 6; ++k) y[k] -= t[k];
       }
       sym6_apply(rec + REC_JI, y, z);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) row[A_Z2 + k] = TA(z[k]);
+      for (int k = 0; k < 6; ++k) row[A_Z2 + k] = z[k];
     }
   }
   tm.sync();
   for (int i = tm.r; i < n; i += P) {
     const T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    T qdd = w[W_Z];
+    const RowP<TA> zs = zst(i);
+    TA qdd = zs[0];
     if (i > 0) {
       // (Ad_{g_i^{-1}} z_{i-1})_0 = (R^T omega)_0
-      const T *zp = w - NT + W_Z;
-      qdd -= w[W_G + 0] * zp[0] + w[W_G + 3] * zp[1] + w[W_G + 6] * zp[2];
+      const RowP<TA> zp = zst(i - 1);
+      qdd -= TA(w[W_G + 0]) * zp[0] + TA(w[W_G + 3]) * zp[1] + TA(w[W_G + 6]) * zp[2];
     }
-    pb.out[i] = qdd;
-    if (!finite_t(qdd)) bad = true;
+    const T q2 = pass ? T(TA(pb.out[i]) + qdd) : T(qdd);
+    pb.out[i] = q2;
+    if (!finite_t(q2)) bad = true;
     if (two) {
       const RowP<TA> row = rowp(wa, n, i);
-      T x = T(row[A_Z2]);
+      TA x = row[A_Z2];
       if (i > 0) {
         const RowP<TA> rp = rowp(wa, n, i - 1);
-        x -= w[W_G + 0] * T(rp[A_Z2]) + w[W_G + 3] * T(rp[A_Z2 + 1]) + w[W_G + 6] * T(rp[A_Z2 + 2]);
+        x -= TA(w[W_G + 0]) * rp[A_Z2] + TA(w[W_G + 3]) * rp[A_Z2 + 1] + TA(w[W_G + 6]) * rp[A_Z2 + 2];
       }
-      out2[i] = x;
-      if (!finite_t(x)) bad = true;
+      out2[i] = T(x);
+      if (!finite_t(T(x))) bad = true;
     }
   }
+  if (passes > 1) tm.sync();  // the refinement pass reads this pass's qdd
+  }  // passes
   const bool any_bad = tm.any(bad);
   if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
 }

@@ -86,11 +86,14 @@ constexpr int MODE_ID = 1;      // tau = ID(q, qd, qdd)
 constexpr int MODE_LINEAR = 2;  // tau_delta = in3 (solve M x = in3: joint transforms only)
 constexpr int MODE_FD2 = 3;     // MODE_FD into out, and M^{-1} in4 into out4 with the same
                                 // factorisation (the adjoint's linear solve beside FD)
+constexpr int MODE_RES = 4;     // inverse dynamics only (the FP32 CFA refinement pass):
+                                // tau_delta = in3 - ID(q, qd, out), the residual of out
 
 struct KArgs {
   const void *model;         // [L][REC] of T
+  const void *model64;       // [L][REC] of double (the FP64 copy; mixed-precision CFA blocks)
   const int64_t *model_off;  // [K + 1]
-  const int32_t *prob_chain; // [N]
+  const int32_t *prob_chain; // [N] chain of each problem, or null: problem p is chain p
   const int64_t *state_off;  // [N + 1]
   const int64_t *sq_off;     // [N + 1] prefix sums of n_p^2
   const int32_t *order;      // [N] processing order (longest first)

@@ -329,6 +329,7 @@ void fill_tables(fd_server_s *S, const std::vector<Req *> &list, int base) {
 fdk::KArgs base_args(fd_server_s *S) {
   fdk::KArgs a{};
   a.model = S->A.model;
+  a.model64 = S->A.model;
   a.model_off = S->d_moff;
   a.prob_chain = S->d_prob;
   a.state_off = S->d_soff;

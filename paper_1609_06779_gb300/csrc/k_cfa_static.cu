@@ -5,7 +5,6 @@
 
 #include <cstdio>
 #include <mutex>
-#include <vector>
 
 #include "fd_internal.h"
 #include "fd_launch.h"
@@ -13,13 +12,12 @@
 
 namespace {
 
-// 32 MiB per device: a 256 KiB problem -> chain map (identity) followed by the
-// CFA workspace. At FP64 the workspace needs 32 x 8 + 196 x 8 = 1 824 bytes per
-// link (about 18 000 links); mixed 32 x 4 + 196 x 8 = 1 696 (about 19 000);
-// FP32 32 x 4 + 196 x 4 = 912 (about 36 000).
+// 32 MiB per device, all of it CFA workspace. At FP64 the workspace needs
+// 32 x 8 + 196 x 8 = 1 824 bytes per link (about 18 000 links); mixed
+// 32 x 4 + 196 x 8 = 1 696 (about 19 000); FP32 32 x 4 + 196 x 4 = 912 (about
+// 36 000). Problem p is chain p, so no problem map is needed (the kernels read a
+// null map as the identity).
 constexpr size_t kScratchBytes = size_t(32) << 20;
-constexpr int kMaxProblems = 1 << 16;
-constexpr size_t kMapBytes = size_t(kMaxProblems) * sizeof(int32_t);
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -30,7 +28,8 @@ unsigned char *g_base[kMaxDevices] = {};
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Once per device, with that device current: the device address of g_scratch
-// (the host-side name is only a stand-in) and the identity problem map.
+// (in host code its name is only a stand-in for the device array). Nothing is
+// copied to the device, so there is nothing to wait for.
 fd_status setup(int dev, unsigned char **base) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_base[dev]) {
@@ -40,17 +39,9 @@ fd_status setup(int dev, unsigned char **base) {
   void *p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     char msg[256];
     snprintf(msg, sizeof msg, "fd_solve_cfa_static: cudaGetSymbolAddress: %s",
-             cudaGetErrorString(e));
-    return fdk_fail(FD_ERR_CUDA, msg);
-  }
-  std::vector<int32_t> ident(kMaxProblems);
-  for (int k = 0; k < kMaxProblems; ++k) ident[k] = k;
-  e = cudaMemcpy(p, ident.data(), kMapBytes, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    char msg[256];
-    snprintf(msg, sizeof msg, "fd_solve_cfa_static: copying the problem map: %s",
              cudaGetErrorString(e));
     return fdk_fail(FD_ERR_CUDA, msg);
   }
@@ -67,10 +58,9 @@ extern "C" fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const 
   if (!chain) return fdk_fail(FD_ERR_INVALID_ARG, "fd_solve_cfa_static: NULL chain");
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fdk_fail(FD_ERR_INVALID_ARG, "fd_solve_cfa_static: bad precision");
-  if (!(team == 0 || team == 1 || team == 2 || team == 4 || team == 8 || team == 16 ||
-        team == 32))
+  if (team < 0 || (team > 0 && !fdk_valid_team(team)))
     return fdk_fail(FD_ERR_INVALID_ARG,
-                    "fd_solve_cfa_static: team is not 0 or a power of two <= 32");
+                    "fd_solve_cfa_static: team is not 0 or a power of two <= 256");
   if (chain->n_chains == 0 || chain->n_links == 0) return FD_OK;
   if (!q || !qdot || !tau || !qddot)
     return fdk_fail(FD_ERR_INVALID_ARG, "fd_solve_cfa_static: NULL state array");
@@ -78,23 +68,23 @@ extern "C" fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const 
   const size_t L = static_cast<size_t>(chain->n_links);
   const size_t t_bytes = align256(L * fdk::NT * ts);
   const size_t need = t_bytes + align256(L * fdk::NA_CFA * as);
-  if (chain->n_chains > kMaxProblems || need > kScratchBytes - kMapBytes) {
+  if (need > kScratchBytes) {
     char msg[320];
     snprintf(msg, sizeof msg,
              "fd_solve_cfa_static: %d chains / %lld links need %zu bytes of scratch; the "
-             "static scratch holds %zu bytes and at most %d chains (use fd_solve_batch "
-             "with a workspace for larger batches)",
-             chain->n_chains, static_cast<long long>(chain->n_links), need,
-             kScratchBytes - kMapBytes, kMaxProblems);
+             "static scratch holds %zu bytes (use fd_solve_batch with a workspace for "
+             "larger sets)",
+             chain->n_chains, static_cast<long long>(chain->n_links), need, kScratchBytes);
     return fdk_fail(FD_ERR_INVALID_ARG, msg);
   }
+  if (chain->device >= kMaxDevices)
+    return fdk_fail(FD_ERR_INVALID_ARG, "fd_solve_cfa_static: device index too large");
   int prev = 0;
   cudaGetDevice(&prev);
   cudaError_t e = cudaSetDevice(chain->device);
-  if (e != cudaSuccess) return fdk_fail(FD_ERR_CUDA, "fd_solve_cfa_static: cudaSetDevice");
-  if (chain->device >= kMaxDevices) {
-    cudaSetDevice(prev);
-    return fdk_fail(FD_ERR_INVALID_ARG, "fd_solve_cfa_static: device index too large");
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fdk_fail(FD_ERR_CUDA, "fd_solve_cfa_static: cudaSetDevice");
   }
   unsigned char *base = nullptr;
   fd_status st = setup(chain->device, &base);
@@ -102,19 +92,13 @@ extern "C" fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const 
     cudaSetDevice(prev);
     return st;
   }
-  int t = team;
-  if (t == 0) {  // enough lanes to fill the GPU, no more lanes than links
-    long long per = (152LL * 512) / chain->n_chains;
-    t = 1;
-    while (2LL * t <= per && t < 32) t *= 2;
-    int cap = 1;
-    while (cap < chain->max_links && cap < 32) cap *= 2;
-    if (t > cap) t = cap;
-  }
+  // team 0: the same default as fd_solve_batch with an untuned batch plan
+  const int t = team > 0 ? team : fdk_default_team(FD_CFA, chain->n_chains, chain->max_links);
   fdk::KArgs a{};
   a.model = prec == FD_FP64 ? chain->d_model64 : chain->d_model32;
+  a.model64 = chain->d_model64;
   a.model_off = chain->d_off;
-  a.prob_chain = reinterpret_cast<const int32_t *>(base);
+  a.prob_chain = nullptr;  // problem p is chain p
   a.state_off = chain->d_off;
   a.sq_off = chain->d_off;
   a.order = nullptr;
@@ -124,14 +108,15 @@ extern "C" fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const 
   a.qd = qdot;
   a.in3 = tau;
   a.out = qddot;
-  a.ws_t = base + kMapBytes;
-  a.ws_a = base + kMapBytes + t_bytes;
+  a.ws_t = base;
+  a.ws_a = base + t_bytes;
   a.status = status;
   for (int k = 0; k < 3; ++k) a.grav[k] = chain->grav[k];
   const int prec_k = prec == FD_FP64 ? 0 : (prec == FD_FP32 ? 1 : 2);
   e = fdk::launch_cfa(a, prec_k, t, static_cast<cudaStream_t>(stream));
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     char msg[256];
     snprintf(msg, sizeof msg, "fd_solve_cfa_static: launch: %s", cudaGetErrorString(e));
     return fdk_fail(FD_ERR_CUDA, msg);

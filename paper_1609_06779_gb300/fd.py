@@ -242,13 +242,22 @@ def solve_cfa_static(chains: ChainSet, q, qd, tau, prec="fp64", team=0, out=None
     avoid torch's allocation as well."""
     torch = _torch()
     dt = _state_dtype(prec)
-    n_links = chains.info()[1]
-    for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau")):
+    n_chains, n_links = chains.info()[0], chains.info()[1]
+
+    def check(t, nm):
         if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt \
                 or not t.is_contiguous() or t.numel() != n_links:
             raise FDError(1, f"{nm}: need a contiguous CUDA {dt} tensor of {n_links} elements")
+    for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau")):
+        check(t, nm)
     if out is None:
         out = torch.empty_like(q)
+    check(out, "qddot")
+    if status is not None and (not isinstance(status, torch.Tensor) or not status.is_cuda
+                               or status.dtype != torch.int32 or not status.is_contiguous()
+                               or status.numel() < n_chains):
+        raise FDError(1, f"status must be a contiguous CUDA int32 tensor of at least "
+                         f"{n_chains} elements")
     s = stream if stream is not None else torch.cuda.current_stream(q.device)
     _check(load().fd_solve_cfa_static(chains.handle, q.data_ptr(), qd.data_ptr(), tau.data_ptr(),
                                       out.data_ptr(), PRECS[prec], int(team),
