@@ -136,7 +136,11 @@ fd_status fd_batch_info(fd_batch_t batch, int32_t *n_problems, int64_t *n_state_
 /*
  * Threads that cooperate on one problem ("team"): 0 lets the library choose
  * (the autotuned size if fd_autotune ran for this batch, algorithm and
- * precision, else a size that fills the GPU); otherwise a power of two from 1
+ * precision, else a size that fills the GPU; for a batch whose chains fall
+ * into several length classes -- ceil(log2 n) differs -- one launch whose grid
+ * is split by class, each class with its own team of 1 .. 128 lanes: its
+ * autotuned one, else the size that fills the GPU with that class alone;
+ * see fd_batch_classes); otherwise a power of two from 1
  * (one thread per chain: serial recursions) through 32 (one warp per chain:
  * warp-shuffle scans and OEE levels across lanes) to 256 (one block per chain:
  * scans across warps through shared memory). FD_ABIA keeps its articulated-
@@ -186,17 +190,46 @@ fd_status fd_inverse_dynamics(fd_batch_t batch, const void *q, const void *qdot,
 /*
  * fd_autotune -- pick the team size for (batch, algo, prec) by timing.
  *
- * The paper leaves the parallel schedule to the implementation; this times
- * every team size (1 .. 256, at most the longest chain rounded up to a power of
- * two; ABIA: 1) whose workspace fits in workspace_bytes, one warm-up and two
- * timed solves each with CUDA events on `stream`, and records the fastest in the
- * batch plan: later calls with team 0 use it. Synchronises the stream. Inputs as
- * fd_solve_batch (qddot is overwritten). *best_team (may be NULL) receives the
- * choice.
+ * The paper leaves the parallel schedule to the implementation. For a batch of
+ * one length class this times every team size (1 .. 256, at most the longest
+ * chain rounded up to a power of two; ABIA: 1, 8, 16, 32) whose workspace fits
+ * in workspace_bytes, one warm-up and two timed solves each with CUDA events on
+ * `stream`, and records the fastest in the batch plan. For a batch of several
+ * length classes it does the same per class (teams up to 128), each class
+ * launched alone, and records one team per class; *best_team (may be NULL)
+ * then receives 0. Later calls with team 0 use the recorded teams. Choices are
+ * also kept in a process-wide cache keyed by GPU, algorithm, precision, length
+ * class and ceil(log2) of the problem count; a cached entry is used without
+ * timing (fd_autotune_cache_load / _save persist it). Synchronises the stream.
+ * Inputs as fd_solve_batch (qddot is overwritten).
  */
 fd_status fd_autotune(fd_batch_t batch, fd_algo algo, fd_prec prec, const void *q,
                       const void *qdot, const void *tau, void *qddot, void *workspace,
                       size_t workspace_bytes, void *stream, int32_t *best_team);
+
+/*
+ * fd_batch_classes -- the length classes of a batch (not in the paper: the
+ * schedule of a team-0 solve). Problems whose chains share ceil(log2 n) form a
+ * class (n <= 1: one class); *n_classes receives their number, and for the
+ * first min(max, *n_classes) classes, longest first, the shortest and longest
+ * chain, the problem count and the team a team-0 solve of (algo, prec) gives
+ * the class (algo -1: fd_inverse_dynamics). Output arrays are host memory and
+ * may be NULL.
+ */
+fd_status fd_batch_classes(fd_batch_t batch, int32_t algo, fd_prec prec, int32_t max,
+                           int32_t *n_classes, int32_t *min_len, int32_t *max_len,
+                           int32_t *count, int32_t *team);
+
+/*
+ * The autotune cache (see fd_autotune): load merges the JSON file at `path`
+ * into the process-wide cache (a missing file loads nothing; a malformed one is
+ * FD_ERR_INVALID_ARG) and sets *n_loaded (may be NULL); save writes the whole
+ * cache to `path` (through a temporary file renamed into place); clear empties
+ * it. Host only; thread safe.
+ */
+fd_status fd_autotune_cache_load(const char *path, int32_t *n_loaded);
+fd_status fd_autotune_cache_save(const char *path);
+fd_status fd_autotune_cache_clear(void);
 
 /*
  * fd_solve_adjoint -- reverse-mode derivatives of qdd = FD(q, qdot, tau).
@@ -238,10 +271,11 @@ fd_status fd_solve_adjoint(fd_batch_t batch, const void *q, const void *qdot, co
  *
  * Problem p is chain p of `chain` (no batch plan); q, qdot, tau (inputs) and
  * qddot (output) are device arrays of the chain set's total link count, packed
- * in chain order, double for FD_FP64 and float for FD_FP32 / FD_MIXED. team: 0
- * or a power of two from 1 to 256, as for fd_solve_batch (team 0 takes the
- * default fd_solve_batch uses for a batch plan that was not autotuned); the
- * result equals fd_solve_batch's at the same team bit for bit. status as for
+ * in chain order, double for FD_FP64 and float for FD_FP32 / FD_MIXED. team: a
+ * power of two from 1 to 256, as for fd_solve_batch, or 0: one team for all
+ * chains, the largest power of two not above 152 x 2048 / n_chains, capped at
+ * the longest chain rounded up to a power of two (no split by length class);
+ * the result equals fd_solve_batch's at the same team bit for bit. status as for
  * fd_solve_batch. Limit: the CFA workspace of all links must fit in 32 MiB
  * (FD_FP64: 1 824 bytes per link, about 18 000 links; FD_MIXED about 19 000;
  * FD_FP32 about 36 000); larger sets return FD_ERR_INVALID_ARG with the sizes

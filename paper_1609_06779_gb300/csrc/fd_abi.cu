@@ -8,10 +8,14 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/fd_gb300.h"
@@ -400,11 +404,27 @@ fd_status fd_batch_create(fd_chain_t c, int32_t n_problems, const int32_t *chain
   std::stable_sort(order.begin(), order.end(),
                    [&](int32_t x, int32_t y) { return len[x] > len[y]; });
 
+  // length classes over the processing order (ceil(log2 n) decreases along it)
+  std::vector<fd_batch_s::LenClass> classes;
+  for (int32_t t = 0; t < n_problems; ++t) {
+    const int32_t n = len[order[t]];
+    int key = 0;
+    while ((1 << key) < n) ++key;
+    if (classes.empty() || classes.back().key != key)
+      classes.push_back({key, t, 0, n, n});
+    auto &cl = classes.back();
+    ++cl.count;
+    cl.min_len = std::min(cl.min_len, n);
+    cl.max_len = std::max(cl.max_len, n);
+  }
+
   int prev = 0;
   cudaGetDevice(&prev);
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto *b = new fd_batch_s();
+  b->classes = classes;
+  b->ctuned.assign(classes.size() * 12, 0);
   b->chain = c;
   b->device = c->device;
   b->n_problems = n_problems;
@@ -490,6 +510,55 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int /*team: no l
 
 bool valid_team(int t) { return fdk_valid_team(t); }
 
+// team 0 on a batch of several length classes: one launch split by class
+bool use_classes(const fd_batch_s *b, int32_t team) { return team == 0 && b->classes.size() > 1; }
+
+int class_team(const fd_batch_s *b, size_t c, int32_t algo, fd_prec prec) {
+  if (algo >= 0) {
+    const int tuned = b->ctuned[c * 12 + static_cast<size_t>(algo) * 3 + prec];
+    if (tuned > 0) return tuned;
+  }
+  const auto &cl = b->classes[c];
+  return std::min(fdk_default_team(algo, cl.count, cl.max_len), 128);
+}
+
+// The adjoint's reverse sweep: component lanes (team 8..32) up to 64 links, else
+// the forward solve's team (ABIA's serial team 1 would scan nothing: CFA's).
+int sweep_team(const fd_batch_s *b, size_t c, int32_t algo, fd_prec prec) {
+  const int t = class_team(b, c, algo, prec);
+  if (b->classes[c].max_len <= 64) return std::min(std::max(t, 8), 32);
+  return algo == FD_ABIA ? class_team(b, c, FD_CFA, prec) : t;
+}
+
+// The grid split of a class launch: every class (only < 0) or class `only` alone.
+fdk::ClassTable class_table(const fd_batch_s *b, const std::vector<int> &teams, int only = -1) {
+  fdk::ClassTable ct{};
+  int nb = 0, k = 0;
+  for (size_t c = 0; c < b->classes.size(); ++c) {
+    if (only >= 0 && static_cast<int>(c) != only) continue;
+    const auto &cl = b->classes[c];
+    ct.blk[k] = nb;
+    ct.first[k] = cl.first;
+    ct.team[k] = teams[c];
+    nb += static_cast<int>((static_cast<int64_t>(cl.count) * teams[c] + fdk::BLOCK - 1) /
+                           fdk::BLOCK);
+    ++k;
+    ct.first[k] = cl.first + cl.count;
+  }
+  ct.n = k;
+  ct.blk[k] = nb;
+  return ct;
+}
+
+cudaError_t launch_classes(const fdk::KArgs &a, int32_t algo, int prec_k,
+                           const fdk::ClassTable &ct, cudaStream_t s) {
+  if (algo == -1) return fdk::launch_id_multi(a, prec_k, ct, s);
+  if (algo == FD_CFA) return fdk::launch_cfa_multi(a, prec_k, ct, s);
+  if (algo == FD_CFA_CR) return fdk::launch_cfa_cr_multi(a, prec_k, ct, s);
+  if (algo == FD_JSIIA) return fdk::launch_jsiia_multi(a, prec_k, ct, s);
+  return fdk::launch_abia_multi(a, prec_k, ct, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -501,9 +570,11 @@ size_t fd_workspace_size(fd_batch_t b, int32_t algo, fd_prec prec, int32_t team)
   return w.t_bytes + w.a_bytes;
 }
 
+// only_class >= 0: launch that length class alone with `team` (the autotuner)
 static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, const void *in3,
                                void *out, int32_t algo, fd_prec prec, int32_t team, void *ws,
-                               size_t ws_bytes, int32_t *status, void *stream, const char *who) {
+                               size_t ws_bytes, int32_t *status, void *stream, const char *who,
+                               int only_class = -1) {
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
@@ -547,7 +618,14 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   cudaError_t e = cudaSetDevice(b->chain->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto s = static_cast<cudaStream_t>(stream);
-  if (algo == -1) e = fdk::launch_id(a, prec_k, t, s);
+  if (only_class >= 0 || use_classes(b, team)) {
+    std::vector<int> teams(b->classes.size());
+    for (size_t c = 0; c < teams.size(); ++c)
+      teams[c] = (only_class >= 0 && static_cast<int>(c) == only_class && team > 0)
+                     ? team
+                     : class_team(b, c, algo, prec);
+    e = launch_classes(a, algo, prec_k, class_table(b, teams, only_class), s);
+  } else if (algo == -1) e = fdk::launch_id(a, prec_k, t, s);
   else if (algo == FD_CFA) e = fdk::launch_cfa(a, prec_k, t, s);
   else if (algo == FD_CFA_CR) e = fdk::launch_cfa_cr(a, prec_k, t, s);
   else if (algo == FD_JSIIA) e = fdk::launch_jsiia(a, prec_k, t, s);
@@ -643,7 +721,14 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
   cudaError_t e = cudaSetDevice(b->chain->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto s = static_cast<cudaStream_t>(stream);
+  const bool split = use_classes(b, team);
+  std::vector<int> fd_teams(b->classes.size()), sw_teams(b->classes.size());
+  for (size_t c = 0; split && c < fd_teams.size(); ++c) {
+    fd_teams[c] = class_team(b, c, algo, prec);
+    sw_teams[c] = sweep_team(b, c, algo, prec);
+  }
   auto run_fd = [&](fdk::KArgs &k) {
+    if (split) return launch_classes(k, algo, prec_k, class_table(b, fd_teams), s);
     if (algo == FD_CFA) return fdk::launch_cfa(k, prec_k, t, s);
     if (algo == FD_CFA_CR) return fdk::launch_cfa_cr(k, prec_k, t, s);
     if (algo == FD_JSIIA) return fdk::launch_jsiia(k, prec_k, t, s);
@@ -682,7 +767,9 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
     const int tr = b->max_links <= 64 ? std::max(t, 8) > 32 ? 32 : std::max(t, 8)
                    : (algo == FD_ABIA ? resolve_team(b, FD_CFA, prec, 0) : t);
     r.team = tr;
-    e = fdk::launch_adjoint_rnea(r, prec == FD_FP64 ? 0 : 1, tr, s);
+    e = split ? fdk::launch_adjoint_rnea_multi(r, prec == FD_FP64 ? 0 : 1,
+                                               class_table(b, sw_teams), s)
+              : fdk::launch_adjoint_rnea(r, prec == FD_FP64 ? 0 : 1, tr, s);
   }
   cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, who);
@@ -690,6 +777,103 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
 }
 
 }  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------ autotune cache
+//
+// Process-wide: the fastest team per (GPU, algorithm, precision, length class,
+// problem-count class), filled by fd_autotune and persisted as JSON by
+// fd_autotune_cache_save / _load, so a later process skips the timing.
+struct TuneKey {
+  std::string gpu;
+  int algo, prec, len_class, count_class;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(gpu, algo, prec, len_class, count_class) <
+           std::tie(o.gpu, o.algo, o.prec, o.len_class, o.count_class);
+  }
+};
+struct TuneVal {
+  int team;
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+int ceil_log2(int64_t v) {
+  int k = 0;
+  while ((int64_t(1) << k) < v) ++k;
+  return k;
+}
+
+std::string gpu_name(int dev) {
+  cudaDeviceProp pr{};
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  char buf[320];
+  snprintf(buf, sizeof buf, "%s (%d SMs)", pr.name, pr.multiProcessorCount);
+  return buf;
+}
+
+// Times `cand` teams on one length class (cls >= 0) or the whole batch (cls < 0):
+// one warm-up and two timed solves each; returns the fastest (0 if none fits).
+fd_status time_teams(fd_batch_t b, fd_algo algo, fd_prec prec, const void *q, const void *qdot,
+                     const void *tau, void *qddot, void *workspace, size_t workspace_bytes,
+                     cudaStream_t s, const std::vector<int> &cand, int cls, int *best,
+                     float *best_ms, const char *who) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  *best = 0;
+  *best_ms = 0.f;
+  fd_status st = FD_OK;
+  for (int t : cand) {
+    const WsPlan w = ws_plan(b, algo, prec, t);
+    if (w.t_bytes + w.a_bytes > workspace_bytes) continue;
+    st = launch_common(b, q, qdot, tau, qddot, algo, prec, t, workspace, workspace_bytes,
+                       nullptr, s, who, cls);
+    if (st != FD_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && st == FD_OK; ++r)
+      st = launch_common(b, q, qdot, tau, qddot, algo, prec, t, workspace, workspace_bytes,
+                         nullptr, s, who, cls);
+    cudaEventRecord(e1, s);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, who);
+      break;
+    }
+    if (st != FD_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 2;
+    if (*best == 0 || ms < *best_ms) {
+      *best = t;
+      *best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+std::vector<int> team_candidates(fd_algo algo, int max_len, int cap_team) {
+  std::vector<int> cand;
+  if (algo == FD_ABIA) {
+    // ABIA's lane teams spread each step's 6x6 update over 6 or 12 lanes, which
+    // pays even for chains shorter than the team
+    for (int t : {1, 8, 16, 32}) cand.push_back(t);
+  } else {
+    int cap = 1;
+    while (cap < max_len && cap < cap_team) cap *= 2;
+    for (int t = 1; t <= cap; t *= 2) cand.push_back(t);
+  }
+  return cand;
+}
+
+}  // namespace
 
 extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const void *q,
                                  const void *qdot, const void *tau, void *qddot,
@@ -701,16 +885,6 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision", who);
-  int cap = 1;
-  while (cap < b->max_links && cap < 256) cap *= 2;
-  std::vector<int> cand;
-  if (algo == FD_ABIA) {
-    // ABIA's lane teams spread each step's 6x6 update over 6 or 12 lanes, which
-    // pays even for chains shorter than the team
-    for (int t : {1, 8, 16, 32}) cand.push_back(t);
-  } else {
-    for (int t = 1; t <= cap; t *= 2) cand.push_back(t);
-  }
   if (b->n_problems == 0 || b->n_state_links == 0) {
     if (best_team) *best_team = 1;
     return FD_OK;
@@ -719,42 +893,167 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
   cudaGetDevice(&prev);
   cudaError_t e = cudaSetDevice(b->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  const std::string gpu = gpu_name(b->device);
   auto s = static_cast<cudaStream_t>(stream);
-  int best = 0;
-  float best_ms = 0.f;
   fd_status st = FD_OK;
-  for (int t : cand) {
-    const WsPlan w = ws_plan(b, algo, prec, t);
-    if (w.t_bytes + w.a_bytes > workspace_bytes) continue;
-    st = launch_common(b, q, qdot, tau, qddot, algo, prec, t, workspace, workspace_bytes,
-                       nullptr, stream, who);
-    if (st != FD_OK) break;
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < 2 && st == FD_OK; ++r)
-      st = launch_common(b, q, qdot, tau, qddot, algo, prec, t, workspace, workspace_bytes,
-                         nullptr, stream, who);
-    cudaEventRecord(e1, s);
-    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-      st = cuda_fail(e, who);
-      break;
+  const bool split = b->classes.size() > 1;
+  // one length class (or the whole batch): its team from the cache, else timed
+  auto tune = [&](int cls, int max_len, int64_t count, int len_class, int cap_team,
+                  int *out) -> fd_status {
+    const TuneKey key{gpu, static_cast<int>(algo), static_cast<int>(prec), len_class,
+                      ceil_log2(count)};
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        *out = it->second.team;
+        return FD_OK;
+      }
     }
-    if (st != FD_OK) break;
+    int best = 0;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best == 0 || ms < best_ms) {
-      best = t;
-      best_ms = ms;
+    const fd_status r = time_teams(b, algo, prec, q, qdot, tau, qddot, workspace, workspace_bytes,
+                                   s, team_candidates(algo, max_len, cap_team), cls, &best, &ms,
+                                   who);
+    if (r != FD_OK) return r;
+    if (best == 0) return fail(FD_ERR_INVALID_ARG, "%s: workspace too small for any team", who);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = TuneVal{best, ms};
+    *out = best;
+    return FD_OK;
+  };
+  if (split) {
+    // per length class, each timed alone in the class launch (teams up to 128)
+    for (size_t c = 0; c < b->classes.size() && st == FD_OK; ++c) {
+      const auto &cl = b->classes[c];
+      int best = 0;
+      st = tune(static_cast<int>(c), cl.max_len, cl.count, cl.key, 128, &best);
+      if (st == FD_OK) b->ctuned[c * 12 + static_cast<size_t>(algo) * 3 + prec] = best;
+    }
+    if (st == FD_OK && best_team) *best_team = 0;
+  } else {
+    int best = 0;
+    st = tune(-1, b->max_links, b->n_problems, ceil_log2(std::max(b->max_links, 1)), 256, &best);
+    if (st == FD_OK) {
+      b->tuned[algo][prec] = best;
+      if (best_team) *best_team = best;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaSetDevice(prev);
-  if (st != FD_OK) return st;
-  if (best == 0) return fail(FD_ERR_INVALID_ARG, "%s: workspace too small for any team", who);
-  b->tuned[algo][prec] = best;
-  if (best_team) *best_team = best;
+  return st;
+}
+
+extern "C" fd_status fd_batch_classes(fd_batch_t b, int32_t algo, fd_prec prec, int32_t max,
+                                      int32_t *n_classes, int32_t *min_len, int32_t *max_len,
+                                      int32_t *count, int32_t *team) {
+  if (!b || !n_classes) return fail(FD_ERR_INVALID_ARG, "fd_batch_classes: NULL argument");
+  if (algo < -1 || algo > FD_CFA_CR || prec < FD_FP64 || prec > FD_MIXED)
+    return fail(FD_ERR_INVALID_ARG, "fd_batch_classes: bad algorithm or precision");
+  *n_classes = static_cast<int32_t>(b->classes.size());
+  const bool split = b->classes.size() > 1;
+  for (size_t c = 0; c < b->classes.size() && static_cast<int32_t>(c) < max; ++c) {
+    const auto &cl = b->classes[c];
+    if (min_len) min_len[c] = cl.min_len;
+    if (max_len) max_len[c] = cl.max_len;
+    if (count) count[c] = cl.count;
+    if (team) team[c] = split ? class_team(b, c, algo, prec) : resolve_team(b, algo, prec, 0);
+  }
+  return FD_OK;
+}
+
+extern "C" fd_status fd_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  return FD_OK;
+}
+
+extern "C" fd_status fd_autotune_cache_save(const char *path) {
+  if (!path) return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_save: NULL path");
+  std::string js = "{\"format\": \"fd_gb300 autotune cache 1\", \"entries\": [";
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    bool first = true;
+    for (const auto &kv : g_tune) {
+      std::string g;
+      for (char ch : kv.first.gpu)
+        if (ch != '"' && ch != '\\') g += ch;
+      char buf[512];
+      snprintf(buf, sizeof buf,
+               "%s\n  {\"gpu\": \"%s\", \"algo\": %d, \"prec\": %d, \"len_class\": %d, "
+               "\"count_class\": %d, \"team\": %d, \"ms\": %.6g}",
+               first ? "" : ",", g.c_str(), kv.first.algo, kv.first.prec, kv.first.len_class,
+               kv.first.count_class, kv.second.team, static_cast<double>(kv.second.ms));
+      js += buf;
+      first = false;
+    }
+  }
+  js += "\n]}\n";
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = std::fopen(tmp.c_str(), "w");
+  if (!f) return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_save: cannot write %s", tmp.c_str());
+  const bool ok = std::fwrite(js.data(), 1, js.size(), f) == js.size();
+  std::fclose(f);
+  if (!ok || std::rename(tmp.c_str(), path) != 0)
+    return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_save: cannot write %s", path);
+  return FD_OK;
+}
+
+extern "C" fd_status fd_autotune_cache_load(const char *path, int32_t *n_loaded) {
+  if (n_loaded) *n_loaded = 0;
+  if (!path) return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_load: NULL path");
+  FILE *f = std::fopen(path, "r");
+  if (!f) return FD_OK;  // no cache yet
+  std::string js;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) js.append(buf, got);
+  std::fclose(f);
+  if (js.find("fd_gb300 autotune cache 1") == std::string::npos)
+    return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_load: %s is not an autotune cache", path);
+  // entries are flat objects of string and integer fields
+  auto field = [](const std::string &obj, const char *name, std::string *sval, long *ival) {
+    const std::string pat = std::string("\"") + name + "\"";
+    size_t p = obj.find(pat);
+    if (p == std::string::npos) return false;
+    p = obj.find(':', p + pat.size());
+    if (p == std::string::npos) return false;
+    ++p;
+    while (p < obj.size() && obj[p] == ' ') ++p;
+    if (sval) {
+      if (p >= obj.size() || obj[p] != '"') return false;
+      const size_t q = obj.find('"', p + 1);
+      if (q == std::string::npos) return false;
+      *sval = obj.substr(p + 1, q - p - 1);
+      return true;
+    }
+    char *end = nullptr;
+    *ival = std::strtol(obj.c_str() + p, &end, 10);
+    return end != obj.c_str() + p;
+  };
+  size_t pos = js.find('[');
+  int n = 0;
+  std::map<TuneKey, TuneVal> add;
+  while (pos != std::string::npos) {
+    const size_t a = js.find('{', pos);
+    if (a == std::string::npos) break;
+    const size_t z = js.find('}', a);
+    if (z == std::string::npos)
+      return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_load: %s is truncated", path);
+    const std::string obj = js.substr(a, z - a + 1);
+    std::string gpu;
+    long algo = 0, prec = 0, lc = 0, cc = 0, team = 0;
+    if (!field(obj, "gpu", &gpu, nullptr) || !field(obj, "algo", nullptr, &algo) ||
+        !field(obj, "prec", nullptr, &prec) || !field(obj, "len_class", nullptr, &lc) ||
+        !field(obj, "count_class", nullptr, &cc) || !field(obj, "team", nullptr, &team) ||
+        algo < 0 || algo > FD_CFA_CR || prec < 0 || prec > FD_MIXED || !fdk_valid_team(team) ||
+        (algo == FD_ABIA && !fdk::abia_team_ok(static_cast<int>(team))))
+      return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_load: bad entry in %s", path);
+    add[TuneKey{gpu, int(algo), int(prec), int(lc), int(cc)}] = TuneVal{int(team), 0.f};
+    ++n;
+    pos = z + 1;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto &kv : add) g_tune[kv.first] = kv.second;
+  if (n_loaded) *n_loaded = n;
   return FD_OK;
 }

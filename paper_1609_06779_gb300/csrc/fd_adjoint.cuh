@@ -185,10 +185,10 @@ __device__ __forceinline__ void adjoint_lanes(const Team<P> &tm, const Prob<T> &
 }
 
 template <class T, int P>
-__global__ void __launch_bounds__(block_for<P>()) adjoint_rnea_kernel(KArgs A) {
+__device__ __forceinline__ void adjoint_body(const KArgs &A, const Range &rg) {
   Team<P> tm;
   Prob<T> pb;
-  if (!load_problem<T, P>(A, tm, pb, NT_ADJ)) return;
+  if (!load_problem<T, P>(A, rg, tm, pb, NT_ADJ)) return;
   const int a = pb.a, b = pb.b;
   const int64_t s0 = A.state_off[pb.p];
   const T *lam = static_cast<const T *>(A.lam) + s0;
@@ -359,6 +359,22 @@ __global__ void __launch_bounds__(block_for<P>()) adjoint_rnea_kernel(KArgs A) {
       mbar[i] = -(dot6(Fb, JmA) - dot6(adVFb, JmV));
     }
   }
+}
+
+template <class T, int P>
+__global__ void __launch_bounds__(block_for<P>()) adjoint_rnea_kernel(KArgs A) {
+  adjoint_body<T, P>(A, Range{0, 0, A.n_problems});
+}
+
+// One launch over length classes (see the ClassTable kernels of fd_kernels.cuh).
+template <class T>
+__global__ void __launch_bounds__(128) adjoint_multi_kernel(KArgs A, ClassTable ct) {
+  const int c = class_of_block(ct);
+  const Range rg{ct.blk[c], ct.first[c], ct.first[c + 1]};
+#define FDK_C(PP) \
+  case PP: adjoint_body<T, PP>(A, rg); break;
+  FDK_CLASS_TEAMS(FDK_C)
+#undef FDK_C
 }
 
 }  // namespace fdk

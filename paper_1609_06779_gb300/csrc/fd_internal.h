@@ -32,6 +32,15 @@ struct fd_batch_s {
   int64_t *d_sq_off = nullptr;
   int32_t *d_order = nullptr;
   int tuned[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // autotuned team per [algo][prec]
+  // Length classes: problems whose link counts share ceil(log2 n) (n <= 1: class
+  // 0), as contiguous ranges [first, first + count) of the processing order
+  // (longest first). A batch with more than one class is solved with team 0 in
+  // one launch whose grid is split by class, each class with its own team.
+  struct LenClass {
+    int32_t key, first, count, min_len, max_len;
+  };
+  std::vector<LenClass> classes;
+  std::vector<int> ctuned;  // autotuned team per [class][algo][prec] (0: not tuned)
 };
 
 // Sets the calling thread's fd_last_error message and returns st.

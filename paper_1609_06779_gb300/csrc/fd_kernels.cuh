@@ -25,10 +25,11 @@ struct Prob {
 };
 
 template <class T, int P>
-__device__ __forceinline__ bool load_problem(const KArgs &A, const Team<P> &tm, Prob<T> &pb,
-                                             int nt_stride) {
-  const long long team = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) / P;
-  if (team >= A.n_problems) return false;
+__device__ __forceinline__ bool load_problem(const KArgs &A, const Range &rg, const Team<P> &tm,
+                                             Prob<T> &pb, int nt_stride) {
+  const long long team =
+      rg.t0 + (static_cast<long long>(blockIdx.x - rg.blk0) * blockDim.x + threadIdx.x) / P;
+  if (team >= rg.t1) return false;
   const int p = A.order ? A.order[team] : static_cast<int>(team);
   const int c = A.prob_chain ? A.prob_chain[p] : p;  // no map: problem p is chain p
   const int64_t m0 = A.model_off[c];
@@ -422,12 +423,17 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
 }
 
 template <class T, int P>
-__global__ void __launch_bounds__(block_for<P>()) id_kernel(KArgs A) {
+__device__ __forceinline__ void id_body(const KArgs &A, const Range &rg) {
   Team<P> tm;
   Prob<T> pb;
-  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  if (!load_problem<T, P>(A, rg, tm, pb, NT)) return;
   id_team<T, P>(tm, pb, A.grav, MODE_ID);
   for (int i = pb.a; i < pb.b; ++i) pb.out[i] = pb.wt[static_cast<int64_t>(i) * NT + W_TD];
+}
+
+template <class T, int P>
+__global__ void __launch_bounds__(block_for<P>()) id_kernel(KArgs A) {
+  id_body<T, P>(A, Range{0, 0, A.n_problems});
 }
 
 // -------------------------------------------------------------------- CFA
@@ -828,10 +834,10 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, bool 
 // right-hand side (tau_delta := in4) rides along: the blocks D, U and their
 // elimination are shared, only R, F_c and CalcAcc are done twice.
 template <class T, class TA, int P, int BTD, bool TWO>
-__device__ __forceinline__ void cfa_body(const KArgs &A) {
+__device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
   Team<P> tm;
   Prob<T> pb;
-  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  if (!load_problem<T, P>(A, rg, tm, pb, NT)) return;
   const int n = pb.n;
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_CFA;
   bool bad = false;
@@ -1068,23 +1074,23 @@ __device__ __forceinline__ void cfa_body(const KArgs &A) {
 
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(KArgs A) {
-  cfa_body<T, TA, P, 0, false>(A);
+  cfa_body<T, TA, P, 0, false>(A, Range{0, 0, A.n_problems});
 }
 
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_cr_kernel(KArgs A) {
-  cfa_body<T, TA, P, 1, false>(A);
+  cfa_body<T, TA, P, 1, false>(A, Range{0, 0, A.n_problems});
 }
 
 // MODE_FD2: forward dynamics and the adjoint's linear solve in one elimination
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa2_kernel(KArgs A) {
-  cfa_body<T, TA, P, 0, true>(A);
+  cfa_body<T, TA, P, 0, true>(A, Range{0, 0, A.n_problems});
 }
 
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_cr2_kernel(KArgs A) {
-  cfa_body<T, TA, P, 1, true>(A);
+  cfa_body<T, TA, P, 1, true>(A, Range{0, 0, A.n_problems});
 }
 
 // ------------------------------------------------------------------ JSIIA
@@ -1321,12 +1327,12 @@ __device__ __forceinline__ void congruence_pair(const Team<P> &tm, const SE3<TA>
 // per lane through a shared-memory transpose) for teams of 8 and more, on a pair
 // of lanes for teams of 2 and 4, on one lane alone.
 template <class T, class TA, int P>
-__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel(KArgs A) {
+__device__ __forceinline__ void jsiia_body(const KArgs &A, const Range &rg) {
   constexpr int NXB = P >= 8 ? block_for<P>() / P : 1;
   __shared__ TA xbuf[NXB][2][36];
   Team<P> tm;
   Prob<T> pb;
-  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  if (!load_problem<T, P>(A, rg, tm, pb, NT)) return;
   const int n = pb.n, a = pb.a, b = pb.b;
   const int64_t s0 = A.state_off[pb.p];
   TA *vec = static_cast<TA *>(A.ws_a) + s0 * NA_JSIIA + A.sq_off[pb.p] * NSQ_JSIIA;
@@ -1668,6 +1674,11 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
   if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
 }
 
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel(KArgs A) {
+  jsiia_body<T, TA, P>(A, Range{0, 0, A.n_problems});
+}
+
 // ------------------------------------------------------------------- ABIA
 
 
@@ -1679,10 +1690,10 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 4 : 1) jsiia_kernel
 // side in4 shares the articulated inertias; its bias force and acceleration pass
 // give M^{-1} in4 in out4.
 template <class T, class TA, bool TWO>
-__global__ void __launch_bounds__(128, TWO ? 3 : 4) abia_kernel(KArgs A) {
+__device__ __forceinline__ void abia_body(const KArgs &A, const Range &rg) {
   Team<1> tm;
   Prob<T> pb;
-  if (!load_problem<T, 1>(A, tm, pb, NT)) return;
+  if (!load_problem<T, 1>(A, rg, tm, pb, NT)) return;
   const int n = pb.n;
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_ABIA;
   bool bad = false;
@@ -1781,6 +1792,11 @@ __global__ void __launch_bounds__(128, TWO ? 3 : 4) abia_kernel(KArgs A) {
   set_status(A.status, pb.p, bad ? 2 : 0);
 }
 
+template <class T, class TA, bool TWO>
+__global__ void __launch_bounds__(128, TWO ? 3 : 4) abia_kernel(KArgs A) {
+  abia_body<T, TA, TWO>(A, Range{0, 0, A.n_problems});
+}
+
 
 // ABIA with a team of P (8..32) lanes per problem. Inverse dynamics runs on
 // the team (component lanes or segmented scans). The articulated-inertia
@@ -1792,12 +1808,12 @@ __global__ void __launch_bounds__(128, TWO ? 3 : 4) abia_kernel(KArgs A) {
 // carry one component per lane, as in the component-lane inverse dynamics.
 // Each step's operands are loaded one step ahead (the loop is latency-bound).
 template <class T, class TA, int P, bool TWO>
-__global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
+__device__ __forceinline__ void abia_team_body(const KArgs &A, const Range &rg) {
   static_assert(P >= 8 && P <= 32, "six rows of P need a team of 8..32 lanes");
   __shared__ TA xbuf[128 / P][2][36];
   Team<P> tm;
   Prob<T> pb;
-  if (!load_problem<T, P>(A, tm, pb, NT)) return;
+  if (!load_problem<T, P>(A, rg, tm, pb, NT)) return;
   const int n = pb.n;
   const int r = tm.r < 6 ? tm.r : 5;  // lanes 6.. shadow row 5 and write nothing
   const bool top = r < 3;
@@ -2095,6 +2111,75 @@ __global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
     }
   }
   if (tm.r == 0) set_status(A.status, pb.p, bad ? 2 : 0);
+}
+
+template <class T, class TA, int P, bool TWO>
+__global__ void __launch_bounds__(128) abia_team_kernel(KArgs A) {
+  abia_team_body<T, TA, P, TWO>(A, Range{0, 0, A.n_problems});
+}
+
+// ---------------------------------------------------------- length classes
+//
+// One launch over a batch whose problems fall into length classes: the grid is
+// split into the classes' block ranges (ClassTable), and each block runs the
+// body of its class's team size. The kernels instantiate every team size up to
+// one 128-thread block, so a class of short chains can run one thread per chain
+// while a class of long chains runs a warp or a block per chain in the same
+// launch.
+
+__device__ __forceinline__ int class_of_block(const ClassTable &ct) {
+  int c = 0;
+  while (c + 1 < ct.n && static_cast<int>(blockIdx.x) >= ct.blk[c + 1]) ++c;
+  return c;
+}
+
+#define FDK_CLASS_TEAMS(CALL)                                                          \
+  switch (ct.team[c]) {                                                                \
+    CALL(1) CALL(2) CALL(4) CALL(8) CALL(16) CALL(32) CALL(64) CALL(128) default: break; \
+  }
+
+template <class T>
+__global__ void __launch_bounds__(128) id_multi_kernel(KArgs A, ClassTable ct) {
+  const int c = class_of_block(ct);
+  const Range rg{ct.blk[c], ct.first[c], ct.first[c + 1]};
+#define FDK_C(PP) \
+  case PP: id_body<T, PP>(A, rg); break;
+  FDK_CLASS_TEAMS(FDK_C)
+#undef FDK_C
+}
+
+template <class T, class TA, int BTD, bool TWO>
+__global__ void __launch_bounds__(128, 3) cfa_multi_kernel(KArgs A, ClassTable ct) {
+  const int c = class_of_block(ct);
+  const Range rg{ct.blk[c], ct.first[c], ct.first[c + 1]};
+#define FDK_C(PP) \
+  case PP: cfa_body<T, TA, PP, BTD, TWO>(A, rg); break;
+  FDK_CLASS_TEAMS(FDK_C)
+#undef FDK_C
+}
+
+template <class T, class TA>
+__global__ void __launch_bounds__(128, 4) jsiia_multi_kernel(KArgs A, ClassTable ct) {
+  const int c = class_of_block(ct);
+  const Range rg{ct.blk[c], ct.first[c], ct.first[c + 1]};
+#define FDK_C(PP) \
+  case PP: jsiia_body<T, TA, PP>(A, rg); break;
+  FDK_CLASS_TEAMS(FDK_C)
+#undef FDK_C
+}
+
+// ABIA: team 1 (one thread per chain) or the six-row lane teams of 8, 16, 32
+template <class T, class TA, bool TWO>
+__global__ void __launch_bounds__(128, TWO ? 3 : 4) abia_multi_kernel(KArgs A, ClassTable ct) {
+  const int c = class_of_block(ct);
+  const Range rg{ct.blk[c], ct.first[c], ct.first[c + 1]};
+  switch (ct.team[c]) {
+    case 1: abia_body<T, TA, TWO>(A, rg); break;
+    case 8: abia_team_body<T, TA, 8, TWO>(A, rg); break;
+    case 16: abia_team_body<T, TA, 16, TWO>(A, rg); break;
+    case 32: abia_team_body<T, TA, 32, TWO>(A, rg); break;
+    default: break;
+  }
 }
 
 }  // namespace fdk

@@ -20,6 +20,16 @@ cudaError_t launch_abia(const KArgs &a, int prec, int team, cudaStream_t s);
 inline bool abia_team_ok(int team) { return team == 1 || team == 8 || team == 16 || team == 32; }
 cudaError_t launch_adjoint_rnea(const KArgs &a, int prec, int team, cudaStream_t s);
 
+// One launch over the length classes of `ct` (teams of 1 .. 128 lanes, one per
+// class; ABIA 1, 8, 16 or 32), grid ct.blk[ct.n] blocks of BLOCK threads.
+cudaError_t launch_id_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
+cudaError_t launch_cfa_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
+cudaError_t launch_cfa_cr_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
+cudaError_t launch_jsiia_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
+cudaError_t launch_abia_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
+cudaError_t launch_adjoint_rnea_multi(const KArgs &a, int prec, const ClassTable &ct,
+                                      cudaStream_t s);
+
 inline unsigned grid_for(int n_problems, int team) {
   const int block = team > BLOCK ? team : BLOCK;
   const long long threads = static_cast<long long>(n_problems) * team;

@@ -89,6 +89,24 @@ constexpr int MODE_FD2 = 3;     // MODE_FD into out, and M^{-1} in4 into out4 wi
 constexpr int MODE_RES = 4;     // inverse dynamics only (the FP32 CFA refinement pass):
                                 // tau_delta = in3 - ID(q, qd, out), the residual of out
 
+// The problems one launch (or one length class of a launch) covers: positions
+// t0 .. t1-1 of the processing order, starting at block blk0 of the grid.
+struct Range {
+  int32_t blk0;
+  int32_t t0, t1;
+};
+
+// A launch split into length classes: class c takes blocks blk[c] .. blk[c+1]-1
+// and problems first[c] .. first[c+1]-1 of the processing order (longest first,
+// so a class is a contiguous range), with a team of team[c] lanes per problem.
+constexpr int MAX_CLASSES = 24;
+struct ClassTable {
+  int32_t n;
+  int32_t blk[MAX_CLASSES + 1];
+  int32_t first[MAX_CLASSES + 1];
+  int32_t team[MAX_CLASSES];
+};
+
 struct KArgs {
   const void *model;         // [L][REC] of T
   const void *model64;       // [L][REC] of double (the FP64 copy; mixed-precision CFA blocks)

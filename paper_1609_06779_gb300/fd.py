@@ -73,9 +73,14 @@ def load(build_if_missing: bool = True):
         lib.fd_autotune.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, sz, vp,
                                     ctypes.POINTER(i32)]
         lib.fd_autotune.restype = ctypes.c_int
+        lib.fd_batch_classes.argtypes = [vp, i32, i32, i32, i32p, i32p, i32p, i32p, i32p]
+        lib.fd_autotune_cache_load.argtypes = [ctypes.c_char_p, i32p]
+        lib.fd_autotune_cache_save.argtypes = [ctypes.c_char_p]
+        lib.fd_autotune_cache_clear.argtypes = []
         for f in ("fd_create_chain", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
                   "fd_batch_destroy", "fd_batch_info", "fd_solve_batch", "fd_inverse_dynamics",
-                  "fd_solve_cfa_static"):
+                  "fd_solve_cfa_static", "fd_batch_classes", "fd_autotune_cache_load",
+                  "fd_autotune_cache_save", "fd_autotune_cache_clear"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -332,8 +337,11 @@ def forward_dynamics(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", team=0):
 def autotune(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", max_workspace_bytes=32 << 30,
              stream=None) -> int:
     """Time the team sizes (fd_autotune) and record the fastest in the batch plan;
-    returns it. Team sizes whose workspace exceeds ``max_workspace_bytes`` are
-    skipped, except the smallest."""
+    returns it, or 0 for a batch of several length classes (then every class has
+    its own team: see :func:`batch_classes`). Team sizes whose workspace exceeds
+    ``max_workspace_bytes`` are skipped, except the smallest. Entries of the
+    process-wide autotune cache (:func:`autotune_cache_load`) are used without
+    timing."""
     torch = _torch()
     dt = _state_dtype(prec)
     for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau")):
@@ -353,6 +361,39 @@ def autotune(batch: Batch, q, qd, tau, algo="cfa", prec="fp64", max_workspace_by
                               tau.data_ptr(), out.data_ptr(), ws.data_ptr(), ws.numel(),
                               ctypes.c_void_p(s.cuda_stream), ctypes.byref(best)))
     return best.value
+
+
+def batch_classes(batch: Batch, algo="cfa", prec="fp64"):
+    """The batch's length classes (fd_batch_classes): a list of dicts with the
+    class's shortest and longest chain, its problem count and the team a team-0
+    solve of ``algo`` / ``prec`` runs it with."""
+    lib = load()
+    n = ctypes.c_int32(0)
+    _check(lib.fd_batch_classes(batch.handle, ALGOS[algo] if algo else -1, PRECS[prec], 0,
+                                ctypes.byref(n), None, None, None, None))
+    k = n.value
+    arrs = [(ctypes.c_int32 * max(k, 1))() for _ in range(4)]
+    _check(lib.fd_batch_classes(batch.handle, ALGOS[algo] if algo else -1, PRECS[prec], k,
+                                ctypes.byref(n), *arrs))
+    return [{"min_len": arrs[0][c], "max_len": arrs[1][c], "count": arrs[2][c],
+             "team": arrs[3][c]} for c in range(k)]
+
+
+def autotune_cache_load(path) -> int:
+    """Merge a saved autotune cache into the process-wide one (a missing file
+    loads nothing); returns the number of entries read."""
+    n = ctypes.c_int32(0)
+    _check(load().fd_autotune_cache_load(os.fsencode(path), ctypes.byref(n)))
+    return n.value
+
+
+def autotune_cache_save(path):
+    """Write the process-wide autotune cache as JSON."""
+    _check(load().fd_autotune_cache_save(os.fsencode(path)))
+
+
+def autotune_cache_clear():
+    _check(load().fd_autotune_cache_clear())
 
 
 # ------------------------------------------------------------------- serving

@@ -113,3 +113,36 @@ def test_server_without_a_device_fails_loudly(lib):
     assert lib.fd_serve_create(0, 64 << 20, g, 0, ctypes.byref(h)) == 4
     assert lib.fd_serve_create(0, 1 << 10, g, 0, ctypes.byref(h)) == 1   # budget too small
     assert h.value is None
+
+
+def test_autotune_cache_round_trip(lib, tmp_path):
+    """The autotune cache is host-only JSON: a saved cache loads back, a missing
+    file loads nothing, a malformed one is rejected."""
+    import json
+    fd.autotune_cache_clear()
+    assert fd.autotune_cache_load(str(tmp_path / "missing.json")) == 0
+    src = {"format": "fd_gb300 autotune cache 1", "entries": [
+        {"gpu": "NVIDIA GB300 (152 SMs)", "algo": 2, "prec": 0, "len_class": 5,
+         "count_class": 16, "team": 8, "ms": 11.0},
+        {"gpu": "NVIDIA GB300 (152 SMs)", "algo": 0, "prec": 2, "len_class": 9,
+         "count_class": 10, "team": 32, "ms": 3.2}]}
+    p = tmp_path / "cache.json"
+    p.write_text(json.dumps(src))
+    assert fd.autotune_cache_load(str(p)) == 2
+    out = tmp_path / "saved.json"
+    fd.autotune_cache_save(str(out))
+    got = json.loads(out.read_text())
+    assert got["format"] == src["format"]
+    key = lambda e: (e["algo"], e["prec"], e["len_class"], e["count_class"], e["team"])
+    assert sorted(map(key, got["entries"])) == sorted(map(key, src["entries"]))
+    bad = tmp_path / "bad.json"
+    bad.write_text(json.dumps({"format": "fd_gb300 autotune cache 1", "entries": [
+        {"gpu": "x", "algo": 0, "prec": 0, "len_class": 1, "count_class": 1, "team": 4}]}))
+    with pytest.raises(fd.FDError):          # ABIA has no team of 4
+        fd.autotune_cache_load(str(bad))
+    bad.write_text("{}")
+    with pytest.raises(fd.FDError):
+        fd.autotune_cache_load(str(bad))
+    fd.autotune_cache_clear()
+    fd.autotune_cache_save(str(out))
+    assert json.loads(out.read_text())["entries"] == []

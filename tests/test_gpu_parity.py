@@ -290,7 +290,8 @@ def test_full_size_uniform_batch_sampled(prec):
 
 def test_autotune_records_a_team_and_matches():
     fd = _fd()
-    model = synth.random_chains([32] * 2048 + [7] * 100, seed=71)
+    # one length class (17..32 links): one team for the whole batch
+    model = synth.random_chains([32] * 2048 + [17] * 100, seed=71)
     st = synth.random_states(model.n_links_total, seed=72)
     cs = fd.ChainSet(model)
     b = fd.Batch(cs)

@@ -48,8 +48,19 @@ def _static(lib, fd, cs, q, qd, tau, prec, team, stream):
 def test_static_scratch_cfa_equals_workspace_cfa(prec, team):
     fd, model, st, cs, q, qd, tau = _setup(prec)
     lib = fd.load()
-    b = fd.Batch(cs)  # problem p = chain p, untuned: team 0 resolves to the same default
-    ref = fd.solve(b, q, qd, tau, algo="cfa", prec=prec, team=team)
+    b = fd.Batch(cs)  # problem p = chain p, untuned
+    # team 0: the documented default, the largest power of two not above
+    # 152 x 2048 / n_chains, capped at the longest chain rounded up to a power of two
+    expect = team
+    if team == 0:
+        expect = 1
+        while 2 * expect <= 152 * 2048 // len(LENGTHS) and expect < 256:
+            expect *= 2
+        cap = 1
+        while cap < max(LENGTHS) and cap < 256:
+            cap *= 2
+        expect = min(expect, cap)
+    ref = fd.solve(b, q, qd, tau, algo="cfa", prec=prec, team=expect)
     torch.cuda.synchronize()
     # a non-blocking side stream: nothing orders the solve after work on the legacy stream
     stream = torch.cuda.Stream(priority=0)
