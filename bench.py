@@ -31,7 +31,10 @@ N_LINKS = 32
 ALGOS = ("abia", "jsiia", "cfa")
 METRIC = "FD solves/s (32-link, batch 64K) ABIA/JSIIA/CFA"
 WORKLOAD = "65536 independent 32-link revolute chains (random models, seed 0), FP64"
-FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)
+# GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz): replaced at run time by
+# the rate measured on this GPU (fd_measure_fp64_peak), see measure_peak()
+FP64_PEAK_TFLOPS = 1.25
+PEAK_INFO = {"source": "nominal (not measured)"}
 
 
 def parse():
@@ -124,6 +127,29 @@ def traffic_record(kernel: str, team: int):
     return ent
 
 
+def measure_peak(fd, device):
+    """The FP64 roofline denominator, measured on this GPU: independent DFMA
+    chains (fd_measure_fp64_peak), best of three runs of a few hundred
+    milliseconds, with the SM clock sampled meanwhile."""
+    global FP64_PEAK_TFLOPS, PEAK_INFO
+    clk = Clocks(os.path.join(tempfile.gettempdir(), f"fd_peak_clocks_{os.getpid()}.csv"), device)
+    runs = []
+    with clk:
+        time.sleep(0.3)
+        for _ in range(3):
+            runs.append(fd.measure_fp64_peak(device, 200000))
+    best = max(r[0] for r in runs)
+    cs = clk.summary()
+    FP64_PEAK_TFLOPS = best
+    PEAK_INFO = {"source": "measured: fd_measure_fp64_peak (independent DFMA chains, 4 blocks x "
+                           "128 threads per SM), best of 3",
+                 "tflops_runs": [r[0] for r in runs], "ms_runs": [r[1] for r in runs],
+                 "clocks": cs,
+                 "tflops_at_max_clock": (best * cs["sm_max_mhz"] / cs["sm_mhz"]
+                                         if cs.get("sm_mhz") and cs.get("sm_max_mhz") else None)}
+    return best
+
+
 def measured_hbm_gbs():
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -199,19 +225,31 @@ def accuracy(model, st, outs, sample32=4096):
                            model.offsets[:k32 + 1].copy(), model.gravity)
     ref32 = oracle.fd(sub, f32(st.q[:L32]), f32(st.qdot[:L32]), f32(st.tau[:L32]),
                       algo="cholesky", n_threads=threads).reshape(k32, n)
+    # cond(M) of the sampled chains: a backward-stable single-precision solve
+    # loses about cond(M) eps32; "well conditioned" means cond(M) eps32 <= 1e-4
+    eps32 = float(np.finfo(np.float32).eps)
+    cond = np.array([np.linalg.cond(oracle.mass_matrix(model.chain(k),
+                                                       st.q[model.offsets[k]:model.offsets[k + 1]]))
+                     for k in range(k32)])
     res = {"reference": "FP64 CPU oracle, dense Cholesky", "chains_fp64": K,
-           "chains_float": k32, "float_paths_also_vs_states_rounded_to_fp32": {}}
+           "chains_float": k32, "float_paths_also_vs_states_rounded_to_fp32": {},
+           "cond_M_float_sample": {"min": float(cond.min()), "median": float(np.median(cond)),
+                                   "max": float(cond.max()),
+                                   "well_conditioned_chains": int((cond * eps32 <= 1e-4).sum())},
+           "float_err_over_cond_eps32_max": {}}
 
-    def err(got, r):
+    def errs(got, r):
         scale = np.maximum(np.abs(r).max(axis=1), 1.0)
-        return float((np.abs(got - r).max(axis=1) / scale).max())
+        return np.abs(got - r).max(axis=1) / scale
     for k, v in outs.items():
         got = v.double().numpy()
         rows = got.size // n
         got = got.reshape(rows, n)
-        res[k] = err(got, ref[:rows])
+        res[k] = float(errs(got, ref[:rows]).max())
         if not k.endswith("fp64"):
-            res["float_paths_also_vs_states_rounded_to_fp32"][k] = err(got[:k32], ref32)
+            e32 = errs(got[:k32], ref[:k32])
+            res["float_paths_also_vs_states_rounded_to_fp32"][k] = float(errs(got[:k32], ref32).max())
+            res["float_err_over_cond_eps32_max"][k] = float((e32 / (cond * eps32)).max())
     return res
 
 
@@ -366,12 +404,13 @@ def extra_configs(dev, keep=None):
         kl = {"config": f"{count}x{n}_links_fp64", "model": m, "chain_index": None, "st": st,
               "problems": [0, 1] if n <= 256 else [0], "outs": {}}
         for a in ALGOS + ("cfa_cr",):
-            if a == "jsiia" and n > 256:
-                continue  # cubic in n: about 0.3 s per solve of this batch
+            # JSIIA is cubic in n: at 1 024 links one timed solve, no autotuning
             team = 128 if a == "jsiia" else fd.autotune(b, q, qd, tau, algo=a)
             ws = fd.workspace(b, a, "fp64", team, dev)
             out = torch.empty_like(q)
-            ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, team=team, out=out, ws=ws))
+            reps = (1, 1) if (a == "jsiia" and n > 256) else (3, 1)
+            ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, team=team, out=out, ws=ws),
+                          *reps)
             kl["outs"][a] = out.cpu().numpy()
             fl = roofline.flops(a, [n] * count)
             rl[a] = {"team": team, "ms": ms, "solves_per_s": count / (ms * 1e-3),
@@ -383,7 +422,10 @@ def extra_configs(dev, keep=None):
         del cs, b, q, qd, tau
         torch.cuda.empty_cache()
 
-    # uneven batch: 100 000 chains, n log-uniform in [6, 512], mixed precision
+    # uneven batch: 100 000 chains, n log-uniform in [6, 512], mixed precision:
+    # one launch split by length class (a team per class, autotuned per class),
+    # timed eagerly and as a CUDA-graph replay, against the best single team for
+    # the whole batch and against one launch per distinct length
     lengths = synth.log_uniform_lengths(100000, 6, 512, seed=0)
     m = synth.random_chains(lengths, seed=1)
     st = synth.random_states(m.n_links_total, seed=2)
@@ -395,12 +437,30 @@ def extra_configs(dev, keep=None):
     ku = {"config": "100000_uneven_6_512_mixed", "model": m, "chain_index": None, "st": st,
           "problems": np.random.default_rng(5).choice(100000, 64, replace=False).tolist(),
           "outs": {}}
-    for a in ("abia", "cfa"):
-        team = fd.autotune(b, q, qd, tau, algo=a, prec="mixed")
+    for a in ("abia", "cfa", "cfa_cr"):
+        fd.autotune(b, q, qd, tau, algo=a, prec="mixed")   # per length class
+        classes = fd.batch_classes(b, a, "mixed")
         ws = fd.workspace(b, a, "mixed", 0, dev)
         out = torch.empty_like(q)
         one_ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, prec="mixed", out=out, ws=ws))
+        s_cap = torch.cuda.Stream(device=dev)
+        s_cap.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s_cap):
+            fd.solve(b, q, qd, tau, algo=a, prec="mixed", out=out, ws=ws)
+        torch.cuda.current_stream(dev).wait_stream(s_cap)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fd.solve(b, q, qd, tau, algo=a, prec="mixed", out=out, ws=ws)
+        graph_ms = _time_ms(g.replay)
+        torch.cuda.synchronize()
         ku["outs"][a + "_mixed"] = out.double().cpu().numpy()
+        del g
+        # one team for every chain (the schedule without length classes)
+        single = {}
+        for tm in ((1, 8, 32) if a == "abia" else (4, 8, 16, 32)):
+            single[tm] = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, prec="mixed", team=tm,
+                                                   out=out, ws=ws))
+        best_t = min(single, key=single.get)
         del ws
         # one launch per distinct chain length (static batching per size)
         groups = []
@@ -419,13 +479,22 @@ def extra_configs(dev, keep=None):
                 fd.solve(bb, gq, gqd, gtau, algo=a, prec="mixed", out=go, ws=gw)
 
         ps_ms = _time_ms(per_size)
-        ru[a] = {"team": team, "one_launch_ms": one_ms, "per_size_launches_ms": ps_ms,
-                 "per_size_launches": len(groups),
+        ru[a] = {"classes": [{"links": f"{c['min_len']}-{c['max_len']}", "chains": c["count"],
+                              "team": c["team"]} for c in classes],
+                 "one_launch_ms": one_ms, "graph_replay_ms": graph_ms,
+                 "single_team_ms": {str(k): v for k, v in single.items()},
+                 "best_single_team": best_t,
+                 "per_size_launches_ms": ps_ms, "per_size_launches": len(groups),
+                 "solves_per_s_graph": 100000 / (graph_ms * 1e-3),
                  "solves_per_s_one_launch": 100000 / (one_ms * 1e-3),
-                 "solves_per_s_per_size": 100000 / (ps_ms * 1e-3)}
+                 "solves_per_s_best_single_team": 100000 / (single[best_t] * 1e-3),
+                 "solves_per_s_per_size": 100000 / (ps_ms * 1e-3),
+                 "gflop": roofline.flops(a, lengths) / 1e9,
+                 "tflops_graph": roofline.flops(a, lengths) / (graph_ms * 1e-3) / 1e12}
         del groups
         torch.cuda.empty_cache()
     w = torch.randn(m.n_links_total, dtype=torch.float32, device=dev)
+    fd.autotune(b, q, qd, tau, algo="cfa", prec="mixed")
     adj_ms = _time_ms(lambda: fd.adjoint(b, q, qd, tau, w, algo="cfa", prec="mixed",
                                          masses=False))
     ru["adjoint_cfa_ms"] = adj_ms
@@ -452,8 +521,17 @@ def config_accuracy(keep):
                   n_threads=os.cpu_count() or 1)
         if k["problems"] is not None:
             kw["problems"] = probs
+        t0 = time.perf_counter()
         ref = oracle.fd(m, st.q, st.qdot, st.tau, algo="cholesky", **kw)
+        t1 = time.perf_counter()
         aba = oracle.fd(m, st.q, st.qdot, st.tau, algo="aba", **kw)
+        t2 = time.perf_counter()
+        # the CPU baseline of this configuration: the oracle's two routes on the
+        # sampled problems (OpenMP across problems)
+        cpu_cfg = {"kind": "oracle", "cores": kw["n_threads"], "problems": len(probs),
+                   "cholesky_solves_per_s": len(probs) / max(t1 - t0, 1e-9),
+                   "aba_solves_per_s": len(probs) / max(t2 - t1, 1e-9),
+                   "sample": f"{len(probs)} of {n_prob} problems, FP64"}
         f32 = lambda a: a.astype(np.float32).astype(np.float64)
         ref32 = None
         if any(not name.endswith(("fp64",)) and "mixed" in name for name in k["outs"]):
@@ -466,7 +544,7 @@ def config_accuracy(keep):
                 a, b = int(offs[p]), int(offs[p + 1])
                 e = max(e, float(np.abs(x[a:b] - rf[a:b]).max() / max(np.abs(rf[a:b]).max(), 1.0)))
             return e
-        r = {"sampled_problems": len(probs), "oracle_aba_floor": err(aba)}
+        r = {"sampled_problems": len(probs), "oracle_aba_floor": err(aba), "cpu_oracle": cpu_cfg}
         for name, x in k["outs"].items():
             r[name] = err(x)
             if ref32 is not None and "mixed" in name:
@@ -524,6 +602,8 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     from paper_1609_06779_gb300 import fd
+
+    measure_peak(fd, local)
 
     # weak scaling: every rank solves its own 65 536-chain batch (no data exchange)
     model = synth.random_chains([args.links] * args.chains, seed=rank)
@@ -596,7 +676,7 @@ def main():
     roof = {"bound": "alu", "achieved": rl[dom]["tflops"], "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": rl[dom]["frac"], "traffic": traffic,
             "kernel": f"{dom}_kernel, team {teams[dom]}, FP64",
-            "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s), not measured",
+            "peak_source": PEAK_INFO,
             "algorithmic_flops_per_launch": roofline.flops(dom, lengths),
             "algorithmic_bytes_per_launch": alg_bytes,
             "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak,

@@ -292,6 +292,18 @@ fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const void *qdot,
                               const void *tau, void *qddot, fd_prec prec, int32_t team,
                               int32_t *status, void *stream);
 
+/*
+ * fd_measure_fp64_peak -- the FP64 rate this GPU sustains (not in the paper: the
+ * denominator of the FP64 kernels' roofline, which the FP64 pipe bounds). Runs
+ * independent fused multiply-adds, eight chains per thread, four 128-thread
+ * blocks per SM, `iters` steps per chain (about 2e5 take a few hundred
+ * milliseconds on a GB300), timed with CUDA events on a stream of its own after
+ * a shorter warm-up; *tflops receives 2 x FMAs / time in TFLOP/s and
+ * *elapsed_ms (may be NULL) the timed kernel's duration. Synchronous.
+ */
+fd_status fd_measure_fp64_peak(int32_t device, int32_t iters, double *tflops,
+                               double *elapsed_ms);
+
 /* ------------------------------------------------------------------ serving
  *
  * A server owns one device allocation of mem_budget_bytes (its memory budget)

@@ -74,6 +74,8 @@ def load(build_if_missing: bool = True):
                                     ctypes.POINTER(i32)]
         lib.fd_autotune.restype = ctypes.c_int
         lib.fd_batch_classes.argtypes = [vp, i32, i32, i32, i32p, i32p, i32p, i32p, i32p]
+        lib.fd_measure_fp64_peak.argtypes = [i32, i32, dp, dp]
+        lib.fd_measure_fp64_peak.restype = ctypes.c_int
         lib.fd_autotune_cache_load.argtypes = [ctypes.c_char_p, i32p]
         lib.fd_autotune_cache_save.argtypes = [ctypes.c_char_p]
         lib.fd_autotune_cache_clear.argtypes = []
@@ -377,6 +379,15 @@ def batch_classes(batch: Batch, algo="cfa", prec="fp64"):
                                 ctypes.byref(n), *arrs))
     return [{"min_len": arrs[0][c], "max_len": arrs[1][c], "count": arrs[2][c],
              "team": arrs[3][c]} for c in range(k)]
+
+
+def measure_fp64_peak(device=0, iters=200000):
+    """FP64 TFLOP/s of independent fused multiply-adds on this GPU and the timed
+    kernel's milliseconds (fd_measure_fp64_peak)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().fd_measure_fp64_peak(int(device), int(iters), ctypes.byref(tf),
+                                       ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def autotune_cache_load(path) -> int:
