@@ -372,7 +372,7 @@ def extra_configs(dev, keep=None):
     r1 = {}
     k1 = {"config": "1x7_links_1024_states_fp64", "model": m, "chain_index": ci,
           "state_offsets": so1, "st": st, "problems": None, "outs": {}}
-    for a in ALGOS + ("cfa_cr",):
+    for a in ALGOS + ("cfa_cr", "cfa_hybrid"):
         team = fd.autotune(b, q, qd, tau, algo=a)
         ws = fd.workspace(b, a, "fp64", 0, dev)
         out = torch.empty_like(q)
@@ -403,7 +403,7 @@ def extra_configs(dev, keep=None):
         rl = {}
         kl = {"config": f"{count}x{n}_links_fp64", "model": m, "chain_index": None, "st": st,
               "problems": [0, 1] if n <= 256 else [0], "outs": {}}
-        for a in ALGOS + ("cfa_cr",):
+        for a in ALGOS + ("cfa_cr", "cfa_hybrid"):
             # JSIIA is cubic in n: at 1 024 links one timed solve, no autotuning
             team = 128 if a == "jsiia" else fd.autotune(b, q, qd, tau, algo=a)
             ws = fd.workspace(b, a, "fp64", team, dev)
@@ -437,7 +437,7 @@ def extra_configs(dev, keep=None):
     ku = {"config": "100000_uneven_6_512_mixed", "model": m, "chain_index": None, "st": st,
           "problems": np.random.default_rng(5).choice(100000, 64, replace=False).tolist(),
           "outs": {}}
-    for a in ("abia", "cfa", "cfa_cr"):
+    for a in ("abia", "cfa", "cfa_cr", "cfa_hybrid"):
         fd.autotune(b, q, qd, tau, algo=a, prec="mixed")   # per length class
         classes = fd.batch_classes(b, a, "mixed")
         ws = fd.workspace(b, a, "mixed", 0, dev)
@@ -691,17 +691,19 @@ def main():
     # CFA with block cyclic reduction in place of OEE (context; not part of the step)
     variants = {}
     if rank == 0:
-        tcr = forced.get("cfa_cr") or fd.autotune(batch, q, qd, tau, algo="cfa_cr", prec="fp64")
-        wcr = fd.workspace(batch, "cfa_cr", "fp64", tcr, dev)
-        ocr = torch.empty_like(q)
-        ms = _time_ms(lambda: fd.solve(batch, q, qd, tau, algo="cfa_cr", team=tcr, out=ocr,
-                                       ws=wcr), reps=5, warm=2)
-        fl = roofline.flops("cfa_cr", lengths)
-        acc_outs["cfa_cr_fp64"] = ocr.cpu()
-        variants["cfa_cr_fp64"] = {"team": tcr, "ms": ms, "solves_per_s": args.chains / (ms * 1e-3),
-                                   "tflops": fl / (ms * 1e-3) / 1e12,
-                                   "frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
-        del wcr, ocr
+        for var in ("cfa_cr", "cfa_hybrid"):
+            tcr = forced.get(var) or fd.autotune(batch, q, qd, tau, algo=var, prec="fp64")
+            wcr = fd.workspace(batch, var, "fp64", tcr, dev)
+            ocr = torch.empty_like(q)
+            ms = _time_ms(lambda: fd.solve(batch, q, qd, tau, algo=var, team=tcr, out=ocr,
+                                           ws=wcr), reps=5, warm=2)
+            fl = roofline.flops(var, lengths)
+            acc_outs[f"{var}_fp64"] = ocr.cpu()
+            variants[f"{var}_fp64"] = {"team": tcr, "ms": ms,
+                                       "solves_per_s": args.chains / (ms * 1e-3),
+                                       "tflops": fl / (ms * 1e-3) / 1e12,
+                                       "frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+            del wcr, ocr
         # inverse dynamics alone (fd_inverse_dynamics, the scans of Eq. 2a-2d) and the
         # adjoint (FD and M^-1 w in one elimination, then the reverse sweep) of CFA
         for team in (8,):

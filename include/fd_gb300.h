@@ -45,11 +45,19 @@ typedef enum fd_algo {
   FD_ABIA = 0,  /* articulated-body inertia factorisation (Section II-C) */
   FD_JSIIA = 1, /* joint-space inertia by ID columns + Cholesky (Section II-C) */
   FD_CFA = 2,   /* constraint force algorithm with OEE (Section III, Alg. 1-2) */
-  FD_CFA_CR = 3 /* CFA with the block tri-diagonal system solved by block cyclic
-                   reduction instead of OEE: about n row updates instead of
-                   n ceil(log2 n), the same result (not in the paper's
-                   experiments; the reduction OEE is a variant of, Section IV) */
+  FD_CFA_CR = 3, /* CFA with the block tri-diagonal system solved by block cyclic
+                    reduction instead of OEE: about n row updates instead of
+                    n ceil(log2 n), the same result (not in the paper's
+                    experiments; the reduction OEE is a variant of, Section IV) */
+  FD_CFA_HYBRID = 4 /* CFA with the hybrid partition / cyclic-reduction solve:
+                       each lane eliminates the interior rows of its own run of
+                       rows, block cyclic reduction solves the reduced system of
+                       the runs' end rows across the lanes, each lane back-
+                       substitutes its interior (not in the paper's experiments;
+                       a partitioned form of the reductions of Section IV) */
 } fd_algo;
+
+#define FD_N_ALGOS 5
 
 typedef enum fd_prec {
   FD_FP64 = 0,  /* states and all arithmetic in double */

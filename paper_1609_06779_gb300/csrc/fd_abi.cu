@@ -424,7 +424,7 @@ fd_status fd_batch_create(fd_chain_t c, int32_t n_problems, const int32_t *chain
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto *b = new fd_batch_s();
   b->classes = classes;
-  b->ctuned.assign(classes.size() * 12, 0);
+  b->ctuned.assign(classes.size() * FD_N_ALGOS * 3, 0);
   b->chain = c;
   b->device = c->device;
   b->n_problems = n_problems;
@@ -484,7 +484,7 @@ namespace {
 
 int resolve_team(const fd_batch_s *b, int32_t algo, fd_prec prec, int32_t team) {
   if (team > 0) return team;
-  const int tuned = (algo >= 0 && algo < 4 && prec >= 0 && prec < 3) ? b->tuned[algo][prec] : 0;
+  const int tuned = (algo >= 0 && algo < FD_N_ALGOS && prec >= 0 && prec < 3) ? b->tuned[algo][prec] : 0;
   if (tuned > 0) return tuned;
   return fdk_default_team(algo, b->n_problems, b->max_links);
 }
@@ -500,7 +500,8 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int /*team: no l
   const size_t as = prec == FD_FP32 ? 4 : 8;
   const size_t L = static_cast<size_t>(b->n_state_links);
   WsPlan w{align256(L * fdk::NT * ts), 0};
-  if (algo == FD_CFA || algo == FD_CFA_CR) w.a_bytes = L * fdk::NA_CFA * as;
+  if (algo == FD_CFA || algo == FD_CFA_CR || algo == FD_CFA_HYBRID)
+    w.a_bytes = L * fdk::NA_CFA * as;
   if (algo == FD_JSIIA)
     w.a_bytes = (L * fdk::NA_JSIIA + static_cast<size_t>(b->sum_sq) * fdk::NSQ_JSIIA) * as;
   if (algo == FD_ABIA) w.a_bytes = L * fdk::NA_ABIA * as;
@@ -515,7 +516,7 @@ bool use_classes(const fd_batch_s *b, int32_t team) { return team == 0 && b->cla
 
 int class_team(const fd_batch_s *b, size_t c, int32_t algo, fd_prec prec) {
   if (algo >= 0) {
-    const int tuned = b->ctuned[c * 12 + static_cast<size_t>(algo) * 3 + prec];
+    const int tuned = b->ctuned[(c * FD_N_ALGOS + static_cast<size_t>(algo)) * 3 + prec];
     if (tuned > 0) return tuned;
   }
   const auto &cl = b->classes[c];
@@ -555,6 +556,7 @@ cudaError_t launch_classes(const fdk::KArgs &a, int32_t algo, int prec_k,
   if (algo == -1) return fdk::launch_id_multi(a, prec_k, ct, s);
   if (algo == FD_CFA) return fdk::launch_cfa_multi(a, prec_k, ct, s);
   if (algo == FD_CFA_CR) return fdk::launch_cfa_cr_multi(a, prec_k, ct, s);
+  if (algo == FD_CFA_HYBRID) return fdk::launch_cfa_hy_multi(a, prec_k, ct, s);
   if (algo == FD_JSIIA) return fdk::launch_jsiia_multi(a, prec_k, ct, s);
   return fdk::launch_abia_multi(a, prec_k, ct, s);
 }
@@ -578,7 +580,8 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
-  if (algo != -1 && algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR)
+  if (algo != -1 && algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR &&
+      algo != FD_CFA_HYBRID)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, algo);
   if (team < 0 || (team > 0 && !valid_team(team)))
     return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 256", who, team);
@@ -628,6 +631,7 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   } else if (algo == -1) e = fdk::launch_id(a, prec_k, t, s);
   else if (algo == FD_CFA) e = fdk::launch_cfa(a, prec_k, t, s);
   else if (algo == FD_CFA_CR) e = fdk::launch_cfa_cr(a, prec_k, t, s);
+  else if (algo == FD_CFA_HYBRID) e = fdk::launch_cfa_hy(a, prec_k, t, s);
   else if (algo == FD_JSIIA) e = fdk::launch_jsiia(a, prec_k, t, s);
   else e = fdk::launch_abia(a, prec_k, t, s);
   cudaSetDevice(prev);
@@ -669,7 +673,8 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
                            int32_t *status, void *stream) {
   const char *who = "fd_solve_adjoint";
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
-  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR)
+  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR &&
+      algo != FD_CFA_HYBRID)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, static_cast<int>(algo));
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
@@ -731,6 +736,7 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
     if (split) return launch_classes(k, algo, prec_k, class_table(b, fd_teams), s);
     if (algo == FD_CFA) return fdk::launch_cfa(k, prec_k, t, s);
     if (algo == FD_CFA_CR) return fdk::launch_cfa_cr(k, prec_k, t, s);
+    if (algo == FD_CFA_HYBRID) return fdk::launch_cfa_hy(k, prec_k, t, s);
     if (algo == FD_JSIIA) return fdk::launch_jsiia(k, prec_k, t, s);
     return fdk::launch_abia(k, prec_k, t, s);
   };
@@ -881,7 +887,8 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
                                  int32_t *best_team) {
   const char *who = "fd_autotune";
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
-  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR)
+  if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR &&
+      algo != FD_CFA_HYBRID)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision", who);
@@ -928,7 +935,7 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
       const auto &cl = b->classes[c];
       int best = 0;
       st = tune(static_cast<int>(c), cl.max_len, cl.count, cl.key, 128, &best);
-      if (st == FD_OK) b->ctuned[c * 12 + static_cast<size_t>(algo) * 3 + prec] = best;
+      if (st == FD_OK) b->ctuned[(c * FD_N_ALGOS + static_cast<size_t>(algo)) * 3 + prec] = best;
     }
     if (st == FD_OK && best_team) *best_team = 0;
   } else {
@@ -947,7 +954,7 @@ extern "C" fd_status fd_batch_classes(fd_batch_t b, int32_t algo, fd_prec prec, 
                                       int32_t *n_classes, int32_t *min_len, int32_t *max_len,
                                       int32_t *count, int32_t *team) {
   if (!b || !n_classes) return fail(FD_ERR_INVALID_ARG, "fd_batch_classes: NULL argument");
-  if (algo < -1 || algo > FD_CFA_CR || prec < FD_FP64 || prec > FD_MIXED)
+  if (algo < -1 || algo >= FD_N_ALGOS || prec < FD_FP64 || prec > FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "fd_batch_classes: bad algorithm or precision");
   *n_classes = static_cast<int32_t>(b->classes.size());
   const bool split = b->classes.size() > 1;
@@ -1045,7 +1052,7 @@ extern "C" fd_status fd_autotune_cache_load(const char *path, int32_t *n_loaded)
     if (!field(obj, "gpu", &gpu, nullptr) || !field(obj, "algo", nullptr, &algo) ||
         !field(obj, "prec", nullptr, &prec) || !field(obj, "len_class", nullptr, &lc) ||
         !field(obj, "count_class", nullptr, &cc) || !field(obj, "team", nullptr, &team) ||
-        algo < 0 || algo > FD_CFA_CR || prec < 0 || prec > FD_MIXED || !fdk_valid_team(team) ||
+        algo < 0 || algo >= FD_N_ALGOS || prec < 0 || prec > FD_MIXED || !fdk_valid_team(team) ||
         (algo == FD_ABIA && !fdk::abia_team_ok(static_cast<int>(team))))
       return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_load: bad entry in %s", path);
     add[TuneKey{gpu, int(algo), int(prec), int(lc), int(cc)}] = TuneVal{int(team), 0.f};

@@ -31,7 +31,7 @@ struct fd_batch_s {
   int64_t *d_state_off = nullptr;
   int64_t *d_sq_off = nullptr;
   int32_t *d_order = nullptr;
-  int tuned[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // autotuned team per [algo][prec]
+  int tuned[FD_N_ALGOS][3] = {};  // autotuned team per [algo][prec]
   // Length classes: problems whose link counts share ceil(log2 n) (n <= 1: class
   // 0), as contiguous ranges [first, first + count) of the processing order
   // (longest first). A batch with more than one class is solved with team 0 in

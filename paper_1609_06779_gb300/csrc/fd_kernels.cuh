@@ -580,9 +580,10 @@ __device__ __forceinline__ void calc_ublock(const SE3<T> &gn, const T *Ki, Out U
 // g = L^{-1} R. Both neighbours of the row reuse them (SolvSys of Algorithm 2
 // with D = L L^T): E U_{i+d} = Z G_{i+d}, E R_{i+d} = Z g_{i+d} with
 // Z = U_i L_{i+d}^{-T}, and K U_{i-d} = G^T G, K R_{i-d} = G^T g of row i-d.
+// has_next: U_m couples row m to a row below it (else no G is formed).
 template <class TA>
-__device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD, int srcU,
-                                           int srcR, int srcR2 = -1) {
+__device__ __forceinline__ bool oee_factor_at(int m, bool has_next, int n, TA *wa, int srcD,
+                                              int srcU, int srcR, int srcR2 = -1) {
   const RowP<TA> row = rowp(wa, n, m);
   TA Dm[15], L[15], inv[5];
 #pragma unroll
@@ -605,7 +606,7 @@ __device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD
 #pragma unroll
     for (int k = 0; k < 5; ++k) row[A_GR2 + k] = r[k];
   }
-  if (m + d < n) {  // U_m couples row m to m + d; zero beyond
+  if (has_next) {  // U_m couples row m to the next row; zero beyond
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       TA col[5];
@@ -619,14 +620,22 @@ __device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD
   return ok;
 }
 
+template <class TA>
+__device__ __forceinline__ bool oee_factor(int m, int d, int n, TA *wa, int srcD, int srcU,
+                                           int srcR, int srcR2 = -1) {
+  return oee_factor_at<TA>(m, m + d < n, n, wa, srcD, srcU, srcR, srcR2);
+}
+
 // One OEE update of row i at distance d (Section IV, update rule and Algorithm 2,
 // right-hand sides all at level j-1):
 //   D_i -= E_i U_i^T + K_i U_{i-d},  R_i -= E_i R_{i+d} + K_i R_{i-d},
 //   U_i = -E_i U_{i+d},  E_i = U_i D_{i+d}^{-1},  K_i = U_{i-d}^T D_{i-d}^{-1}.
+// The rows it reads are given explicitly: inext / iprev are the rows row i is
+// coupled to below and above (-1: none), has_nn whether inext has a row below it.
 template <class TA>
-__device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int srcD, int srcU,
-                                        int srcR, TA *Dn, TA *Un, TA *Rn, int srcR2 = -1,
-                                        TA *Rn2 = nullptr) {
+__device__ __forceinline__ void oee_row_at(int i, int inext, bool has_nn, int iprev, int n,
+                                           const TA *wa, int srcD, int srcU, int srcR, TA *Dn,
+                                           TA *Un, TA *Rn, int srcR2 = -1, TA *Rn2 = nullptr) {
   const RowP<const TA> row = rowp(wa, n, i);
   const bool two = srcR2 >= 0;
 #pragma unroll
@@ -639,8 +648,8 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
   }
 #pragma unroll
   for (int k = 0; k < 25; ++k) Un[k] = TA(0);
-  if (i + d < n) {
-    const RowP<const TA> nb = rowp(wa, n, i + d);
+  if (inext >= 0) {
+    const RowP<const TA> nb = rowp(wa, n, inext);
     TA L[15], inv[5];
 #pragma unroll
     for (int k = 0; k < 15; ++k) L[k] = nb[A_L + k];
@@ -674,7 +683,7 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
 #pragma unroll
         for (int k = 0; k < 5; ++k) Rn2[r] -= Z[r][k] * gr[k];
     }
-    if (i + 2 * d < n) {
+    if (has_nn) {
 #pragma unroll
       for (int r = 0; r < 5; ++r)
 #pragma unroll
@@ -686,8 +695,8 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
         }
     }
   }
-  if (i - d >= 0) {
-    const RowP<const TA> pr = rowp(wa, n, i - d);
+  if (iprev >= 0) {
+    const RowP<const TA> pr = rowp(wa, n, iprev);
     TA G[5][5];
 #pragma unroll
     for (int k = 0; k < 5; ++k)
@@ -717,6 +726,14 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
   }
 }
 
+template <class TA>
+__device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int srcD, int srcU,
+                                        int srcR, TA *Dn, TA *Un, TA *Rn, int srcR2 = -1,
+                                        TA *Rn2 = nullptr) {
+  oee_row_at<TA>(i, i + d < n ? i + d : -1, i + 2 * d < n, i - d >= 0 ? i - d : -1, n, wa, srcD,
+                 srcU, srcR, Dn, Un, Rn, srcR2, Rn2);
+}
+
 // Block cyclic reduction of the symmetric block tri-diagonal system (the
 // work-efficient alternative to OEE): at level j (distance d = 2^{j-1}) the
 // active rows are i with (i + 1) % d == 0; those with (i + 1) / d odd are
@@ -725,31 +742,40 @@ __device__ __forceinline__ void oee_row(int i, int d, int n, const TA *wa, int s
 // row formulas. About n row updates in total instead of n ceil(log2 n). Back
 // substitution then solves the rows level by level from the last one down:
 // x_i = D_i^{-1} (R_i - U_{i-d}^T x_{i-d} - U_i x_{i+d}).
-template <class TA, int P>
-__device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, bool two) {
+//
+// cr_solve_map runs it on a system of N rows stored at rows row(0) < ... <
+// row(N-1) of a chain's n-row workspace: row(r)'s U0 couples it to row(r+1)
+// (the hybrid schedule's reduced system); cr_solve is the identity map.
+template <class TA, int P, class Map>
+__device__ __forceinline__ bool cr_solve_map(const Team<P> &tm, TA *wa, int n, int N,
+                                             const Map &row_of, bool two) {
   bool bad = false;
   int levels = 0;
-  while ((1 << levels) < n) ++levels;
+  while ((1 << levels) < N) ++levels;
   // the active rows of level j are i = (t + 1) d - 1, t = 0, 1, ...: lanes take t
   // round robin (t even: eliminated, t odd: kept)
   for (int j = 1; j <= levels; ++j) {
     const int d = 1 << (j - 1);
-    for (int t = 2 * tm.r; (t + 1) * d - 1 < n; t += 2 * P) {  // eliminated rows
+    for (int t = 2 * tm.r; (t + 1) * d - 1 < N; t += 2 * P) {  // eliminated rows
       const int m = (t + 1) * d - 1;
-      bad |= !oee_factor<TA>(m, d, n, wa, A_D0, A_U0, A_R0, two ? A_R20 : -1);
+      const int rm = row_of(m);
+      bad |= !oee_factor_at<TA>(rm, m + d < N, n, wa, A_D0, A_U0, A_R0, two ? A_R20 : -1);
       if (m - d >= 0) {  // keep the lower coupling for the back substitution
-        const RowP<TA> lo = rowp(wa, n, m - d) + A_U0;
-        const RowP<TA> row = rowp(wa, n, m);
+        const RowP<TA> lo = rowp(wa, n, row_of(m - d)) + A_U0;
+        const RowP<TA> row = rowp(wa, n, rm);
 #pragma unroll
         for (int k = 0; k < 25; ++k) row[A_LO + k] = lo[k];
       }
     }
     tm.sync();
-    for (int t = 2 * tm.r + 1; (t + 1) * d - 1 < n; t += 2 * P) {  // kept rows: update in place
+    for (int t = 2 * tm.r + 1; (t + 1) * d - 1 < N; t += 2 * P) {  // kept rows: update in place
       const int i = (t + 1) * d - 1;
+      const int ri = row_of(i);
       TA Dn[15], Un[25], Rn[5], Rn2[5];
-      oee_row<TA>(i, d, n, wa, A_D0, A_U0, A_R0, Dn, Un, Rn, two ? A_R20 : -1, Rn2);
-      const RowP<TA> row = rowp(wa, n, i);
+      oee_row_at<TA>(ri, i + d < N ? row_of(i + d) : -1, i + 2 * d < N,
+                     i - d >= 0 ? row_of(i - d) : -1, n, wa, A_D0, A_U0, A_R0, Dn, Un, Rn,
+                     two ? A_R20 : -1, Rn2);
+      const RowP<TA> row = rowp(wa, n, ri);
 #pragma unroll
       for (int k = 0; k < 15; ++k) row[A_D0 + k] = Dn[k];
 #pragma unroll
@@ -763,12 +789,12 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, bool 
     }
     tm.sync();
   }
-  // rows never eliminated (n a power of two: row n - 1) are decoupled by now;
+  // rows never eliminated (N a power of two: row N - 1) are decoupled by now;
   // a row is eliminated at level 1 + (trailing zeros of i + 1)
-  for (int i = tm.r; i < n; i += P) {
+  for (int i = tm.r; i < N; i += P) {
     const int je = __ffs(i + 1);
     if (je <= levels) continue;
-    const RowP<TA> row = rowp(wa, n, i);
+    const RowP<TA> row = rowp(wa, n, row_of(i));
     TA Dm[15], L[15], inv[5], r[5];
 #pragma unroll
     for (int k = 0; k < 15; ++k) Dm[k] = row[A_D0 + k];
@@ -791,9 +817,9 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, bool 
   tm.sync();
   for (int j = levels; j >= 1; --j) {
     const int d = 1 << (j - 1);
-    for (int t = 2 * tm.r; (t + 1) * d - 1 < n; t += 2 * P) {
+    for (int t = 2 * tm.r; (t + 1) * d - 1 < N; t += 2 * P) {
       const int i = (t + 1) * d - 1;
-      const RowP<TA> row = rowp(wa, n, i);
+      const RowP<TA> row = rowp(wa, n, row_of(i));
       TA L[15], inv[5];
 #pragma unroll
       for (int k = 0; k < 15; ++k) L[k] = row[A_L + k];
@@ -804,15 +830,15 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, bool 
         TA r[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) r[k] = row[fR + k];
-        if (i + d < n) {  // - U_i x_{i+d}
-          const RowP<TA> xn = rowp(wa, n, i + d) + fX;
+        if (i + d < N) {  // - U_i x_{i+d}
+          const RowP<TA> xn = rowp(wa, n, row_of(i + d)) + fX;
 #pragma unroll
           for (int rr = 0; rr < 5; ++rr)
 #pragma unroll
             for (int k = 0; k < 5; ++k) r[rr] -= row[A_U0 + 5 * rr + k] * xn[k];
         }
         if (i - d >= 0) {  // - U_{i-d}^T x_{i-d}
-          const RowP<TA> xp = rowp(wa, n, i - d) + fX;
+          const RowP<TA> xp = rowp(wa, n, row_of(i - d)) + fX;
 #pragma unroll
           for (int rr = 0; rr < 5; ++rr)
 #pragma unroll
@@ -829,8 +855,169 @@ __device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, bool 
   return bad;
 }
 
+struct IdentityRows {
+  __device__ __forceinline__ int operator()(int r) const { return r; }
+};
+
+template <class TA, int P>
+__device__ __forceinline__ bool cr_solve(const Team<P> &tm, TA *wa, int n, bool two) {
+  return cr_solve_map<TA, P>(tm, wa, n, n, IdentityRows{}, two);
+}
+
+// The hybrid partition / cyclic-reduction schedule of the block tri-diagonal
+// system (a work-efficient relative of OEE; Section IV discusses reductions of
+// this system). The n rows are cut into m = min(P, n / 2) contiguous segments,
+// one per lane; segment l = [s_l, e_l) keeps its first and last rows and its
+// lane eliminates the interior rows s_l + 1 .. e_l - 2 top down by block
+// Gaussian elimination: row k, coupled to the segment's first row a by F and to
+// row k + 1 by U_k, is factored (D_k = L L^T) and folded into both, D_a -= G1^T
+// G1, R_a -= G1^T g, D_{k+1} -= G2^T G2, R_{k+1} -= G2^T g, and the coupling of a
+// moves on to k + 1, F <- -G1^T G2 (G1 = L^{-1} F^T, G2 = L^{-1} U_k, g = L^{-1}
+// R_k): Schur complements of the SPD matrix, so every pivot stays SPD. The
+// kept rows form a block tri-diagonal system of 2m rows (a_l -- e_l - 1 coupled
+// by the final F, e_l - 1 -- a_{l+1} by the original U) that block cyclic
+// reduction solves across the lanes; each lane then back-substitutes its
+// interior bottom up, L^T x_k = g - G1 x_a - G2 x_{k+1}. Interior rows keep L,
+// 1 / diag L, g, G1 and G2 in their own fields (A_L, A_LI, A_GR, A_LO, A_G).
+template <class TA, int P>
+__device__ __forceinline__ bool hybrid_solve(const Team<P> &tm, TA *wa, int n, bool two) {
+  bool bad = false;
+  if (n <= 2) return cr_solve<TA, P>(tm, wa, n, two);
+  const int m = min(P, n / 2);
+  auto seg_start = [&](int l) { return static_cast<int>((static_cast<int64_t>(l) * n) / m); };
+  if (tm.r < m) {
+    const int a = seg_start(tm.r), e = seg_start(tm.r + 1);
+    const RowP<TA> ra = rowp(wa, n, a);
+    TA F[25];  // the coupling block (a, k) of the current frontier row k
+#pragma unroll
+    for (int k = 0; k < 25; ++k) F[k] = ra[A_U0 + k];
+    for (int k = a + 1; k <= e - 2; ++k) {
+      const RowP<TA> rk = rowp(wa, n, k);
+      TA Dm[15], L[15], inv[5];
+#pragma unroll
+      for (int q = 0; q < 15; ++q) Dm[q] = rk[A_D0 + q];
+      bad |= !chol5(Dm, L, inv);
+#pragma unroll
+      for (int q = 0; q < 15; ++q) rk[A_L + q] = L[q];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) rk[A_LI + q] = inv[q];
+      // G1 = L^{-1} F^T (column c of F^T is row c of F), G2 = L^{-1} U_k
+      TA G1[5][5], G2[5][5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        TA col[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) col[q] = F[5 * c + q];
+        fwd5(L, inv, col);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) G1[q][c] = col[q];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) col[q] = rk[A_U0 + 5 * q + c];
+        fwd5(L, inv, col);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) G2[q][c] = col[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          rk[A_LO + 5 * q + c] = G1[q][c];
+          rk[A_G + 5 * q + c] = G2[q][c];
+        }
+      const RowP<TA> rn = rowp(wa, n, k + 1);
+      for (int h = 0; h < (two ? 2 : 1); ++h) {
+        const int fR = h ? A_R20 : A_R0, fG = h ? A_GR2 : A_GR;
+        TA g[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) g[q] = rk[fR + q];
+        fwd5(L, inv, g);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) rk[fG + q] = g[q];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+          TA sa = ra[fR + r], sn = rn[fR + r];
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            sa -= G1[q][r] * g[q];
+            sn -= G2[q][r] * g[q];
+          }
+          ra[fR + r] = sa;
+          rn[fR + r] = sn;
+        }
+      }
+      // D_a -= G1^T G1, D_{k+1} -= G2^T G2 (lower triangles), F <- -G1^T G2
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) {
+          TA sa = ra[A_D0 + l5(r, c)], sn = rn[A_D0 + l5(r, c)];
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            sa -= G1[q][r] * G1[q][c];
+            sn -= G2[q][r] * G2[q][c];
+          }
+          ra[A_D0 + l5(r, c)] = sa;
+          rn[A_D0 + l5(r, c)] = sn;
+        }
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          TA t = TA(0);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) t -= G1[q][r] * G2[q][c];
+          F[5 * r + c] = t;
+        }
+    }
+    // the segment's first row now couples to its last row by F
+#pragma unroll
+    for (int k = 0; k < 25; ++k) ra[A_U0 + k] = F[k];
+  }
+  tm.sync();
+  // the reduced system: reduced row 2l is s_l, 2l + 1 is e_l - 1
+  auto row_of = [&](int r) { return (r & 1) ? seg_start((r >> 1) + 1) - 1 : seg_start(r >> 1); };
+  bad |= cr_solve_map<TA, P>(tm, wa, n, 2 * m, row_of, two);
+  if (tm.r < m) {
+    const int a = seg_start(tm.r), e = seg_start(tm.r + 1);
+    const RowP<TA> ra = rowp(wa, n, a);
+    for (int h = 0; h < (two ? 2 : 1); ++h) {
+      const int fX = h ? A_FC2 : A_FC, fG = h ? A_GR2 : A_GR;
+      TA xa[5], xn[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        xa[q] = ra[fX + q];
+        xn[q] = rowp(wa, n, e - 1)[fX + q];
+      }
+      for (int k = e - 2; k >= a + 1; --k) {
+        const RowP<TA> rk = rowp(wa, n, k);
+        TA L[15], inv[5], x[5];
+#pragma unroll
+        for (int q = 0; q < 15; ++q) L[q] = rk[A_L + q];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) inv[q] = rk[A_LI + q];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+          TA t = rk[fG + r];
+#pragma unroll
+          for (int q = 0; q < 5; ++q) t -= rk[A_LO + 5 * r + q] * xa[q] + rk[A_G + 5 * r + q] * xn[q];
+          x[r] = t;
+        }
+        bwd5(L, inv, x);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          rk[fX + q] = x[q];
+          xn[q] = x[q];
+        }
+      }
+    }
+  }
+  tm.sync();
+  return bad;
+}
+
 // Algorithm 1 for one problem; BTD selects SolvBTDSys: 0 = odd-even
-// elimination (Algorithm 2), 1 = block cyclic reduction. In MODE_FD2 a second
+// elimination (Algorithm 2), 1 = block cyclic reduction, 2 = the hybrid
+// partition / cyclic-reduction schedule. In MODE_FD2 a second
 // right-hand side (tau_delta := in4) rides along: the blocks D, U and their
 // elimination are shared, only R, F_c and CalcAcc are done twice.
 template <class T, class TA, int P, int BTD, bool TWO>
@@ -957,6 +1144,9 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
   if constexpr (BTD == 1) {
     // SolvBTDSys by block cyclic reduction
     bad |= cr_solve<TA, P>(tm, wa, n, two);
+  } else if constexpr (BTD == 2) {
+    // SolvBTDSys by the hybrid partition / cyclic-reduction schedule
+    bad |= hybrid_solve<TA, P>(tm, wa, n, two);
   } else {
   // SolvBTDSys: odd-even elimination, ceil(log2 n) levels (Algorithm 2)
   int levels = 0;
@@ -1091,6 +1281,12 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa2_kernel(
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_cr2_kernel(KArgs A) {
   cfa_body<T, TA, P, 1, true>(A, Range{0, 0, A.n_problems});
+}
+
+// the hybrid partition / cyclic-reduction schedule (one or two right-hand sides)
+template <class T, class TA, bool TWO, int P>
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_hy_kernel(KArgs A) {
+  cfa_body<T, TA, P, 2, TWO>(A, Range{0, 0, A.n_problems});
 }
 
 // ------------------------------------------------------------------ JSIIA

@@ -13,6 +13,7 @@ constexpr int BLOCK = 128;
 cudaError_t launch_id(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_cfa(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_cfa_cr(const KArgs &a, int prec, int team, cudaStream_t s);
+cudaError_t launch_cfa_hy(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_jsiia(const KArgs &a, int prec, int team, cudaStream_t s);
 // team 1: one thread per problem; 8, 16, 32: rows of the articulated inertia
 // spread over six lanes of the team.
@@ -25,6 +26,7 @@ cudaError_t launch_adjoint_rnea(const KArgs &a, int prec, int team, cudaStream_t
 cudaError_t launch_id_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
 cudaError_t launch_cfa_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
 cudaError_t launch_cfa_cr_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
+cudaError_t launch_cfa_hy_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
 cudaError_t launch_jsiia_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
 cudaError_t launch_abia_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s);
 cudaError_t launch_adjoint_rnea_multi(const KArgs &a, int prec, const ClassTable &ct,

@@ -57,6 +57,31 @@ cudaError_t launch_cfa_cr_multi_f64(const KArgs &a, const ClassTable &ct, cudaSt
 cudaError_t launch_cfa_cr_multi_f32(const KArgs &a, const ClassTable &ct, cudaStream_t s);
 cudaError_t launch_cfa_cr_multi_mixed(const KArgs &a, const ClassTable &ct, cudaStream_t s);
 
+cudaError_t launch_cfa_hy_f64(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa_hy_f32(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa_hy_mixed(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa_hy_multi_f64(const KArgs &a, const ClassTable &ct, cudaStream_t s);
+cudaError_t launch_cfa_hy_multi_f32(const KArgs &a, const ClassTable &ct, cudaStream_t s);
+cudaError_t launch_cfa_hy_multi_mixed(const KArgs &a, const ClassTable &ct, cudaStream_t s);
+
+cudaError_t launch_cfa_hy(const KArgs &a, int prec, int team, cudaStream_t s) {
+  switch (prec) {
+    case 0: return launch_cfa_hy_f64(a, team, s);
+    case 1: return launch_cfa_hy_f32(a, team, s);
+    case 2: return launch_cfa_hy_mixed(a, team, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_cfa_hy_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s) {
+  switch (prec) {
+    case 0: return launch_cfa_hy_multi_f64(a, ct, s);
+    case 1: return launch_cfa_hy_multi_f32(a, ct, s);
+    case 2: return launch_cfa_hy_multi_mixed(a, ct, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_cfa_multi(const KArgs &a, int prec, const ClassTable &ct, cudaStream_t s) {
   switch (prec) {
     case 0: return launch_cfa_multi_f64(a, ct, s);

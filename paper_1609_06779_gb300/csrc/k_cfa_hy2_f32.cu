@@ -1,0 +1,17 @@
+// CFA kernels with the hybrid partition / cyclic-reduction solve for T = float,
+// TA = float, two right-hand sides (MODE_FD2).
+#include "fd_kernels.cuh"
+#include "fd_launch.h"
+
+namespace fdk {
+
+cudaError_t launch_cfa_hy2_f32(const KArgs &a, int team, cudaStream_t s) {
+  const unsigned g = grid_for(a.n_problems, team);
+  switch (team) {
+    FDK_TEAM_CASES(cfa_hy_kernel, float, float, true)
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fdk

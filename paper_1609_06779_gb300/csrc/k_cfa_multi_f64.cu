@@ -1,17 +1,18 @@
 // cfa kernels over length classes (one launch, a team per class) for
-// T = double, TA = double (one translation unit per precision).
+// T = double, TA = double, one right-hand side (one translation unit per precision
+// and mode).
 #include "fd_kernels.cuh"
 #include "fd_launch.h"
 
 namespace fdk {
 
+cudaError_t launch_cfa2_multi_f64(const KArgs &a, const ClassTable &ct, cudaStream_t s);
+
 cudaError_t launch_cfa_multi_f64(const KArgs &a, const ClassTable &ct, cudaStream_t s) {
+  if (a.mode == MODE_FD2) return launch_cfa2_multi_f64(a, ct, s);
   const unsigned g = static_cast<unsigned>(ct.blk[ct.n]);
   if (g == 0) return cudaSuccess;
-  if (a.mode == MODE_FD2)
-    cfa_multi_kernel<double, double, 0, true><<<g, BLOCK, 0, s>>>(a, ct);
-  else
-    cfa_multi_kernel<double, double, 0, false><<<g, BLOCK, 0, s>>>(a, ct);
+  cfa_multi_kernel<double, double, 0, false><<<g, BLOCK, 0, s>>>(a, ct);
   return cudaGetLastError();
 }
 

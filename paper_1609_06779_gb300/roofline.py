@@ -116,8 +116,24 @@ def cfa_cr_flops(n: int) -> int:
     return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 78) + cr_flops(n) + n * 120
 
 
+def hybrid_flops(n: int) -> int:
+    """The hybrid partition / cyclic-reduction solve at the serial schedule (one
+    segment: every row but the first and the last is interior): per interior row
+    the Cholesky factor 60, G1 = L^{-1} F^T and G2 = L^{-1} U 250, g 25, the
+    updates of the first row and the next row (G1^T G1, G2^T G2 150 each, G1^T g,
+    G2^T g 50 each), the moved coupling F = -G1^T G2 250, and the back
+    substitution 125; the two kept rows by cyclic reduction."""
+    if n <= 2:
+        return cr_flops(n)
+    return (n - 2) * (60 + 250 + 25 + 300 + 100 + 250 + 125) + cr_flops(2)
+
+
+def cfa_hybrid_flops(n: int) -> int:
+    return id_flops(n) + n * (D_BLOCKS + U_BLOCK + 78) + hybrid_flops(n) + n * 120
+
+
 FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops,
-         "cfa_cr": cfa_cr_flops}
+         "cfa_cr": cfa_cr_flops, "cfa_hybrid": cfa_hybrid_flops}
 
 
 def flops(algo: str, lengths) -> int:

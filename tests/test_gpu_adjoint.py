@@ -42,7 +42,7 @@ def _oracle_vjp(model, st, w):
     return gq, gqd, gm
 
 
-@pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr"])
+@pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr", "cfa_hybrid"])
 @pytest.mark.parametrize("team", [1, 4, 8])
 def test_adjoint_matches_oracle_finite_differences(algo, team):
     if algo == "abia" and team == 4:

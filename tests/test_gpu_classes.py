@@ -34,7 +34,7 @@ def _setup(lengths, seed, dt=torch.float64):
     return fd, model, st, cs, b, t(st.q), t(st.qdot), t(st.tau)
 
 
-@pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr"])
+@pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr", "cfa_hybrid"])
 def test_class_split_fp64_parity_and_bitwise(algo):
     fd, model, st, cs, b, q, qd, tau = _setup(LENGTHS, 41)
     classes = fd.batch_classes(b, algo)
@@ -66,7 +66,7 @@ def test_class_split_float_paths(prec):
     fd, model, st, cs, b, q, qd, tau = _setup(LENGTHS, 43, torch.float32)
     ref = oracle.fd(model, st.q, st.qdot, st.tau)
     lens = np.diff(model.offsets)
-    for algo in ("abia", "jsiia", "cfa", "cfa_cr"):
+    for algo in ("abia", "jsiia", "cfa", "cfa_cr", "cfa_hybrid"):
         got = fd.solve(b, q, qd, tau, algo=algo, prec=prec, team=0).double().cpu().numpy()
         err = _rel_err(got, ref, model.offsets)
         short = lens[lens > 0] <= 8

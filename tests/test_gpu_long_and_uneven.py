@@ -45,9 +45,10 @@ def test_long_chains_fp64(n, count):
     floors = {a: _rel_err(oracle.fd(model, st.q, st.qdot, st.tau, algo=o, n_threads=8), ref,
                           model.offsets) for a, o in (("abia", "aba"), ("cfa", "cfa"))}
     floors["jsiia"] = floors["abia"]
-    floors["cfa_cr"] = floors["cfa"]
+    floors["cfa_cr"] = floors["cfa_hybrid"] = floors["cfa"]
     for algo, team in (("abia", 1), ("abia", 8), ("abia", 32), ("cfa", 32), ("cfa", 8), ("cfa", 256), ("jsiia", 32),
-                       ("jsiia", 128), ("cfa_cr", 1), ("cfa_cr", 32), ("cfa_cr", 256)):
+                       ("jsiia", 128), ("cfa_cr", 1), ("cfa_cr", 32), ("cfa_cr", 256),
+                       ("cfa_hybrid", 1), ("cfa_hybrid", 32), ("cfa_hybrid", 256)):
         got, status = _gpu(model, st, algo, "fp64", team)
         assert (status == 0).all(), (algo, team)
         err = _rel_err(got, ref, model.offsets)

@@ -55,7 +55,7 @@ def _run(model, st, algo, prec, team, chain_index=None):
 RAGGED = [1, 2, 3, 5, 7, 8, 13, 31, 32, 33, 47, 64, 100]
 
 
-@pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr"])
+@pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr", "cfa_hybrid"])
 @pytest.mark.parametrize("team", [1, 2, 4, 8, 16, 32, 64, 128, 256])
 def test_fd_fp64_ragged_parity(algo, team):
     if algo == "abia" and team not in (1, 8, 16, 32):
@@ -99,7 +99,7 @@ def _check_float_bars(err, cond, what):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
-@pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr"])
+@pytest.mark.parametrize("algo", ["abia", "jsiia", "cfa", "cfa_cr", "cfa_hybrid"])
 def test_fd_fp32_parity_short_chains(prec, algo):
     model = synth.random_chains([1, 2, 4, 7, 7, 7, 8] * 8, seed=11)
     st = synth.random_states(model.n_links_total, seed=12)
@@ -155,7 +155,7 @@ def test_nonfinite_input_flags_only_its_problem():
     bad.tau[off[2]] = np.inf
     bad.q[off[4] + 8] = np.nan
     clean = [0, 3]
-    for algo in ("abia", "jsiia", "cfa", "cfa_cr"):
+    for algo in ("abia", "jsiia", "cfa", "cfa_cr", "cfa_hybrid"):
         for prec, team in (("fp64", 1), ("fp64", 2), ("fp64", 8), ("mixed", 8), ("fp32", 1)):
             if algo == "abia" and team == 2:
                 continue
@@ -174,7 +174,8 @@ def test_all_algorithms_and_teams_agree():
     st = synth.random_states(model.n_links_total, seed=22)
     base, _ = _run(model, st, "cfa", "fp64", 32)
     for algo, team in (("cfa", 1), ("cfa", 4), ("jsiia", 1), ("jsiia", 32), ("abia", 1),
-                       ("abia", 8), ("abia", 32), ("cfa_cr", 1), ("cfa_cr", 8), ("cfa_cr", 32)):
+                       ("abia", 8), ("abia", 32), ("cfa_cr", 1), ("cfa_cr", 8), ("cfa_cr", 32),
+                       ("cfa_hybrid", 1), ("cfa_hybrid", 8), ("cfa_hybrid", 32)):
         got, _ = _run(model, st, algo, "fp64", team)
         assert _rel_err(got, base, model.offsets).max() < 1e-10, (algo, team)
 
@@ -217,7 +218,7 @@ def test_cuda_graph_replay_matches_eager():
     t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
     st0 = synth.random_states(model.n_links_total, seed=82)
     q, qd, tau = t(st0.q), t(st0.qdot), t(st0.tau)
-    for algo, team in (("abia", 8), ("jsiia", 8), ("cfa", 8), ("cfa_cr", 4)):
+    for algo, team in (("abia", 8), ("jsiia", 8), ("cfa", 8), ("cfa_cr", 4), ("cfa_hybrid", 8)):
         ws = fd.workspace(b, algo, "fp64", team, q.device)
         out = torch.empty_like(q)
         s = torch.cuda.Stream()
