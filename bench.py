@@ -372,7 +372,7 @@ def extra_configs(dev, keep=None):
     r1 = {}
     k1 = {"config": "1x7_links_1024_states_fp64", "model": m, "chain_index": ci,
           "state_offsets": so1, "st": st, "problems": None, "outs": {}}
-    for a in ALGOS + ("cfa_cr", "cfa_hybrid"):
+    for a in ALGOS + ("cfa_cr", "cfa_hybrid", "abia_scan"):
         team = fd.autotune(b, q, qd, tau, algo=a)
         ws = fd.workspace(b, a, "fp64", 0, dev)
         out = torch.empty_like(q)
@@ -403,7 +403,7 @@ def extra_configs(dev, keep=None):
         rl = {}
         kl = {"config": f"{count}x{n}_links_fp64", "model": m, "chain_index": None, "st": st,
               "problems": [0, 1] if n <= 256 else [0], "outs": {}}
-        for a in ALGOS + ("cfa_cr", "cfa_hybrid"):
+        for a in ALGOS + ("cfa_cr", "cfa_hybrid", "abia_scan"):
             # JSIIA is cubic in n: at 1 024 links one timed solve, no autotuning
             team = 128 if a == "jsiia" else fd.autotune(b, q, qd, tau, algo=a)
             ws = fd.workspace(b, a, "fp64", team, dev)

@@ -49,15 +49,23 @@ typedef enum fd_algo {
                     reduction instead of OEE: about n row updates instead of
                     n ceil(log2 n), the same result (not in the paper's
                     experiments; the reduction OEE is a variant of, Section IV) */
-  FD_CFA_HYBRID = 4 /* CFA with the hybrid partition / cyclic-reduction solve:
+  FD_CFA_HYBRID = 4, /* CFA with the hybrid partition / cyclic-reduction solve:
                        each lane eliminates the interior rows of its own run of
                        rows, block cyclic reduction solves the reduced system of
                        the runs' end rows across the lanes, each lane back-
                        substitutes its interior (not in the paper's experiments;
                        a partitioned form of the reductions of Section IV) */
+  FD_ABIA_SCAN = 5 /* ABIA with the articulated-inertia recursion as a parallel
+                      scan over the team's lanes (Section III holds the ABI
+                      recursion to be serial up to a constant factor; this is
+                      its associative form: the Riccati step on the constraint-
+                      space compliance composes as a Schur complement of an SPD
+                      block matrix). FP64 only, teams of 8 .. 256 lanes, no
+                      adjoint; every lane does about five times the serial work
+                      in n / team + log2 team steps */
 } fd_algo;
 
-#define FD_N_ALGOS 5
+#define FD_N_ALGOS 6
 
 typedef enum fd_prec {
   FD_FP64 = 0,  /* states and all arithmetic in double */

@@ -221,6 +221,13 @@ fd_status fdk_pack_chain(int64_t first, int64_t n, const double *joint_axes,
 fd_status fdk_fail(fd_status st, const char *msg) { return fail(st, "%s", msg); }
 
 int fdk_default_team(int32_t algo, int64_t n_problems, int32_t max_links) {
+  // the ABI scan: segments of about four links (its lanes do about five times the
+  // serial work, so longer segments pay only when the GPU is full)
+  if (algo == FD_ABIA_SCAN) {
+    int t = 8;
+    while (t < 256 && 4 * t < max_links) t *= 2;
+    return t;
+  }
   // ABIA: one thread per problem once a warp per FP64 unit (152 SMs x 4) is
   // busy with 32 problems each; below that, spread each step over a team of 8
   if (algo == FD_ABIA) return n_problems > 152 * 4 * 8 ? 1 : 8;
@@ -504,7 +511,7 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int /*team: no l
     w.a_bytes = L * fdk::NA_CFA * as;
   if (algo == FD_JSIIA)
     w.a_bytes = (L * fdk::NA_JSIIA + static_cast<size_t>(b->sum_sq) * fdk::NSQ_JSIIA) * as;
-  if (algo == FD_ABIA) w.a_bytes = L * fdk::NA_ABIA * as;
+  if (algo == FD_ABIA || algo == FD_ABIA_SCAN) w.a_bytes = L * fdk::NA_ABIA * as;
   w.a_bytes = align256(w.a_bytes);
   return w;
 }
@@ -513,6 +520,9 @@ bool valid_team(int t) { return fdk_valid_team(t); }
 
 // team 0 on a batch of several length classes: one launch split by class
 bool use_classes(const fd_batch_s *b, int32_t team) { return team == 0 && b->classes.size() > 1; }
+bool use_classes(const fd_batch_s *b, int32_t algo, int32_t team) {
+  return algo != FD_ABIA_SCAN && use_classes(b, team);
+}
 
 int class_team(const fd_batch_s *b, size_t c, int32_t algo, fd_prec prec) {
   if (algo >= 0) {
@@ -581,13 +591,16 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
   if (algo != -1 && algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR &&
-      algo != FD_CFA_HYBRID)
+      algo != FD_CFA_HYBRID && algo != FD_ABIA_SCAN)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, algo);
   if (team < 0 || (team > 0 && !valid_team(team)))
     return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 256", who, team);
   if (algo == FD_ABIA && team > 0 && !fdk::abia_team_ok(team))
     return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs teams of 1, 8, 16 or 32 lanes, not %d", who,
                 team);
+  if (algo == FD_ABIA_SCAN && (prec != FD_FP64 || (team > 0 && !fdk::abia_scan_team_ok(team))))
+    return fail(FD_ERR_UNSUPPORTED, "%s: the ABI scan runs in FP64 on teams of 8 .. 256 lanes",
+                who);
   if (b->n_problems == 0 || b->n_state_links == 0) return FD_OK;
   if (!q || !qd || !in3 || !out) return fail(FD_ERR_INVALID_ARG, "%s: NULL state array", who);
   const int t = resolve_team(b, algo, prec, team);
@@ -621,7 +634,7 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   cudaError_t e = cudaSetDevice(b->chain->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto s = static_cast<cudaStream_t>(stream);
-  if (only_class >= 0 || use_classes(b, team)) {
+  if (only_class >= 0 || use_classes(b, algo, team)) {
     std::vector<int> teams(b->classes.size());
     for (size_t c = 0; c < teams.size(); ++c)
       teams[c] = (only_class >= 0 && static_cast<int>(c) == only_class && team > 0)
@@ -633,6 +646,7 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   else if (algo == FD_CFA_CR) e = fdk::launch_cfa_cr(a, prec_k, t, s);
   else if (algo == FD_CFA_HYBRID) e = fdk::launch_cfa_hy(a, prec_k, t, s);
   else if (algo == FD_JSIIA) e = fdk::launch_jsiia(a, prec_k, t, s);
+  else if (algo == FD_ABIA_SCAN) e = fdk::launch_abia_scan(a, prec_k, t, s);
   else e = fdk::launch_abia(a, prec_k, t, s);
   cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, who);
@@ -674,7 +688,7 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
   const char *who = "fd_solve_adjoint";
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
   if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR &&
-      algo != FD_CFA_HYBRID)
+      algo != FD_CFA_HYBRID && algo != FD_ABIA_SCAN)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, static_cast<int>(algo));
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
@@ -683,6 +697,8 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
   if (algo == FD_ABIA && team > 0 && !fdk::abia_team_ok(team))
     return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs teams of 1, 8, 16 or 32 lanes, not %d", who,
                 team);
+  if (algo == FD_ABIA_SCAN)
+    return fail(FD_ERR_UNSUPPORTED, "%s: the ABI scan has no adjoint (use FD_ABIA)", who);
   if (mass_bar && !b->chain->rigid)
     return fail(FD_ERR_UNSUPPORTED,
                 "%s: mass gradients need rigid-body inertias (J = [[I - m c^c^, m c^], "
@@ -726,7 +742,7 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
   cudaError_t e = cudaSetDevice(b->chain->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto s = static_cast<cudaStream_t>(stream);
-  const bool split = use_classes(b, team);
+  const bool split = use_classes(b, algo, team);
   std::vector<int> fd_teams(b->classes.size()), sw_teams(b->classes.size());
   for (size_t c = 0; split && c < fd_teams.size(); ++c) {
     fd_teams[c] = class_team(b, c, algo, prec);
@@ -871,6 +887,10 @@ std::vector<int> team_candidates(fd_algo algo, int max_len, int cap_team) {
     // ABIA's lane teams spread each step's 6x6 update over 6 or 12 lanes, which
     // pays even for chains shorter than the team
     for (int t : {1, 8, 16, 32}) cand.push_back(t);
+  } else if (algo == FD_ABIA_SCAN) {
+    int cap = 8;
+    while (cap < max_len && cap < cap_team) cap *= 2;
+    for (int t = 8; t <= cap; t *= 2) cand.push_back(t);
   } else {
     int cap = 1;
     while (cap < max_len && cap < cap_team) cap *= 2;
@@ -888,8 +908,10 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
   const char *who = "fd_autotune";
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
   if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR &&
-      algo != FD_CFA_HYBRID)
+      algo != FD_CFA_HYBRID && algo != FD_ABIA_SCAN)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm", who);
+  if (algo == FD_ABIA_SCAN && prec != FD_FP64)
+    return fail(FD_ERR_UNSUPPORTED, "%s: the ABI scan runs in FP64", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision", who);
   if (b->n_problems == 0 || b->n_state_links == 0) {
@@ -903,7 +925,7 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
   const std::string gpu = gpu_name(b->device);
   auto s = static_cast<cudaStream_t>(stream);
   fd_status st = FD_OK;
-  const bool split = b->classes.size() > 1;
+  const bool split = b->classes.size() > 1 && algo != FD_ABIA_SCAN;
   // one length class (or the whole batch): its team from the cache, else timed
   auto tune = [&](int cls, int max_len, int64_t count, int len_class, int cap_team,
                   int *out) -> fd_status {
@@ -963,7 +985,9 @@ extern "C" fd_status fd_batch_classes(fd_batch_t b, int32_t algo, fd_prec prec, 
     if (min_len) min_len[c] = cl.min_len;
     if (max_len) max_len[c] = cl.max_len;
     if (count) count[c] = cl.count;
-    if (team) team[c] = split ? class_team(b, c, algo, prec) : resolve_team(b, algo, prec, 0);
+    if (team)
+      team[c] = (split && algo != FD_ABIA_SCAN) ? class_team(b, c, algo, prec)
+                                                 : resolve_team(b, algo, prec, 0);
   }
   return FD_OK;
 }

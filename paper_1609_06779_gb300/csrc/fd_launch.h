@@ -20,6 +20,9 @@ cudaError_t launch_jsiia(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_abia(const KArgs &a, int prec, int team, cudaStream_t s);
 inline bool abia_team_ok(int team) { return team == 1 || team == 8 || team == 16 || team == 32; }
 cudaError_t launch_adjoint_rnea(const KArgs &a, int prec, int team, cudaStream_t s);
+// ABIA with the articulated-inertia recursion as a scan: FP64 (prec 0), teams 8 .. 256.
+cudaError_t launch_abia_scan(const KArgs &a, int prec, int team, cudaStream_t s);
+inline bool abia_scan_team_ok(int team) { return team >= 8 && team <= 256; }
 
 // One launch over the length classes of `ct` (teams of 1 .. 128 lanes, one per
 // class; ABIA 1, 8, 16 or 32), grid ct.blk[ct.n] blocks of BLOCK threads.

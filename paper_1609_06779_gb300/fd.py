@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-ALGOS = {"abia": 0, "jsiia": 1, "cfa": 2, "cfa_cr": 3, "cfa_hybrid": 4}
+ALGOS = {"abia": 0, "jsiia": 1, "cfa": 2, "cfa_cr": 3, "cfa_hybrid": 4, "abia_scan": 5}
 PRECS = {"fp64": 0, "fp32": 1, "mixed": 2}
 STATUS = {0: "FD_OK", 1: "FD_ERR_INVALID_ARG", 2: "FD_ERR_NOT_SPD", 3: "FD_ERR_OOM",
           4: "FD_ERR_CUDA", 5: "FD_ERR_TIMEOUT", 6: "FD_ERR_NUMERIC", 7: "FD_ERR_BUSY",

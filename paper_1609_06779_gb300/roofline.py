@@ -133,7 +133,10 @@ def cfa_hybrid_flops(n: int) -> int:
 
 
 FLOPS = {"id": id_flops, "abia": abia_flops, "jsiia": jsiia_flops, "cfa": cfa_flops,
-         "cfa_cr": cfa_cr_flops, "cfa_hybrid": cfa_hybrid_flops}
+         "cfa_cr": cfa_cr_flops, "cfa_hybrid": cfa_hybrid_flops,
+         # the ABI scan computes the ABIA: its useful work is ABIA's serial count
+         # (the scan's compositions are the price of the depth, not work)
+         "abia_scan": abia_flops}
 
 
 def flops(algo: str, lengths) -> int:
