@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the context variants (CR, hybrid, ID, adjoint, FP32, mixed)")
+    ap.add_argument("--no-peak", action="store_true",
+                    help="do not measure the FP64 peak (report against the nominal 1.25 TFLOP/s)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     return ap.parse_args()
@@ -603,7 +607,8 @@ def main():
     torch.cuda.set_device(dev)
     from paper_1609_06779_gb300 import fd
 
-    measure_peak(fd, local)
+    if not args.no_peak:
+        measure_peak(fd, local)
 
     # weak scaling: every rank solves its own 65 536-chain batch (no data exchange)
     model = synth.random_chains([args.links] * args.chains, seed=rank)
@@ -690,7 +695,7 @@ def main():
 
     # CFA with block cyclic reduction in place of OEE (context; not part of the step)
     variants = {}
-    if rank == 0:
+    if rank == 0 and not args.no_variants:
         for var in ("cfa_cr", "cfa_hybrid"):
             tcr = forced.get(var) or fd.autotune(batch, q, qd, tau, algo=var, prec="fp64")
             wcr = fd.workspace(batch, var, "fp64", tcr, dev)
@@ -745,7 +750,7 @@ def main():
                                                "solves_per_s": 3 * args.chains / (ms * 1e-3),
                                                "results_equal_device_step": same3}
     # FP32 and mixed variants of each algorithm (context; not part of the step)
-    if rank == 0:
+    if rank == 0 and not args.no_variants:
         q32, qd32, tau32 = (x.float() for x in (q, qd, tau))
         for prec in ("fp32", "mixed"):
             for a in ALGOS:

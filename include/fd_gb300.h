@@ -212,11 +212,14 @@ fd_status fd_inverse_dynamics(fd_batch_t batch, const void *q, const void *qdot,
  * in workspace_bytes, one warm-up and two timed solves each with CUDA events on
  * `stream`, and records the fastest in the batch plan. For a batch of several
  * length classes it does the same per class (teams up to 128), each class
- * launched alone, and records one team per class; *best_team (may be NULL)
- * then receives 0. Later calls with team 0 use the recorded teams. Choices are
+ * launched alone, then refines the choice inside the whole launch (each class
+ * in turn, longest first, tries its other teams with the others fixed and
+ * keeps one that makes the whole launch at least 1% faster), and records one
+ * team per class; *best_team (may be NULL) then receives 0. Later calls with team 0 use the recorded teams. Choices are
  * also kept in a process-wide cache keyed by GPU, algorithm, precision, length
  * class and ceil(log2) of the problem count; a cached entry is used without
- * timing (fd_autotune_cache_load / _save persist it). Synchronises the stream.
+ * timing (fd_autotune_cache_load / _save persist it; refined choices are kept
+ * under a key of the whole batch's classes as well). Synchronises the stream.
  * Inputs as fd_solve_batch (qddot is overwritten).
  */
 fd_status fd_autotune(fd_batch_t batch, fd_algo algo, fd_prec prec, const void *q,

@@ -807,12 +807,16 @@ namespace {
 // Process-wide: the fastest team per (GPU, algorithm, precision, length class,
 // problem-count class), filled by fd_autotune and persisted as JSON by
 // fd_autotune_cache_save / _load, so a later process skips the timing.
+// mix: 0 for a class timed alone (or a one-class batch); for a class's team
+// refined inside its batch's whole launch, a hash of the batch's classes and
+// their problem-count classes (the choice depends on the company it keeps)
 struct TuneKey {
   std::string gpu;
   int algo, prec, len_class, count_class;
+  uint32_t mix;
   bool operator<(const TuneKey &o) const {
-    return std::tie(gpu, algo, prec, len_class, count_class) <
-           std::tie(o.gpu, o.algo, o.prec, o.len_class, o.count_class);
+    return std::tie(gpu, algo, prec, len_class, count_class, mix) <
+           std::tie(o.gpu, o.algo, o.prec, o.len_class, o.count_class, o.mix);
   }
 };
 struct TuneVal {
@@ -930,7 +934,7 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
   auto tune = [&](int cls, int max_len, int64_t count, int len_class, int cap_team,
                   int *out) -> fd_status {
     const TuneKey key{gpu, static_cast<int>(algo), static_cast<int>(prec), len_class,
-                      ceil_log2(count)};
+                      ceil_log2(count), 0u};
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune.find(key);
@@ -958,6 +962,81 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
       int best = 0;
       st = tune(static_cast<int>(c), cl.max_len, cl.count, cl.key, 128, &best);
       if (st == FD_OK) b->ctuned[(c * FD_N_ALGOS + static_cast<size_t>(algo)) * 3 + prec] = best;
+    }
+    // then refine inside the whole launch: a class's best team alone is not its
+    // best among the others (the longest class sets the launch's tail), so each
+    // class in turn, longest first, tries its other teams with the rest fixed
+    uint32_t mix = 2166136261u;  // FNV-1a over the classes' keys and count classes
+    for (const auto &cl : b->classes)
+      for (int v : {cl.key, ceil_log2(cl.count)}) mix = (mix ^ static_cast<uint32_t>(v)) * 16777619u;
+    mix |= 1u;
+    const size_t nc = b->classes.size();
+    auto slot = [&](size_t c) -> int & {
+      return b->ctuned[(c * FD_N_ALGOS + static_cast<size_t>(algo)) * 3 + prec];
+    };
+    bool cached = true;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      for (size_t c = 0; c < nc && cached; ++c) {
+        const auto &cl = b->classes[c];
+        auto it = g_tune.find(TuneKey{gpu, static_cast<int>(algo), static_cast<int>(prec), cl.key,
+                                      ceil_log2(cl.count), mix});
+        if (it == g_tune.end()) cached = false;
+      }
+      if (cached)
+        for (size_t c = 0; c < nc; ++c) {
+          const auto &cl = b->classes[c];
+          slot(c) = g_tune[TuneKey{gpu, static_cast<int>(algo), static_cast<int>(prec), cl.key,
+                                   ceil_log2(cl.count), mix}].team;
+        }
+    }
+    if (st == FD_OK && !cached) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      auto whole = [&](float *ms) -> fd_status {
+        fd_status r = launch_common(b, q, qdot, tau, qddot, algo, prec, 0, workspace,
+                                    workspace_bytes, nullptr, s, who);
+        if (r != FD_OK) return r;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 2 && r == FD_OK; ++k)
+          r = launch_common(b, q, qdot, tau, qddot, algo, prec, 0, workspace, workspace_bytes,
+                            nullptr, s, who);
+        cudaEventRecord(e1, s);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        cudaEventElapsedTime(ms, e0, e1);
+        *ms /= 2;
+        return r;
+      };
+      float best_ms = 0.f;
+      st = whole(&best_ms);
+      for (size_t c = 0; c < nc && st == FD_OK; ++c) {
+        const int keep = slot(c);
+        int best_t = keep;
+        for (int t : team_candidates(algo, b->classes[c].max_len, 128)) {
+          if (t == keep) continue;
+          slot(c) = t;
+          float ms = 0.f;
+          st = whole(&ms);
+          if (st != FD_OK) break;
+          if (ms < 0.99f * best_ms) {
+            best_ms = ms;
+            best_t = t;
+          }
+        }
+        slot(c) = best_t;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (st == FD_OK) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (size_t c = 0; c < nc; ++c) {
+          const auto &cl = b->classes[c];
+          g_tune[TuneKey{gpu, static_cast<int>(algo), static_cast<int>(prec), cl.key,
+                         ceil_log2(cl.count), mix}] = TuneVal{slot(c), best_ms};
+        }
+      }
     }
     if (st == FD_OK && best_team) *best_team = 0;
   } else {
@@ -1011,9 +1090,10 @@ extern "C" fd_status fd_autotune_cache_save(const char *path) {
       char buf[512];
       snprintf(buf, sizeof buf,
                "%s\n  {\"gpu\": \"%s\", \"algo\": %d, \"prec\": %d, \"len_class\": %d, "
-               "\"count_class\": %d, \"team\": %d, \"ms\": %.6g}",
+               "\"count_class\": %d, \"mix\": %u, \"team\": %d, \"ms\": %.6g}",
                first ? "" : ",", g.c_str(), kv.first.algo, kv.first.prec, kv.first.len_class,
-               kv.first.count_class, kv.second.team, static_cast<double>(kv.second.ms));
+               kv.first.count_class, kv.first.mix, kv.second.team,
+               static_cast<double>(kv.second.ms));
       js += buf;
       first = false;
     }
@@ -1079,7 +1159,11 @@ extern "C" fd_status fd_autotune_cache_load(const char *path, int32_t *n_loaded)
         algo < 0 || algo >= FD_N_ALGOS || prec < 0 || prec > FD_MIXED || !fdk_valid_team(team) ||
         (algo == FD_ABIA && !fdk::abia_team_ok(static_cast<int>(team))))
       return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_load: bad entry in %s", path);
-    add[TuneKey{gpu, int(algo), int(prec), int(lc), int(cc)}] = TuneVal{int(team), 0.f};
+    long mixv = 0;
+    if (obj.find("\"mix\"") != std::string::npos && !field(obj, "mix", nullptr, &mixv))
+      return fail(FD_ERR_INVALID_ARG, "fd_autotune_cache_load: bad entry in %s", path);
+    add[TuneKey{gpu, int(algo), int(prec), int(lc), int(cc), static_cast<uint32_t>(mixv)}] =
+        TuneVal{int(team), 0.f};
     ++n;
     pos = z + 1;
   }
