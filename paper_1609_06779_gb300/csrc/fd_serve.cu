@@ -145,6 +145,17 @@ int team_for(TeamKind k, int n) {
   if (k == kTeamCFA) return n <= 32 ? 8 : (n <= 64 ? 32 : (n <= 128 ? 64 : 128));
   return n <= 32 ? 8 : (n <= 64 ? 16 : (n <= 128 ? 32 : 64));
 }
+// ABIA rollouts of chains over 64 links run the ABI recursion as a scan
+// (FD_ABIA_SCAN) on 64 lanes (one to four links per lane up to 256 links), so a
+// step's depth is a few links plus log2 64 instead of the whole chain. About 150
+// such rollouts are in flight at 20 000 requests/s, so the class is not purely
+// latency-bound: 64 lanes measured a little faster than the serial recursion on
+// twelve lanes (tick 0.97 -> 0.96 ms), 128 lanes slower (1.21 ms: the scan's
+// fivefold work). One team for the whole class keeps a request's arithmetic
+// independent of the mix.
+constexpr int kScanAbove = 64;
+constexpr int kScanTeam = 64;
+
 // Rollouts by length class, by algorithm and chain length only. A tick lasts
 // about as long as its longest chains' serial recursions (an ABIA step costs a
 // few microseconds per link on its critical lane), so the rollouts of a shorter
@@ -487,7 +498,8 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
   if (e == cudaSuccess) e = cudaEventRecord(S->ev_fork, S->stream);
   for (int k = 0; k < fd_server_s::kAux && e == cudaSuccess; ++k)
     e = cudaStreamWaitEvent(S->aux[k], S->ev_fork, 0);
-  auto fd_range = [&](int algo, int mode, int s, int c, int t, cudaStream_t st) {
+  auto fd_range = [&](int algo, int mode, int s, int c, int t, cudaStream_t st,
+                      bool scan = false) {
     fdk::KArgs a = base_args(S);
     a.prob_chain = S->d_prob + s;
     a.state_off = S->d_soff + s;
@@ -503,6 +515,7 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
     a.team = t;
     a.ws_a = algo == FD_CFA ? S->A.ws_c : S->A.ws_b;
     if (algo == FD_CFA) return fdk::launch_cfa(a, 0, t, st);
+    if (scan) return fdk::launch_abia_scan(a, 0, t, st);
     return fdk::launch_abia(a, 0, t, st);
   };
   auto fd_launch = [&](int algo, int mode, int p0, int cnt) {
@@ -523,13 +536,14 @@ fd_status tick(fd_server_s *S, std::unique_lock<std::mutex> &lk) {
       while (e2 < p0 + cnt &&
              (per_size ? all[e2]->n == all[s]->n : roll_class(algo, all[e2]->n) == rc))
         ++e2;
-      const int c = e2 - s, t = team_for(k, all[s]->n);
+      const bool scan = algo == FD_ABIA && all[s]->n > kScanAbove;
+      const int c = e2 - s, t = scan ? kScanTeam : team_for(k, all[s]->n);
       cudaStream_t st = S->aux[roll_aux(algo, all[s]->n)];
       for (int j = 0; j < all[s]->adv; ++j) {
         int cj = 0;
         while (cj < c && all[s + cj]->adv > j) ++cj;
         S->launches += 2;
-        cudaError_t err = fd_range(algo, fdk::MODE_FD, s, cj, t, st);
+        cudaError_t err = fd_range(algo, fdk::MODE_FD, s, cj, t, st, scan);
         if (err != cudaSuccess) return err;
         rollout_step_kernel<<<(cj + 3) / 4, 128, 0, st>>>(S->d_prob + s, S->d_moff,
                                                           S->d_soff + s, cj, S->A);
