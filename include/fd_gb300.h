@@ -60,9 +60,9 @@ typedef enum fd_algo {
                       recursion to be serial up to a constant factor; this is
                       its associative form: the Riccati step on the constraint-
                       space compliance composes as a Schur complement of an SPD
-                      block matrix). FP64 only, teams of 8 .. 256 lanes, no
-                      adjoint; every lane does about five times the serial work
-                      in n / team + log2 team steps */
+                      block matrix). FP64 only, teams of 8 .. 256 lanes (no
+                      split by length class); every lane does about five times
+                      the serial work in n / team + log2 team steps */
 } fd_algo;
 
 #define FD_N_ALGOS 6

@@ -697,8 +697,9 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
   if (algo == FD_ABIA && team > 0 && !fdk::abia_team_ok(team))
     return fail(FD_ERR_UNSUPPORTED, "%s: ABIA runs teams of 1, 8, 16 or 32 lanes, not %d", who,
                 team);
-  if (algo == FD_ABIA_SCAN)
-    return fail(FD_ERR_UNSUPPORTED, "%s: the ABI scan has no adjoint (use FD_ABIA)", who);
+  if (algo == FD_ABIA_SCAN && (prec != FD_FP64 || (team > 0 && !fdk::abia_scan_team_ok(team))))
+    return fail(FD_ERR_UNSUPPORTED, "%s: the ABI scan runs in FP64 on teams of 8 .. 256 lanes",
+                who);
   if (mass_bar && !b->chain->rigid)
     return fail(FD_ERR_UNSUPPORTED,
                 "%s: mass gradients need rigid-body inertias (J = [[I - m c^c^, m c^], "
@@ -754,6 +755,7 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
     if (algo == FD_CFA_CR) return fdk::launch_cfa_cr(k, prec_k, t, s);
     if (algo == FD_CFA_HYBRID) return fdk::launch_cfa_hy(k, prec_k, t, s);
     if (algo == FD_JSIIA) return fdk::launch_jsiia(k, prec_k, t, s);
+    if (algo == FD_ABIA_SCAN) return fdk::launch_abia_scan(k, prec_k, t, s);
     return fdk::launch_abia(k, prec_k, t, s);
   };
   // 1-2. lambda = M^{-1} qdd_bar with the algorithm's own factorisation: tau_bar;
@@ -787,7 +789,8 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
     // the reverse sweep: component lanes (team 8) for chains of up to 64 links,
     // else the algorithm's team (ABIA's serial team 1 would scan nothing)
     const int tr = b->max_links <= 64 ? std::max(t, 8) > 32 ? 32 : std::max(t, 8)
-                   : (algo == FD_ABIA ? resolve_team(b, FD_CFA, prec, 0) : t);
+                   : ((algo == FD_ABIA || algo == FD_ABIA_SCAN) ? resolve_team(b, FD_CFA, prec, 0)
+                                                                : t);
     r.team = tr;
     e = split ? fdk::launch_adjoint_rnea_multi(r, prec == FD_FP64 ? 0 : 1,
                                                class_table(b, sw_teams), s)

@@ -170,9 +170,11 @@ __device__ __forceinline__ void ric_link(const Prob<double> &pb, int i, RicMap &
   }
 }
 
-// An affine map x -> M x + v of 6-vectors (M row-major); id: the identity.
+// An affine map x -> M x + v of 6-vectors (M row-major), with a second
+// translation v2 for a second right-hand side y -> M y + v2 (MODE_FD2: the
+// adjoint's M^{-1} w beside FD; the matrices are the same); id: the identity.
 struct AffMap {
-  double M[36], v[6];
+  double M[36], v[6], v2[6];
   bool id;
 };
 
@@ -181,7 +183,9 @@ __device__ __forceinline__ void aff_store(double *s, const AffMap &a) {
   for (int k = 0; k < 36; ++k) s[k] = a.M[k];
 #pragma unroll
   for (int k = 0; k < 6; ++k) s[36 + k] = a.v[k];
-  s[42] = a.id ? 1.0 : 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) s[42 + k] = a.v2[k];
+  s[48] = a.id ? 1.0 : 0.0;
 }
 
 __device__ __forceinline__ void aff_load(const double *s, AffMap &a) {
@@ -189,23 +193,33 @@ __device__ __forceinline__ void aff_load(const double *s, AffMap &a) {
   for (int k = 0; k < 36; ++k) a.M[k] = s[k];
 #pragma unroll
   for (int k = 0; k < 6; ++k) a.v[k] = s[36 + k];
-  a.id = s[42] != 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) a.v2[k] = s[42 + k];
+  a.id = s[48] != 0.0;
 }
 
-// a1 <- a1 o a2 (a2 applied first): (M1 M2, M1 v2 + v1)
+// a1 <- a1 o a2 (a2 applied first): (M1 M2, M1 v_2 + v_1), the second
+// translations alike when TWO
+template <bool TWO>
 __device__ __forceinline__ void aff_compose(AffMap &a1, const AffMap &a2) {
   if (a2.id) return;
   if (a1.id) {
     a1 = a2;
     return;
   }
-  double M[36], v[6];
+  double M[36], v[6], w[6];
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
     double s = a1.v[r];
 #pragma unroll
     for (int k = 0; k < 6; ++k) s += a1.M[6 * r + k] * a2.v[k];
     v[r] = s;
+    if (TWO) {
+      double t = a1.v2[r];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) t += a1.M[6 * r + k] * a2.v2[k];
+      w[r] = t;
+    }
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       double t = 0.0;
@@ -218,14 +232,19 @@ __device__ __forceinline__ void aff_compose(AffMap &a1, const AffMap &a2) {
   for (int k = 0; k < 36; ++k) a1.M[k] = M[k];
 #pragma unroll
   for (int k = 0; k < 6; ++k) a1.v[k] = v[k];
+  if (TWO) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a1.v2[k] = w[k];
+  }
 }
 
-__device__ __forceinline__ void aff_apply(const AffMap &a, double *x) {
+// x <- M x + v (second = false) or M x + v2 (second = true)
+__device__ __forceinline__ void aff_apply(const AffMap &a, double *x, bool second = false) {
   if (a.id) return;
   double y[6];
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
-    double s = a.v[r];
+    double s = second ? a.v2[r] : a.v[r];
 #pragma unroll
     for (int k = 0; k < 6; ++k) s += a.M[6 * r + k] * x[k];
     y[r] = s;
@@ -262,7 +281,10 @@ __device__ __forceinline__ bool team_scan_maps(const Team<P> &tm, double *slot, 
   return ok;
 }
 
-template <int P>
+// TWO (MODE_FD2): a second right-hand side in4 shares the articulated inertias;
+// its bias forces and accelerations ride in the affine maps' second translation
+// and give M^{-1} in4 in out4 (the adjoint's linear solve beside FD).
+template <int P, bool TWO>
 __device__ __forceinline__ void abia_scan_body(const KArgs &A, const Range &rg, double *smem) {
   Team<P> tm;
   Prob<double> pb;
@@ -271,6 +293,8 @@ __device__ __forceinline__ void abia_scan_body(const KArgs &A, const Range &rg, 
   double *slot = smem + static_cast<int64_t>(threadIdx.x) * SCAN_SLOT;
   double *wa = static_cast<double *>(A.ws_a) + A.state_off[pb.p] * NA_ABIA;
   bool bad = false;
+  const double *td2 = TWO ? static_cast<const double *>(A.in4) + A.state_off[pb.p] : nullptr;
+  double *out2 = TWO ? static_cast<double *>(A.out4) + A.state_off[pb.p] : nullptr;
 
   // tau_delta = tau - ID(q, qd, 0) (Algorithm 1's bias torque) and the joint transforms
   id_team<double, P>(tm, pb, A.grav, A.mode);
@@ -339,7 +363,7 @@ __device__ __forceinline__ void abia_scan_body(const KArgs &A, const Range &rg, 
 #pragma unroll
       for (int k = 0; k < 36; ++k) m.M[k] = 0.0;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) m.v[k] = 0.0;
+      for (int k = 0; k < 6; ++k) m.v[k] = m.v2[k] = 0.0;
       return;
     }
     SE3<double> gn;
@@ -362,26 +386,36 @@ __device__ __forceinline__ void abia_scan_body(const KArgs &A, const Range &rg, 
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) m.v[k] = xh[k] * (td * Dinv);
+    if (TWO) {
+      const double t2 = td2[i + 1];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) m.v2[k] = xh[k] * (t2 * Dinv);
+    }
   };
   AffMap sa;
   sa.id = true;
   for (int i = a; i < b; ++i) {
     AffMap m;
     bias_map(i, m);
-    aff_compose(sa, m);
+    aff_compose<TWO>(sa, m);
   }
   team_scan_maps<P, true>(
       tm, slot, sa, [](double *s, const AffMap &m) { aff_store(s, m); },
       [](const double *s, AffMap &m) { aff_load(s, m); },
-      [](AffMap &x, const AffMap &y) { aff_compose(x, y); return true; });
-  double p[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      [](AffMap &x, const AffMap &y) { aff_compose<TWO>(x, y); return true; });
+  double p[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, p2[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   aff_apply(sa, p);
+  if (TWO) aff_apply(sa, p2, true);
   for (int i = b - 1; i >= a; --i) {
     AffMap m;
     bias_map(i, m);
     aff_apply(m, p);  // p_i
     double *ra = wa + static_cast<int64_t>(i) * NA_ABIA;
     ra[A_UU] = (pb.wt[static_cast<int64_t>(i) * NT + W_TD] - p[0]) * ra[A_DD];  // u_i / D_i
+    if (TWO) {
+      aff_apply(m, p2, true);
+      ra[A_UU2] = (td2[i] - p2[0]) * ra[A_DD];
+    }
   }
   tm.sync();
 
@@ -408,21 +442,26 @@ __device__ __forceinline__ void abia_scan_body(const KArgs &A, const Range &rg, 
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) m.v[k] = k == 0 ? ri[A_UU] : 0.0;
+    if (TWO) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) m.v2[k] = k == 0 ? ri[A_UU2] : 0.0;
+    }
   };
   AffMap fa;
   fa.id = true;
   for (int i = a; i < b; ++i) {  // fa = map_{b-1} o ... o map_a
     AffMap m;
     acc_map(i, m);
-    aff_compose(m, fa);
+    aff_compose<TWO>(m, fa);
     fa = m;
   }
   team_scan_maps<P, false>(
       tm, slot, fa, [](double *s, const AffMap &m) { aff_store(s, m); },
       [](const double *s, AffMap &m) { aff_load(s, m); },
-      [](AffMap &x, const AffMap &y) { aff_compose(x, y); return true; });
-  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      [](AffMap &x, const AffMap &y) { aff_compose<TWO>(x, y); return true; });
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, acc2[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   aff_apply(fa, acc);
+  if (TWO) aff_apply(fa, acc2, true);
   for (int i = a; i < b; ++i) {
     const double *ri = wa + static_cast<int64_t>(i) * NA_ABIA;
     SE3<double> g;
@@ -438,15 +477,27 @@ __device__ __forceinline__ void abia_scan_body(const KArgs &A, const Range &rg, 
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[k] = ap[k];
     acc[0] += qdd;
+    if (TWO) {
+      adinv(g, acc2, ap);
+      double s2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s2 += ri[A_H + k] * ap[k];
+      const double x = ri[A_UU2] - s2 * ri[A_DD];
+      out2[i] = x;
+      if (!finite_t(x)) bad = true;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc2[k] = ap[k];
+      acc2[0] += x;
+    }
   }
   const bool any_bad = tm.any(bad);
   if (tm.r == 0) set_status(A.status, pb.p, any_bad ? 2 : 0);
 }
 
-template <int P>
+template <int P, bool TWO>
 __global__ void __launch_bounds__(block_for<P>()) abia_scan_kernel(KArgs A) {
   extern __shared__ __align__(16) double scan_smem[];
-  abia_scan_body<P>(A, Range{0, 0, A.n_problems}, scan_smem);
+  abia_scan_body<P, TWO>(A, Range{0, 0, A.n_problems}, scan_smem);
 }
 
 }  // namespace fdk

@@ -4,16 +4,21 @@
 
 namespace fdk {
 
-template <int P>
-static cudaError_t go(const KArgs &a, cudaStream_t s) {
+template <int P, bool TWO>
+static cudaError_t go2(const KArgs &a, cudaStream_t s) {
   const unsigned g = grid_for(a.n_problems, P);
   const size_t smem = static_cast<size_t>(block_for<P>()) * SCAN_SLOT * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(abia_scan_kernel<P>,
+  cudaError_t e = cudaFuncSetAttribute(abia_scan_kernel<P, TWO>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  abia_scan_kernel<P><<<g, block_for<P>(), smem, s>>>(a);
+  abia_scan_kernel<P, TWO><<<g, block_for<P>(), smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t go(const KArgs &a, cudaStream_t s) {
+  return a.mode == MODE_FD2 ? go2<P, true>(a, s) : go2<P, false>(a, s);
 }
 
 cudaError_t launch_abia_scan(const KArgs &a, int prec, int team, cudaStream_t s) {

@@ -76,7 +76,31 @@ def test_abia_scan_unsupported_options():
         _solve(model, st, 4)       # teams of 8 .. 256
     cs = fd.ChainSet(model)
     b = fd.Batch(cs)
-    x = torch.zeros(17, dtype=torch.float64, device="cuda")
+    x = torch.zeros(17, dtype=torch.float32, device="cuda")
     with pytest.raises(fd.FDError) as e:
-        fd.adjoint(b, x, x, x, x, algo="abia_scan")
+        fd.adjoint(b, x, x, x, x, algo="abia_scan", prec="fp32")
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("team", [8, 64])
+def test_abia_scan_adjoint_matches_abia(team):
+    """The adjoint with the scan's shared elimination (FD and M^-1 w in one pass,
+    MODE_FD2) equals ABIA's within the FP64 bars (tau_bar = M^-1 w a plain solve;
+    q_bar, qdot_bar the adjoint's 1e-6 bar against central differences)."""
+    from paper_1609_06779_gb300 import fd
+    model = synth.random_chains([1, 5, 12, 33, 64, 100], seed=71)
+    st = synth.random_states(model.n_links_total, seed=72)
+    cs = fd.ChainSet(model)
+    b = fd.Batch(cs)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    w = torch.randn(model.n_links_total, dtype=torch.float64, device="cuda")
+    q, qd, tau = t(st.q), t(st.qdot), t(st.tau)
+    got = fd.adjoint(b, q, qd, tau, w, algo="abia_scan", team=team)
+    ref = fd.adjoint(b, q, qd, tau, w, algo="abia", team=8)
+    for x, y, tol in zip(got, ref, (1e-6, 1e-6, 1e-9, 1e-6)):
+        err = _rel_err(x.cpu().numpy(), y.cpu().numpy(), model.offsets)
+        assert err.max() < tol, (team, err.max())
+    # and the forward result of the shared pass equals the plain solve's
+    qdd_scan = fd.solve(b, q, qd, tau, algo="abia_scan", team=team).cpu().numpy()
+    qdd = fd.solve(b, q, qd, tau, algo="abia").cpu().numpy()
+    assert _rel_err(qdd_scan, qdd, model.offsets).max() < 1e-10
