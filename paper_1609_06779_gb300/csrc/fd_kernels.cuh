@@ -1032,14 +1032,28 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
   const T *td2 = two ? static_cast<const T *>(A.in4) + A.state_off[pb.p] : nullptr;
   T *out2 = two ? static_cast<T *>(A.out4) + A.state_off[pb.p] : nullptr;
 
-  // Single precision only: one refinement step. Algorithm 2 finishes every row
-  // with a full Schur complement of A, which in FP32 cancels down to about
-  // cond(A) eps32 relative accuracy; a second pass solves M d = tau - ID(q, qd,
-  // qdd) with the same algorithm (a Newton step on the inverse dynamics, Eq. 2,
-  // whose residual is exact to the inverse dynamics' own rounding) and adds d.
+  // Single precision only: refinement. Algorithm 2 finishes every row with a
+  // full Schur complement of A, which in FP32 cancels down to about cond(A)
+  // eps32 relative accuracy; a second pass solves M d = tau - ID(q, qd, qdd)
+  // with the same algorithm (a Newton step on the inverse dynamics, Eq. 2, whose
+  // residual is exact to the inverse dynamics' own rounding) and adds d. Each
+  // step shrinks the error by about the solve's own relative accuracy, so a
+  // problem whose first correction exceeds 1% of its solution (its first solve
+  // was that far off) takes a third pass.
   constexpr bool refine = std::is_same<T, float>::value && std::is_same<TA, float>::value && !TWO;
-  const int passes = (refine && A.mode == MODE_FD) ? 2 : 1;
+  const int passes = (refine && A.mode == MODE_FD) ? 3 : 1;
+  T corr = T(0), qmax = T(0);  // this lane's largest correction and |qdd| of the last pass
   for (int pass = 0; pass < passes; ++pass) {
+  if (pass == 2) {
+    T qm = qmax;
+    if constexpr (P > 1 && P <= 32) {  // the team's largest |qdd| (lanes of larger teams use their own)
+#pragma unroll
+      for (int o = 1; o < P; o *= 2) qm = fmax(qm, __shfl_xor_sync(tm.mask, qm, o, P));
+    }
+    if (!tm.any(corr > T(1e-2) * qm)) break;
+  }
+  corr = T(0);
+  qmax = T(0);
   // bias torque and tau_delta (Algorithm 1: CalcInvDyn, CalcDiffTorques); on the
   // refinement pass the residual tau - ID(q, qd, qdd) of the first pass's qdd
   id_team<T, P>(tm, pb, A.grav, pass ? MODE_RES : A.mode);
@@ -1245,6 +1259,10 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
     const T q2 = pass ? T(TA(pb.out[i]) + qdd) : T(qdd);
     pb.out[i] = q2;
     if (!finite_t(q2)) bad = true;
+    if (passes > 1) {
+      qmax = fmax(qmax, fabs(q2));
+      if (pass) corr = fmax(corr, T(fabs(qdd)));
+    }
     if (two) {
       const RowP<TA> row = rowp(wa, n, i);
       TA x = row[A_Z2];
