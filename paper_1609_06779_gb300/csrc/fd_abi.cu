@@ -519,7 +519,11 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int /*team: no l
 bool valid_team(int t) { return fdk_valid_team(t); }
 
 // team 0 on a batch of several length classes: one launch split by class
-bool use_classes(const fd_batch_s *b, int32_t team) { return team == 0 && b->classes.size() > 1; }
+// (at most fdk::MAX_CLASSES classes fit a launch's table; chains of up to 2^20
+// links give 21)
+bool use_classes(const fd_batch_s *b, int32_t team) {
+  return team == 0 && b->classes.size() > 1 && b->classes.size() <= fdk::MAX_CLASSES;
+}
 bool use_classes(const fd_batch_s *b, int32_t algo, int32_t team) {
   return algo != FD_ABIA_SCAN && use_classes(b, team);
 }
@@ -932,7 +936,7 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
   const std::string gpu = gpu_name(b->device);
   auto s = static_cast<cudaStream_t>(stream);
   fd_status st = FD_OK;
-  const bool split = b->classes.size() > 1 && algo != FD_ABIA_SCAN;
+  const bool split = algo != FD_ABIA_SCAN && use_classes(b, 0);
   // one length class (or the whole batch): its team from the cache, else timed
   auto tune = [&](int cls, int max_len, int64_t count, int len_class, int cap_team,
                   int *out) -> fd_status {
@@ -1061,7 +1065,7 @@ extern "C" fd_status fd_batch_classes(fd_batch_t b, int32_t algo, fd_prec prec, 
   if (algo < -1 || algo >= FD_N_ALGOS || prec < FD_FP64 || prec > FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "fd_batch_classes: bad algorithm or precision");
   *n_classes = static_cast<int32_t>(b->classes.size());
-  const bool split = b->classes.size() > 1;
+  const bool split = use_classes(b, 0);
   for (size_t c = 0; c < b->classes.size() && static_cast<int32_t>(c) < max; ++c) {
     const auto &cl = b->classes[c];
     if (min_len) min_len[c] = cl.min_len;
