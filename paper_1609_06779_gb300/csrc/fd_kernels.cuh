@@ -1309,6 +1309,16 @@ __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_hy_kerne
 
 // ------------------------------------------------------------------ JSIIA
 
+// Rows of one lane blocked together in the entries of M and in the Cholesky's
+// trailing updates (a shared operand loaded once serves them all), for teams of
+// up to four lanes, whose lanes hold many rows. Measured: 65 536 x 32 at team 2,
+// one row 4.17 ms, two 3.86-3.90, four 3.95 (register pressure); 256 x 256 at
+// team 128 two rows took 4.35 to 5.00 ms, so larger teams keep one.
+template <int P>
+__host__ __device__ constexpr int jsiia_rows_blocked() {
+  return P <= 4 ? 2 : 1;
+}
+
 // Ad_{g^{-1}}^T P Ad_{g^{-1}} of a packed symmetric 6x6 P, added to Out.
 // With X^T = [[I, p^], [0, I]] diag(R, R) (X^T (n; f) = (R n + p x R f; R f)) and
 // P = [[A, B], [B^T, C]] in 3x3 blocks: rotate the blocks, A' = R A R^T,
@@ -1707,16 +1717,28 @@ __device__ __forceinline__ void jsiia_body(const KArgs &A, const Range &rg) {
       }
     }
     tm.sync();
-    for (int t = 0; t * P < n; ++t) {
-      const int i = t * P + ((t & 1) ? (P - 1 - tm.r) : tm.r);
-      if (i >= n) continue;
-      TA f[6];
+    // rows RB rounds at a time (in snake order, increasing): each s_k loaded once
+    // serves every row below k
+    constexpr int RB = jsiia_rows_blocked<P>();
+    for (int t = 0; t * P < n; t += RB) {
+      int iq[RB];
+      TA f[RB][6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) f[c] = H[static_cast<int64_t>(i) * 6 + c];
-      for (int k = 0; k < i; ++k) {
+      for (int q = 0; q < RB; ++q) {
+        const int tt = t + q;
+        iq[q] = tt * P + ((tt & 1) ? (P - 1 - tm.r) : tm.r);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f[q][c] = iq[q] < n ? H[static_cast<int64_t>(iq[q]) * 6 + c] : TA(0);
+      }
+      const int last = min(iq[RB - 1], n);
+      for (int k = 0; k < last; ++k) {
         const TA *sv = Sb + static_cast<int64_t>(k) * 6;
-        Mat(i, k) = (((((sv[0] * f[0] + sv[1] * f[1]) + sv[2] * f[2]) + sv[3] * f[3]) +
-                      sv[4] * f[4]) + sv[5] * f[5]);
+        const TA s0 = sv[0], s1 = sv[1], s2 = sv[2], s3 = sv[3], s4 = sv[4], s5 = sv[5];
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+          if (k < iq[q] && iq[q] < n)
+            Mat(iq[q], k) = (((((s0 * f[q][0] + s1 * f[q][1]) + s2 * f[q][2]) + s3 * f[q][3]) +
+                              s4 * f[q][4]) + s5 * f[q][5]);
       }
     }
   } else {
@@ -1797,17 +1819,31 @@ __device__ __forceinline__ void jsiia_body(const KArgs &A, const Range &rg) {
         }
       }
     }
-    // rank-NB update of the trailing rows: M(i, l) -= sum_u L(i, j0+u) L(l, j0+u)
-    for (int i = j0 + jb + tm.r; i < n; i += P) {
-      TA li[NB];
+    // rank-NB update of the trailing rows: M(i, l) -= sum_u L(i, j0+u) L(l, j0+u),
+    // RB of a lane's rows (i, i + P, ...) at a time: each row l of the panel,
+    // loaded once, serves all of them (rows below l only)
+    constexpr int RB = jsiia_rows_blocked<P>();
+    for (int i = j0 + jb + tm.r; i < n; i += RB * P) {
+      TA li[RB][NB];
 #pragma unroll
-      for (int u = 0; u < NB; ++u) li[u] = Mat(i, j0 + u);
-#pragma unroll 2
-      for (int l = j0 + jb; l <= i; ++l) {
-        TA x = Mat(i, l);
+      for (int q = 0; q < RB; ++q)
 #pragma unroll
-        for (int u = 0; u < NB; ++u) x -= li[u] * Mat(l, j0 + u);
-        Mat(i, l) = x;
+        for (int u = 0; u < NB; ++u) li[q][u] = (i + q * P < n) ? Mat(i + q * P, j0 + u) : TA(0);
+      const int last = min(i + (RB - 1) * P, n - 1);
+      for (int l = j0 + jb; l <= last; ++l) {
+        TA pl[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) pl[u] = Mat(l, j0 + u);
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          const int iq = i + q * P;
+          if (iq < n && l <= iq) {
+            TA x = Mat(iq, l);
+#pragma unroll
+            for (int u = 0; u < NB; ++u) x -= li[q][u] * pl[u];
+            Mat(iq, l) = x;
+          }
+        }
       }
     }
     tm.sync();
