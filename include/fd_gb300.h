@@ -204,6 +204,56 @@ fd_status fd_inverse_dynamics(fd_batch_t batch, const void *q, const void *qdot,
                               void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * General projections W for CFA (not in the paper's experiments: its conclusion
+ * leaves the choice of the projection W of Eq. cfa-eq1 open, as a trade of speed
+ * against accuracy). Any W_i (6x5, W_i^T S_i = 0, rank 5) is Wc_i Q_i with Wc_i
+ * the library's own complement (e_2 .. e_6 of the link frame whose x axis is the
+ * joint axis) and Q_i an invertible 5x5 matrix. The system of Eq. cfa-eq2 then
+ * becomes A' = Q^T A Q, R' = Q^T R with Q = diag(Q_i), its solution
+ * F_c' = Q^{-1} F_c, and qdd is the same up to rounding: only the numbers the
+ * odd-even elimination works on change.
+ */
+typedef enum fd_projection {
+  FD_PROJ_CANONICAL = 0,   /* Q_i = I: the blocks fd_solve_batch's CFA solves */
+  FD_PROJ_GIVEN = 1,       /* Q_i given per link (fd_projection_to_canonical) */
+  FD_PROJ_BLOCK_JACOBI = 2 /* Q_i = L_i^{-T} with D_i = L_i L_i^T: every diagonal
+                              block of A' is the identity (state-dependent) */
+} fd_projection;
+
+/*
+ * fd_projection_to_canonical -- Q_i of given projections W_i. Host only.
+ *
+ * joint_axes [n_links][3] as given to fd_create_chain; W [n_links][6][5]
+ * row-major, W_i in link i's frame and (omega; v) order as for fd_create_chain;
+ * Q [n_links][5][5] row-major receives Q_i. FD_ERR_INVALID_ARG for a NULL
+ * array, n_links < 0, a zero axis, |S_i^T W_i| above 1e-9 max|W_i|, or a W_i
+ * whose Q_i is singular to working precision (|det Q_i| at most 1e-12 times the
+ * product of its column norms).
+ */
+fd_status fd_projection_to_canonical(int64_t n_links, const double *joint_axes, const double *W,
+                                     double *Q);
+
+/*
+ * fd_solve_cfa_projected -- CFA (Algorithm 1 with odd-even elimination,
+ * Algorithm 2) on the system of the projection `proj`.
+ *
+ * Arrays, workspace (fd_workspace_size of FD_CFA), status and stream as for
+ * fd_solve_batch. prec: FD_FP64 or FD_FP32 (FD_MIXED: FD_ERR_UNSUPPORTED).
+ * team: as for fd_solve_batch, except that team 0 takes one team for the whole
+ * batch (the autotuned CFA team of a one-class batch, else the default that
+ * fills the GPU; no split by length class). Q: device array [L][25] of double
+ * indexed by the chain set's link (link_offsets of fd_create_chain), Q_i
+ * row-major, required for FD_PROJ_GIVEN (else ignored, may be NULL); not
+ * retained after the solve completes. FD_PROJ_CANONICAL runs fd_solve_batch's
+ * FD_CFA kernel (bit for bit its result at the same team). In FP32 the solve
+ * keeps fd_solve_batch's refinement passes, each with its own projection.
+ */
+fd_status fd_solve_cfa_projected(fd_batch_t batch, const void *q, const void *qdot,
+                                 const void *tau, void *qddot, fd_prec prec, int32_t team,
+                                 fd_projection proj, const double *Q, void *workspace,
+                                 size_t workspace_bytes, int32_t *status, void *stream);
+
+/*
  * fd_autotune -- pick the team size for (batch, algo, prec) by timing.
  *
  * The paper leaves the parallel schedule to the implementation. For a batch of

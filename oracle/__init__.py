@@ -68,11 +68,12 @@ def _load():
             lib.orc_mass_matrix.argtypes = [ci, dp, dp, dp, dp, dp]
             lib.orc_cfa_blocks.argtypes = [ci, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
             lib.orc_oee_solve.argtypes = [ci, ci, dp, dp, dp, dp]
+            lib.orc_fd_cfa_w.argtypes = [ci, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
             lib.orc_fd_batch.argtypes = [ci, ci, i32p, i64p, i64p, dp, dp, dp, dp, dp, dp,
                                          dp, dp, i32p, ci]
             lib.orc_rnea_batch.argtypes = [ci, i32p, i64p, i64p, dp, dp, dp, dp, dp, dp,
                                            dp, dp, ci]
-            for f in (lib.orc_rnea, lib.orc_mass_matrix, lib.orc_cfa_blocks,
+            for f in (lib.orc_rnea, lib.orc_mass_matrix, lib.orc_cfa_blocks, lib.orc_fd_cfa_w,
                       lib.orc_oee_solve, lib.orc_fd_batch, lib.orc_rnea_batch):
                 f.restype = ci
             _lib = lib
@@ -139,6 +140,37 @@ def cfa_blocks(model, q, W=None):
     if st:
         raise RuntimeError(f"oracle cfa blocks failed ({st})")
     return dict(D=D, U=U, B=Bb, Cd=Cd, Co=Co, W=Wout)
+
+
+def fd_cfa_w(model, q, qd, tau, W=None, return_fc=False):
+    """CFA (Algorithms 1 and 2) with the projection W_i of Eq. cfa-eq1 given per
+    link (``W``: L x 6 x 5 in the link frames, W_i^T S_i = 0; None: the default
+    complement), chain p = problem p of a packed model. With ``return_fc`` also
+    the constraint-force coordinates F_c (L x 5), which depend on W."""
+    lib = _load()
+    ax, fr, J, g = _chain_arrays(model)
+    q, qd, tau = _c64(q), _c64(qd), _c64(tau)
+    Wa = None if W is None else _c64(W).reshape(-1, 6, 5)
+    L = ax.shape[0]
+    qdd = np.full(L, np.nan)
+    Fc = np.full((L, 5), np.nan)
+    off = np.asarray(model.offsets, dtype=np.int64)
+    for p in range(len(off) - 1):
+        a, z = int(off[p]), int(off[p + 1])
+        if z == a:
+            continue
+        Wp = None if Wa is None else np.ascontiguousarray(Wa[a:z])
+        out = np.empty(z - a)
+        fc = np.empty((z - a, 5))
+        st = lib.orc_fd_cfa_w(z - a, _d(np.ascontiguousarray(ax[a:z])),
+                              _d(np.ascontiguousarray(fr[a:z])),
+                              _d(np.ascontiguousarray(J[a:z])), _d(g), _d(q[a:z].copy()),
+                              _d(qd[a:z].copy()), _d(tau[a:z].copy()), _d(Wp), _d(out), _d(fc))
+        if st:
+            raise RuntimeError(f"oracle CFA with a given W failed for chain {p} ({st})")
+        qdd[a:z] = out
+        Fc[a:z] = fc
+    return (qdd, Fc) if return_fc else qdd
 
 
 def oee_solve(D, U, R):

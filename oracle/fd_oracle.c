@@ -559,10 +559,12 @@ static int oee_solve(int n, int b, double *D, double *U, double *R, double *F) {
 }
 
 /* Algorithm 1 (CalcFwdDyn_CFA): bias torque by ID, tau_delta, A, B, C,
- * R = -B tau_delta, block tri-diagonal solve by OEE, qdd = C tau_delta + B^T F_c. */
+ * R = -B tau_delta, block tri-diagonal solve by OEE, qdd = C tau_delta + B^T F_c.
+ * Win [n][30]: the projection W_i of Eq. cfa-eq1 (NULL: projection_w); Fc_out
+ * [n][5] (may be NULL) receives the constraint-force coordinates F_c. */
 static int fd_cfa_chain(int n, const double *axes, const double *frames, const double *J,
                         const double *grav, const double *q, const double *qd,
-                        const double *tau, double *qdd) {
+                        const double *tau, const double *Win, double *qdd, double *Fc_out) {
   size_t N = (size_t)n;
   double *td = malloc(sizeof(double) * N), *D = malloc(sizeof(double) * 25 * N);
   double *U = malloc(sizeof(double) * 25 * N), *Bb = malloc(sizeof(double) * 15 * N);
@@ -572,7 +574,7 @@ static int fd_cfa_chain(int n, const double *axes, const double *frames, const d
   if (td && D && U && Bb && Cd && Co && R && Fc) {
     rnea_chain(n, axes, frames, J, grav, q, qd, NULL, td);     /* CalcInvDyn */
     for (int i = 0; i < n; ++i) td[i] = tau[i] - td[i];        /* CalcDiffTorques */
-    st = cfa_blocks(n, axes, frames, J, q, NULL, D, U, Bb, Cd, Co, NULL);
+    st = cfa_blocks(n, axes, frames, J, q, Win, D, U, Bb, Cd, Co, NULL);
     if (st == ORC_OK) {
       for (int i = 0; i < n; ++i)                               /* R = -B tau_delta */
         for (int k = 0; k < 5; ++k) {
@@ -595,6 +597,7 @@ static int fd_cfa_chain(int n, const double *axes, const double *frames, const d
         }
         qdd[j] = s;
       }
+      if (Fc_out) memcpy(Fc_out, Fc, sizeof(double) * 5 * N);
     }
   }
   free(td); free(D); free(U); free(Bb); free(Cd); free(Co); free(R); free(Fc);
@@ -628,6 +631,15 @@ int orc_cfa_blocks(int n, const double *axes, const double *frames, const double
   return cfa_blocks(n, axes, frames, J, q, Win, D, U, Bb, Cd, Co, Wout);
 }
 
+/* CFA of one chain with the projection W [n][30] (Eq. cfa-eq1; NULL: the
+ * default complement); F_c [n][5] may be NULL. */
+int orc_fd_cfa_w(int n, const double *axes, const double *frames, const double *J,
+                 const double *grav, const double *q, const double *qd, const double *tau,
+                 const double *W, double *qdd, double *Fc) {
+  if (n < 1) return ORC_ERR_ARG;
+  return fd_cfa_chain(n, axes, frames, J, grav, q, qd, tau, W, qdd, Fc);
+}
+
 int orc_oee_solve(int n, int b, double *D, double *U, double *R, double *F) {
   if (n < 1 || b < 1 || b > 8) return ORC_ERR_ARG;
   return oee_solve(n, b, D, U, R, F);
@@ -659,7 +671,7 @@ int orc_fd_batch(int algo, int n_problems, const int32_t *chain_of,
                         qd + s0, tau + s0, qdd + s0);
     else if (algo == ORC_ALGO_CFA)
       st = fd_cfa_chain(n, axes + 3 * m0, frames + 12 * m0, J + 36 * m0, grav, q + s0,
-                        qd + s0, tau + s0, qdd + s0);
+                        qd + s0, tau + s0, NULL, qdd + s0, NULL);
     else
       st = ORC_ERR_ARG;
     if (status) status[p] = st;

@@ -586,11 +586,12 @@ size_t fd_workspace_size(fd_batch_t b, int32_t algo, fd_prec prec, int32_t team)
   return w.t_bytes + w.a_bytes;
 }
 
-// only_class >= 0: launch that length class alone with `team` (the autotuner)
+// only_class >= 0: launch that length class alone with `team` (the autotuner);
+// wmode != 0: CFA with a general projection (fdk::WPROJ_*, Q_i in wq)
 static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, const void *in3,
                                void *out, int32_t algo, fd_prec prec, int32_t team, void *ws,
                                size_t ws_bytes, int32_t *status, void *stream, const char *who,
-                               int only_class = -1) {
+                               int only_class = -1, int wmode = 0, const double *wq = nullptr) {
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
@@ -632,13 +633,17 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   a.ws_t = ws;
   a.ws_a = static_cast<char *>(ws) + w.t_bytes;
   a.status = status;
+  a.wq = wq;
+  a.wmode = wmode;
   std::memcpy(a.grav, b->chain->grav, sizeof a.grav);
   int prev = 0;
   cudaGetDevice(&prev);
   cudaError_t e = cudaSetDevice(b->chain->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto s = static_cast<cudaStream_t>(stream);
-  if (only_class >= 0 || use_classes(b, algo, team)) {
+  if (wmode != 0) {
+    e = fdk::launch_cfa_w(a, prec_k, t, s);
+  } else if (only_class >= 0 || use_classes(b, algo, team)) {
     std::vector<int> teams(b->classes.size());
     for (size_t c = 0; c < teams.size(); ++c)
       teams[c] = (only_class >= 0 && static_cast<int>(c) == only_class && team > 0)
@@ -669,6 +674,97 @@ fd_status fd_inverse_dynamics(fd_batch_t b, const void *q, const void *qdot, con
                               size_t workspace_bytes, void *stream) {
   return launch_common(b, q, qdot, qddot, tau, -1, prec == FD_MIXED ? FD_FP32 : prec, team,
                        workspace, workspace_bytes, nullptr, stream, "fd_inverse_dynamics");
+}
+
+fd_status fd_projection_to_canonical(int64_t n_links, const double *joint_axes, const double *W,
+                                     double *Q) {
+  const char *who = "fd_projection_to_canonical";
+  if (n_links < 0) return fail(FD_ERR_INVALID_ARG, "%s: n_links %lld", who, static_cast<long long>(n_links));
+  if (n_links > 0 && (!joint_axes || !W || !Q))
+    return fail(FD_ERR_INVALID_ARG, "%s: NULL array", who);
+  for (int64_t i = 0; i < n_links; ++i) {
+    const double *ax = joint_axes + 3 * i;
+    const double na = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+    if (!(na > 1e-12) || !std::isfinite(na))
+      return fail(FD_ERR_INVALID_ARG, "%s: link %lld has a zero joint axis", who,
+                  static_cast<long long>(i));
+    const double a[3] = {ax[0] / na, ax[1] / na, ax[2] / na};
+    double F[9];
+    axis_frame(a, F);  // link coordinates of the canonical axes (columns)
+    // a wrench in canonical coordinates: (F^T n; F^T f)
+    const double *Wi = W + 30 * i;
+    double Wc[30], scale = 0.0;
+    for (int k = 0; k < 30; ++k) scale = std::max(scale, std::fabs(Wi[k]));
+    for (int h = 0; h < 2; ++h)
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 5; ++c)
+          Wc[5 * (3 * h + r) + c] = F[r] * Wi[5 * (3 * h) + c] + F[3 + r] * Wi[5 * (3 * h + 1) + c] +
+                                    F[6 + r] * Wi[5 * (3 * h + 2) + c];
+    if (!(scale > 0.0) || !std::isfinite(scale))
+      return fail(FD_ERR_INVALID_ARG, "%s: link %lld: W is zero or not finite", who,
+                  static_cast<long long>(i));
+    for (int c = 0; c < 5; ++c)  // row 0 of Wc is S_i^T W_i
+      if (!(std::fabs(Wc[c]) <= 1e-9 * scale))
+        return fail(FD_ERR_INVALID_ARG, "%s: link %lld: W^T S = %.3e, not 0", who,
+                    static_cast<long long>(i), Wc[c]);
+    double *Qi = Q + 25 * i;
+    for (int k = 0; k < 25; ++k) Qi[k] = Wc[5 + k];
+    // |det Q_i| against the product of its column norms, by Gaussian elimination
+    // with partial pivoting on a copy
+    double M[25], cn = 1.0, det = 1.0;
+    std::memcpy(M, Qi, sizeof M);
+    for (int c = 0; c < 5; ++c) {
+      double s2 = 0.0;
+      for (int r = 0; r < 5; ++r) s2 += M[5 * r + c] * M[5 * r + c];
+      cn *= std::sqrt(s2);
+    }
+    for (int c = 0; c < 5 && det != 0.0; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < 5; ++r)
+        if (std::fabs(M[5 * r + c]) > std::fabs(M[5 * piv + c])) piv = r;
+      if (M[5 * piv + c] == 0.0) {
+        det = 0.0;
+        break;
+      }
+      if (piv != c) {
+        for (int k = 0; k < 5; ++k) std::swap(M[5 * c + k], M[5 * piv + k]);
+        det = -det;
+      }
+      det *= M[5 * c + c];
+      for (int r = c + 1; r < 5; ++r) {
+        const double f = M[5 * r + c] / M[5 * c + c];
+        for (int k = c; k < 5; ++k) M[5 * r + k] -= f * M[5 * c + k];
+      }
+    }
+    if (!(std::fabs(det) > 1e-12 * cn))
+      return fail(FD_ERR_INVALID_ARG, "%s: link %lld: W has rank below 5", who,
+                  static_cast<long long>(i));
+  }
+  return FD_OK;
+}
+
+fd_status fd_solve_cfa_projected(fd_batch_t b, const void *q, const void *qdot, const void *tau,
+                                 void *qddot, fd_prec prec, int32_t team, fd_projection proj,
+                                 const double *Q, void *workspace, size_t workspace_bytes,
+                                 int32_t *status, void *stream) {
+  const char *who = "fd_solve_cfa_projected";
+  if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
+  if (proj != FD_PROJ_CANONICAL && proj != FD_PROJ_GIVEN && proj != FD_PROJ_BLOCK_JACOBI)
+    return fail(FD_ERR_INVALID_ARG, "%s: bad projection %d", who, static_cast<int>(proj));
+  if (prec == FD_MIXED)
+    return fail(FD_ERR_UNSUPPORTED, "%s: FP64 and FP32 only", who);
+  if (prec != FD_FP64 && prec != FD_FP32)
+    return fail(FD_ERR_INVALID_ARG, "%s: bad precision %d", who, static_cast<int>(prec));
+  if (proj == FD_PROJ_GIVEN && !Q && b->n_problems > 0 && b->n_state_links > 0)
+    return fail(FD_ERR_INVALID_ARG, "%s: FD_PROJ_GIVEN needs Q", who);
+  if (team < 0 || (team > 0 && !valid_team(team)))
+    return fail(FD_ERR_INVALID_ARG, "%s: team %d is not 0 or a power of two <= 256", who, team);
+  // one team for the whole batch (no split by length class)
+  const int t = resolve_team(b, FD_CFA, prec, team);
+  const int wmode = proj == FD_PROJ_GIVEN ? fdk::WPROJ_GIVEN
+                    : proj == FD_PROJ_BLOCK_JACOBI ? fdk::WPROJ_BLOCK_JACOBI : 0;
+  return launch_common(b, q, qdot, tau, qddot, FD_CFA, prec, t, workspace, workspace_bytes,
+                       status, stream, who, -1, wmode, Q);
 }
 
 }  // extern "C"

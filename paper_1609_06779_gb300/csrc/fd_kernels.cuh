@@ -1020,8 +1020,11 @@ __device__ __forceinline__ bool hybrid_solve(const Team<P> &tm, TA *wa, int n, b
 // partition / cyclic-reduction schedule. In MODE_FD2 a second
 // right-hand side (tau_delta := in4) rides along: the blocks D, U and their
 // elimination are shared, only R, F_c and CalcAcc are done twice.
-template <class T, class TA, int P, int BTD, bool TWO>
+// WP: a general projection W_i = Wc_i Q_i (A.wmode; odd-even elimination, one
+// right-hand side).
+template <class T, class TA, int P, int BTD, bool TWO, bool WP = false>
 __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
+  static_assert(!WP || (BTD == 0 && !TWO), "a general projection runs with OEE, one right-hand side");
   Team<P> tm;
   Prob<T> pb;
   if (!load_problem<T, P>(A, rg, tm, pb, NT)) return;
@@ -1155,6 +1158,108 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
   }
   tm.sync();
 
+  // A general projection (the paper's closing question: other choices of W in
+  // Eq. cfa-eq1). Any W_i with W_i^T S_i = 0 and full rank is Wc_i Q_i with Q_i
+  // invertible, Wc_i the canonical complement e_2 .. e_6 the blocks above use. With
+  // Q = diag(Q_i) the system of Eq. cfa-eq2 becomes A' = Q^T A Q, R' = Q^T R and
+  // its solution F_c' = Q^{-1} F_c, so qdd is unchanged and only the
+  // elimination's numbers differ: D_i' = Q_i^T D_i Q_i, U_i' = Q_i^T U_i Q_{i+1},
+  // R_i' = Q_i^T R_i, and F_c,i = Q_i F_c,i' after the solve. Block Jacobi takes
+  // Q_i = L_i^{-T} with D_i = L_i L_i^T, which makes every D_i' the identity.
+  if constexpr (WP) {
+    for (int i = tm.r; i < n; i += P) {
+      const RowP<TA> row = rowp(wa, n, i);
+      TA Qm[25];
+      if (A.wmode == WPROJ_GIVEN) {
+        const double *src = A.wq + (pb.m0 + i) * 25;
+#pragma unroll
+        for (int k = 0; k < 25; ++k) Qm[k] = TA(src[k]);
+      } else {
+        TA Dm[15], L[15], inv[5];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) Dm[k] = row[A_D0 + k];
+        bad |= !chol5(Dm, L, inv);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {  // column c of L^{-T}: L^T x = e_c
+          TA x[5];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) x[k] = k == c ? TA(1) : TA(0);
+          bwd5(L, inv, x);
+#pragma unroll
+          for (int k = 0; k < 5; ++k) Qm[5 * k + c] = x[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 25; ++k) row[A_Q + k] = Qm[k];
+    }
+    tm.sync();
+    for (int i = tm.r; i < n; i += P) {
+      const RowP<TA> row = rowp(wa, n, i);
+      TA Qm[25], X[25];
+#pragma unroll
+      for (int k = 0; k < 25; ++k) Qm[k] = row[A_Q + k];
+      if (A.wmode == WPROJ_BLOCK_JACOBI) {
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int c = 0; c <= r; ++c) row[A_D0 + l5(r, c)] = r == c ? TA(1) : TA(0);
+      } else {
+        // X = D Q, D' = Q^T X (lower triangle)
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            TA t = TA(0);
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+              t += row[A_D0 + (r >= k ? l5(r, k) : l5(k, r))] * Qm[5 * k + c];
+            X[5 * r + c] = t;
+          }
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int c = 0; c <= r; ++c) {
+            TA t = TA(0);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) t += Qm[5 * k + r] * X[5 * k + c];
+            row[A_D0 + l5(r, c)] = t;
+          }
+      }
+      if (i + 1 < n) {  // X = U Q_{i+1}, U' = Q_i^T X
+        const RowP<TA> qn = rowp(wa, n, i + 1) + A_Q;
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            TA t = TA(0);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) t += row[A_U0 + 5 * r + k] * qn[5 * k + c];
+            X[5 * r + c] = t;
+          }
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            TA t = TA(0);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) t += Qm[5 * k + r] * X[5 * k + c];
+            row[A_U0 + 5 * r + c] = t;
+          }
+      }
+      TA rr[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) rr[k] = row[A_R0 + k];
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        TA t = TA(0);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) t += Qm[5 * k + r] * rr[k];
+        row[A_R0 + r] = t;
+      }
+    }
+    tm.sync();
+  }
+
   if constexpr (BTD == 1) {
     // SolvBTDSys by block cyclic reduction
     bad |= cr_solve<TA, P>(tm, wa, n, two);
@@ -1205,6 +1310,22 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
     }
   }
   tm.sync();
+  }
+  if constexpr (WP) {  // F_c,i = Q_i F_c,i'
+    for (int i = tm.r; i < n; i += P) {
+      const RowP<TA> row = rowp(wa, n, i);
+      TA y[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) y[k] = row[A_FC + k];
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        TA t = TA(0);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) t += row[A_Q + 5 * r + k] * y[k];
+        row[A_FC + r] = t;
+      }
+    }
+    tm.sync();
   }
 
   // CalcAcc: qdd = C tau_delta + B^T F_c = S^T (I-Gamma) J^{-1} (I-Gamma)^T F,
@@ -1283,6 +1404,11 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
 template <class T, class TA, int P>
 __global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_kernel(KArgs A) {
   cfa_body<T, TA, P, 0, false>(A, Range{0, 0, A.n_problems});
+}
+
+template <class T, class TA, int P>
+__global__ void __launch_bounds__(block_for<P>(), P <= 128 ? 3 : 1) cfa_w_kernel(KArgs A) {
+  cfa_body<T, TA, P, 0, false, true>(A, Range{0, 0, A.n_problems});
 }
 
 template <class T, class TA, int P>

@@ -47,6 +47,7 @@ constexpr int A_FC = 110;  // F_c (5)
 constexpr int A_G = 115;   // G = L^{-1} U (row-major 5x5) and g = L^{-1} R of this level
 constexpr int A_GR = 140;
 constexpr int A_LO = 145;  // cyclic reduction: the lower coupling U_{i-d} kept for back substitution
+constexpr int A_Q = 145;   // general projection (odd-even elimination only): Q_i, row-major 5x5
 // a second right-hand side (MODE_FD2: the adjoint's M^{-1} w beside FD)
 constexpr int A_R20 = 170;  // R (5), two buffers
 constexpr int A_R21 = 175;
@@ -131,6 +132,15 @@ struct KArgs {
   void *out3;       // adjoint: mass_bar (or null)
   const void *in4;  // MODE_FD2: second right-hand side w
   void *out4;       // MODE_FD2: M^{-1} w
+  // CFA with a general projection W_i = Wc_i Q_i (Wc_i = e_2 .. e_6 of the
+  // canonical frame): WPROJ_GIVEN takes Q_i from wq ([L][25] double, row-major,
+  // by the model's link index), WPROJ_BLOCK_JACOBI forms Q_i = L_i^{-T} from
+  // D_i = L_i L_i^T
+  const double *wq;
+  int32_t wmode;
 };
+
+constexpr int WPROJ_GIVEN = 1;
+constexpr int WPROJ_BLOCK_JACOBI = 2;
 
 }  // namespace fdk

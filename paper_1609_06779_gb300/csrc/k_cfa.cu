@@ -6,6 +6,8 @@ namespace fdk {
 cudaError_t launch_cfa_f64(const KArgs &a, int team, cudaStream_t s);
 cudaError_t launch_cfa_f32(const KArgs &a, int team, cudaStream_t s);
 cudaError_t launch_cfa_mixed(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa_w_f64(const KArgs &a, int team, cudaStream_t s);
+cudaError_t launch_cfa_w_f32(const KArgs &a, int team, cudaStream_t s);
 cudaError_t launch_cfa_cr_f64(const KArgs &a, int team, cudaStream_t s);
 cudaError_t launch_cfa_cr_f32(const KArgs &a, int team, cudaStream_t s);
 cudaError_t launch_cfa_cr_mixed(const KArgs &a, int team, cudaStream_t s);
@@ -29,6 +31,15 @@ cudaError_t launch_cfa(const KArgs &a, int prec, int team, cudaStream_t s) {
     case 0: return launch_cfa_f64(a, team, s);
     case 1: return launch_cfa_f32(a, team, s);
     case 2: return launch_cfa_mixed(a, team, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// CFA with a general projection (a.wmode, a.wq): FP64 and FP32
+cudaError_t launch_cfa_w(const KArgs &a, int prec, int team, cudaStream_t s) {
+  switch (prec) {
+    case 0: return launch_cfa_w_f64(a, team, s);
+    case 1: return launch_cfa_w_f32(a, team, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -65,6 +65,9 @@ def load(build_if_missing: bool = True):
         lib.fd_solve_batch.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp, vp]
         lib.fd_inverse_dynamics.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
         lib.fd_solve_cfa_static.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, vp]
+        lib.fd_projection_to_canonical.argtypes = [i64, dp, dp, dp]
+        lib.fd_solve_cfa_projected.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, sz,
+                                               vp, vp]
         lib.fd_adjoint_workspace_size.argtypes = [vp, i32, i32, i32]
         lib.fd_adjoint_workspace_size.restype = sz
         lib.fd_solve_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32,
@@ -81,7 +84,8 @@ def load(build_if_missing: bool = True):
         lib.fd_autotune_cache_clear.argtypes = []
         for f in ("fd_create_chain", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
                   "fd_batch_destroy", "fd_batch_info", "fd_solve_batch", "fd_inverse_dynamics",
-                  "fd_solve_cfa_static", "fd_batch_classes", "fd_autotune_cache_load",
+                  "fd_solve_cfa_static", "fd_projection_to_canonical",
+                  "fd_solve_cfa_projected", "fd_batch_classes", "fd_autotune_cache_load",
                   "fd_autotune_cache_save", "fd_autotune_cache_clear"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -239,6 +243,58 @@ def inverse_dynamics(batch: Batch, q, qd, qdd, prec="fp64", team=0, out=None, ws
     _check(load().fd_inverse_dynamics(batch.handle, q.data_ptr(), qd.data_ptr(), qdd.data_ptr(),
                                       out.data_ptr(), PRECS[prec], int(team), ws.data_ptr(),
                                       ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+PROJECTIONS = {"canonical": 0, "given": 1, "block_jacobi": 2}
+
+
+def projection_to_canonical(joint_axes, W) -> np.ndarray:
+    """Q_i (n x 5 x 5) of projections W_i (n x 6 x 5, link frames, (omega; v)
+    order; fd_projection_to_canonical): W_i = Wc_i Q_i, Wc_i the library's own
+    complement of the joint axis. Host only."""
+    ax = np.ascontiguousarray(joint_axes, dtype=np.float64).reshape(-1, 3)
+    Wa = np.ascontiguousarray(W, dtype=np.float64).reshape(ax.shape[0], 6, 5)
+    Q = np.empty((ax.shape[0], 5, 5))
+    _check(load().fd_projection_to_canonical(ax.shape[0], _dptr(ax), _dptr(Wa), _dptr(Q)))
+    return Q
+
+
+def solve_cfa_projected(batch: Batch, q, qd, tau, projection="block_jacobi", Q=None,
+                        prec="fp64", team=0, out=None, ws=None, status=None, stream=None):
+    """CFA on the system of a general projection W_i = Wc_i Q_i
+    (fd_solve_cfa_projected): ``projection`` is "canonical", "given" (``Q``: a
+    CUDA float64 tensor of the chain set's n_links x 5 x 5 entries, from
+    :func:`projection_to_canonical`) or "block_jacobi". FP64 or FP32."""
+    torch = _torch()
+    dt = _state_dtype(prec)
+    for t, nm in ((q, "q"), (qd, "qdot"), (tau, "tau")):
+        _check_state(t, batch, dt, nm)
+    if out is None:
+        out = torch.empty_like(q)
+    _check_state(out, batch, dt, "qddot")
+    if projection not in PROJECTIONS:
+        raise FDError(1, f"unknown projection {projection!r}")
+    qptr = None
+    if projection == "given":
+        n_links = batch.chains.info()[1]
+        if (not isinstance(Q, torch.Tensor) or not Q.is_cuda or Q.dtype != torch.float64
+                or not Q.is_contiguous() or Q.numel() != 25 * n_links):
+            raise FDError(1, f"Q must be a contiguous CUDA float64 tensor of {25 * n_links} "
+                             f"entries")
+        qptr = Q.data_ptr()
+    if ws is None:
+        ws = workspace(batch, "cfa", prec, team, q.device)
+    if status is not None and (status.dtype != torch.int32 or not status.is_cuda
+                               or status.numel() < batch.n_problems):
+        raise FDError(1, "status must be a CUDA int32 tensor of n_problems elements")
+    s = stream if stream is not None else torch.cuda.current_stream(q.device)
+    _check(load().fd_solve_cfa_projected(batch.handle, q.data_ptr(), qd.data_ptr(),
+                                         tau.data_ptr(), out.data_ptr(), PRECS[prec], int(team),
+                                         PROJECTIONS[projection], qptr, ws.data_ptr(),
+                                         ws.numel(),
+                                         None if status is None else status.data_ptr(),
+                                         ctypes.c_void_p(s.cuda_stream)))
     return out
 
 

@@ -146,3 +146,29 @@ def test_autotune_cache_round_trip(lib, tmp_path):
     fd.autotune_cache_clear()
     fd.autotune_cache_save(str(out))
     assert json.loads(out.read_text())["entries"] == []
+
+
+def test_projection_to_canonical(lib):
+    """fd_projection_to_canonical (host only): an orthonormal complement of each
+    joint axis maps to an orthogonal Q_i, W_i Z_i maps to Q_i Z_i, and a W_i that
+    is not a complement of S_i, or has rank below 5, is rejected."""
+    import oracle.dense as dense
+    model = synth.random_chains([4, 3], seed=5)
+    L = model.n_links_total
+    _, Wb = dense.projection(model)
+    Q = fd.projection_to_canonical(model.axes, Wb)
+    for i in range(L):
+        np.testing.assert_allclose(Q[i].T @ Q[i], np.eye(5), atol=1e-13)
+    rng = np.random.default_rng(1)
+    Z = rng.standard_normal((L, 5, 5)) + 2 * np.eye(5)
+    Qz = fd.projection_to_canonical(model.axes, Wb @ Z)
+    np.testing.assert_allclose(Qz, Q @ Z, atol=1e-12)
+    bad = Wb.copy()
+    bad[2, :3, 1] += np.asarray(model.axes)[2] / np.linalg.norm(model.axes[2])  # S^T W != 0
+    with pytest.raises(fd.FDError, match="W\\^T S"):
+        fd.projection_to_canonical(model.axes, bad)
+    low = Wb.copy()
+    low[1, :, 4] = low[1, :, 3]  # two equal columns
+    with pytest.raises(fd.FDError, match="rank"):
+        fd.projection_to_canonical(model.axes, low)
+    assert fd.projection_to_canonical(np.zeros((0, 3)), np.zeros((0, 6, 5))).shape == (0, 5, 5)

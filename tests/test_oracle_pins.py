@@ -310,6 +310,53 @@ def test_cfa_invariant_under_choice_of_w(seed):
     np.testing.assert_allclose(a, c, rtol=1e-9, atol=1e-9)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_cfa_with_given_w_matches_dense_solve(seed):
+    """The oracle's CFA with a given, non-orthogonal W_i (Eq. cfa-eq1): its
+    constraint-force coordinates F_c, which depend on W, equal the dense solve
+    A F_c = -B tau_delta of Eq. cfa-eq2 with the same W; F_c(W_i Z_i) = Z_i^{-1}
+    F_c(W_i); qdd equals the Cholesky route's. Two chains packed, so that the
+    per-chain slicing is pinned too."""
+    rng = np.random.default_rng(seed)
+    lengths = [5, 3]
+    model = synth.random_chains(lengths, seed=seed, random_home_rotation=True)
+    st = synth.random_states(model.n_links_total, seed=seed + 7)
+    _, Wb = dense.projection(model)
+    Z = rng.standard_normal((model.n_links_total, 5, 5)) + 3 * np.eye(5)
+    Wz = Wb @ Z
+    qdd0, fc0 = oracle.fd_cfa_w(model, st.q, st.qdot, st.tau, Wb, return_fc=True)
+    qdd1, fc1 = oracle.fd_cfa_w(model, st.q, st.qdot, st.tau, Wz, return_fc=True)
+    ref = oracle.fd(model, st.q, st.qdot, st.tau, algo="cholesky")
+    np.testing.assert_allclose(qdd0, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    np.testing.assert_allclose(qdd1, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    for i in range(model.n_links_total):
+        np.testing.assert_allclose(fc1[i], np.linalg.solve(Z[i], fc0[i]), rtol=1e-8,
+                                   atol=1e-8 * np.abs(fc0).max())
+    # the dense solve, chain by chain
+    for p in range(len(lengths)):
+        a, z = int(model.offsets[p]), int(model.offsets[p + 1])
+        one = _chain_of(model, a, z)
+        n = z - a
+        W = np.zeros((6 * n, 5 * n))
+        for i in range(n):
+            W[6 * i:6 * i + 6, 5 * i:5 * i + 5] = Wz[a + i]
+        m = dense.cfa_matrices(one, st.q[a:z], W)
+        td = st.tau[a:z] - dense.inverse_dynamics(one, st.q[a:z], st.qdot[a:z], np.zeros(n))
+        fcd = np.linalg.solve(m["A"], -m["B"] @ td).reshape(n, 5)
+        np.testing.assert_allclose(fc1[a:z], fcd, rtol=1e-8, atol=1e-8 * np.abs(fcd).max())
+    # a W that is not a complement of S (W^T S != 0) changes qdd: W is used
+    Wbad = Wz.copy()
+    Wbad[:, :3, 0] += np.asarray(model.axes)[:, :]
+    qbad = oracle.fd_cfa_w(model, st.q, st.qdot, st.tau, Wbad)
+    assert np.abs(qbad - ref).max() > 1e-6 * np.abs(ref).max()
+
+
+def _chain_of(model, a, z):
+    """Links a .. z-1 of a packed model as a model of one chain."""
+    return _single_chain(np.asarray(model.axes)[a:z], np.asarray(model.frames)[a:z],
+                         np.asarray(model.inertias)[a:z], model.gravity)
+
+
 def _random_btd(n, b, rng):
     """A random SPD symmetric block tri-diagonal system: A = L L^T with L block
     lower bi-diagonal."""
