@@ -1165,45 +1165,78 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
   // its solution F_c' = Q^{-1} F_c, so qdd is unchanged and only the
   // elimination's numbers differ: D_i' = Q_i^T D_i Q_i, U_i' = Q_i^T U_i Q_{i+1},
   // R_i' = Q_i^T R_i, and F_c,i = Q_i F_c,i' after the solve. Block Jacobi takes
-  // Q_i = L_i^{-T} with D_i = L_i L_i^T, which makes every D_i' the identity.
+  // Q_i = L_i^{-T} with D_i = L_i L_i^T: every D_i' is the identity and the rest
+  // are triangular solves, U_i' = L_i^{-1} U_i L_{i+1}^{-T}, R_i' = L_i^{-1} R_i,
+  // F_c,i = L_i^{-T} F_c,i'. The row's A_Q slot holds Q_i, or L_i and 1 / L_jj.
   if constexpr (WP) {
+    const bool bj = A.wmode == WPROJ_BLOCK_JACOBI;
     for (int i = tm.r; i < n; i += P) {
       const RowP<TA> row = rowp(wa, n, i);
-      TA Qm[25];
-      if (A.wmode == WPROJ_GIVEN) {
-        const double *src = A.wq + (pb.m0 + i) * 25;
-#pragma unroll
-        for (int k = 0; k < 25; ++k) Qm[k] = TA(src[k]);
-      } else {
+      if (bj) {
         TA Dm[15], L[15], inv[5];
 #pragma unroll
         for (int k = 0; k < 15; ++k) Dm[k] = row[A_D0 + k];
         bad |= !chol5(Dm, L, inv);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {  // column c of L^{-T}: L^T x = e_c
-          TA x[5];
+        for (int k = 0; k < 15; ++k) row[A_Q + k] = L[k];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) x[k] = k == c ? TA(1) : TA(0);
-          bwd5(L, inv, x);
+        for (int k = 0; k < 5; ++k) row[A_Q + 15 + k] = inv[k];
+      } else {
+        const double *src = A.wq + (pb.m0 + i) * 25;
 #pragma unroll
-          for (int k = 0; k < 5; ++k) Qm[5 * k + c] = x[k];
-        }
+        for (int k = 0; k < 25; ++k) row[A_Q + k] = TA(src[k]);
       }
-#pragma unroll
-      for (int k = 0; k < 25; ++k) row[A_Q + k] = Qm[k];
     }
     tm.sync();
     for (int i = tm.r; i < n; i += P) {
       const RowP<TA> row = rowp(wa, n, i);
-      TA Qm[25], X[25];
+      TA X[25];
+      if (bj) {
+        TA L[15], inv[5];
 #pragma unroll
-      for (int k = 0; k < 25; ++k) Qm[k] = row[A_Q + k];
-      if (A.wmode == WPROJ_BLOCK_JACOBI) {
+        for (int k = 0; k < 15; ++k) L[k] = row[A_Q + k];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) inv[k] = row[A_Q + 15 + k];
 #pragma unroll
         for (int r = 0; r < 5; ++r)
 #pragma unroll
           for (int c = 0; c <= r; ++c) row[A_D0 + l5(r, c)] = r == c ? TA(1) : TA(0);
+        if (i + 1 < n) {
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {  // X = L_i^{-1} U_i, column by column
+            TA col[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) col[k] = row[A_U0 + 5 * k + c];
+            fwd5(L, inv, col);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) X[5 * k + c] = col[k];
+          }
+          const RowP<TA> nx = rowp(wa, n, i + 1) + A_Q;
+#pragma unroll
+          for (int k = 0; k < 15; ++k) L[k] = nx[k];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) inv[k] = nx[15 + k];
+#pragma unroll
+          for (int r = 0; r < 5; ++r) {  // row r of X L_{i+1}^{-T} = L_{i+1}^{-1} X_r^T
+            fwd5(L, inv, X + 5 * r);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) row[A_U0 + 5 * r + c] = X[5 * r + c];
+          }
+#pragma unroll
+          for (int k = 0; k < 15; ++k) L[k] = row[A_Q + k];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) inv[k] = row[A_Q + 15 + k];
+        }
+        TA rr[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) rr[k] = row[A_R0 + k];
+        fwd5(L, inv, rr);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) row[A_R0 + k] = rr[k];
       } else {
+        TA Qm[25];
+#pragma unroll
+        for (int k = 0; k < 25; ++k) Qm[k] = row[A_Q + k];
         // X = D Q, D' = Q^T X (lower triangle)
 #pragma unroll
         for (int r = 0; r < 5; ++r)
@@ -1224,37 +1257,37 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
             for (int k = 0; k < 5; ++k) t += Qm[5 * k + r] * X[5 * k + c];
             row[A_D0 + l5(r, c)] = t;
           }
-      }
-      if (i + 1 < n) {  // X = U Q_{i+1}, U' = Q_i^T X
-        const RowP<TA> qn = rowp(wa, n, i + 1) + A_Q;
+        if (i + 1 < n) {  // X = U Q_{i+1}, U' = Q_i^T X
+          const RowP<TA> qn = rowp(wa, n, i + 1) + A_Q;
 #pragma unroll
-        for (int r = 0; r < 5; ++r)
+          for (int r = 0; r < 5; ++r)
 #pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            TA t = TA(0);
+            for (int c = 0; c < 5; ++c) {
+              TA t = TA(0);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) t += row[A_U0 + 5 * r + k] * qn[5 * k + c];
-            X[5 * r + c] = t;
-          }
+              for (int k = 0; k < 5; ++k) t += row[A_U0 + 5 * r + k] * qn[5 * k + c];
+              X[5 * r + c] = t;
+            }
 #pragma unroll
-        for (int r = 0; r < 5; ++r)
+          for (int r = 0; r < 5; ++r)
 #pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            TA t = TA(0);
+            for (int c = 0; c < 5; ++c) {
+              TA t = TA(0);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) t += Qm[5 * k + r] * X[5 * k + c];
-            row[A_U0 + 5 * r + c] = t;
-          }
-      }
-      TA rr[5];
+              for (int k = 0; k < 5; ++k) t += Qm[5 * k + r] * X[5 * k + c];
+              row[A_U0 + 5 * r + c] = t;
+            }
+        }
+        TA rr[5];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) rr[k] = row[A_R0 + k];
+        for (int k = 0; k < 5; ++k) rr[k] = row[A_R0 + k];
 #pragma unroll
-      for (int r = 0; r < 5; ++r) {
-        TA t = TA(0);
+        for (int r = 0; r < 5; ++r) {
+          TA t = TA(0);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) t += Qm[5 * k + r] * rr[k];
-        row[A_R0 + r] = t;
+          for (int k = 0; k < 5; ++k) t += Qm[5 * k + r] * rr[k];
+          row[A_R0 + r] = t;
+        }
       }
     }
     tm.sync();
@@ -1317,12 +1350,23 @@ __device__ __forceinline__ void cfa_body(const KArgs &A, const Range &rg) {
       TA y[5];
 #pragma unroll
       for (int k = 0; k < 5; ++k) y[k] = row[A_FC + k];
+      if (A.wmode == WPROJ_BLOCK_JACOBI) {
+        TA L[15], inv[5];
 #pragma unroll
-      for (int r = 0; r < 5; ++r) {
-        TA t = TA(0);
+        for (int k = 0; k < 15; ++k) L[k] = row[A_Q + k];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) t += row[A_Q + 5 * r + k] * y[k];
-        row[A_FC + r] = t;
+        for (int k = 0; k < 5; ++k) inv[k] = row[A_Q + 15 + k];
+        bwd5(L, inv, y);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) row[A_FC + k] = y[k];
+      } else {
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+          TA t = TA(0);
+#pragma unroll
+          for (int k = 0; k < 5; ++k) t += row[A_Q + 5 * r + k] * y[k];
+          row[A_FC + r] = t;
+        }
       }
     }
     tm.sync();

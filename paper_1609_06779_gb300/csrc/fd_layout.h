@@ -47,7 +47,8 @@ constexpr int A_FC = 110;  // F_c (5)
 constexpr int A_G = 115;   // G = L^{-1} U (row-major 5x5) and g = L^{-1} R of this level
 constexpr int A_GR = 140;
 constexpr int A_LO = 145;  // cyclic reduction: the lower coupling U_{i-d} kept for back substitution
-constexpr int A_Q = 145;   // general projection (odd-even elimination only): Q_i, row-major 5x5
+constexpr int A_Q = 145;   // general projection (odd-even elimination only): Q_i (row-major
+                           // 5x5), or for block Jacobi L_i (15) and 1 / L_jj (5)
 // a second right-hand side (MODE_FD2: the adjoint's M^{-1} w beside FD)
 constexpr int A_R20 = 170;  // R (5), two buffers
 constexpr int A_R21 = 175;
