@@ -773,6 +773,20 @@ def main():
                 variants[f"{a}_{prec}"] = {"ms": ms, "solves_per_s": args.chains / (ms / 1e3)}
                 acc_outs[f"{a}_{prec}"] = o[:n_acc].cpu()
                 del w
+        # CFA on the block-Jacobi projection (fd_solve_cfa_projected: W_i = Wc_i
+        # L_i^{-T}, the paper's open choice of W in Eq. cfa-eq1): the same qdd,
+        # another elimination's rounding
+        for prec, (qq, qqd, qtau) in (("fp64", (q, qd, tau)), ("fp32", (q32, qd32, tau32))):
+            tv = forced.get("cfa", 0)
+            w = fd.workspace(batch, "cfa", prec, tv, dev)
+            o = torch.empty_like(qq)
+            ms = _time_ms(lambda: fd.solve_cfa_projected(batch, qq, qqd, qtau,
+                                                         projection="block_jacobi", prec=prec,
+                                                         team=tv, out=o, ws=w), reps=3, warm=2)
+            variants[f"cfa_block_jacobi_{prec}"] = {"ms": ms,
+                                                    "solves_per_s": args.chains / (ms / 1e3)}
+            acc_outs[f"cfa_block_jacobi_{prec}"] = o.cpu() if prec == "fp64" else o[:n_acc].cpu()
+            del w, o
 
     # end to end through the C ABI with host buffers (pinned), copies timed: every
     # step copies its inputs host -> device and its three results device -> host.
