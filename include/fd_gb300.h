@@ -121,6 +121,27 @@ fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets,
                           const double *spatial_inertias, const double gravity[3],
                           int32_t device, fd_chain_t *out);
 
+/*
+ * fd_create_tree -- copy a set of kinematic trees (branched robots) to the
+ * device (not in the paper, whose algorithms are stated for serial chains; its
+ * future work names branched robots). Arrays as for fd_create_chain, plus
+ * parents [L] (host): the parent of each link within its tree, -1 for a link
+ * attached to the fixed base, else a link of the same tree with a smaller index
+ * (0-based within the tree; a tree's links are numbered parents first, so a
+ * tree may hold several branches and several links on the base). link_frames[i]
+ * is the home transform from the parent's frame (or the base's) to link i's.
+ * Otherwise FD_ERR_INVALID_ARG. A set of trees solves with FD_ABIA, FD_JSIIA
+ * (fd_solve_batch, FD_FP64 or FD_FP32, one thread per tree: team 0 or 1) and
+ * fd_inverse_dynamics; CFA, the ABI scan, the adjoint, the projected and static
+ * solves return FD_ERR_UNSUPPORTED (CFA's system of Eq. cfa-eq2 is block
+ * tri-diagonal only on a serial chain). parents[i] = i - 1 within every tree
+ * gives the same model as fd_create_chain. Free it with fd_destroy_chain.
+ */
+fd_status fd_create_tree(int32_t n_trees, const int64_t *link_offsets, const int32_t *parents,
+                         const double *joint_axes, const double *link_frames,
+                         const double *spatial_inertias, const double gravity[3],
+                         int32_t device, fd_chain_t *out);
+
 fd_status fd_destroy_chain(fd_chain_t chain);
 
 /* Number of chains, total links and the longest chain's link count. */

@@ -12,6 +12,8 @@ It shares no code with the CUDA path and never imports it.
   (the mass matrix of Eq. 3's definition, T, A, B, C of Eq. cfa-eq2 and
   Eq. fijany-final).
 * ``scan.py`` holds the scan formulation of a bi-diagonal system (Section II-B).
+* Kinematic trees (``fd_tree``, ``rnea_tree``): ``dense.py``'s definitions with
+  Gamma over a parent array.
 
 Parity status: every function is pinned by the CPU tests (closed forms, the
 dense definitions, energy and power balance, agreement of independent routes);
@@ -140,6 +142,33 @@ def cfa_blocks(model, q, W=None):
     if st:
         raise RuntimeError(f"oracle cfa blocks failed ({st})")
     return dict(D=D, U=U, B=Bb, Cd=Cd, Co=Co, W=Wout)
+
+
+def fd_tree(model, q, qd, tau):
+    """Forward dynamics of every kinematic tree of a packed model
+    (``model.parents``; tree p = problem p) from the dense definitions of
+    ``dense`` (Eq. 2a-2d and Eq. 3 with Gamma over the parent array, Eq. 4)."""
+    from . import dense
+    q, qd, tau = _c64(q), _c64(qd), _c64(tau)
+    out = np.full(q.shape[0], np.nan)
+    for p in range(model.n_chains):
+        a, z = int(model.offsets[p]), int(model.offsets[p + 1])
+        if z > a:
+            out[a:z] = dense.forward_dynamics(model.chain(p), q[a:z], qd[a:z], tau[a:z])
+    return out
+
+
+def rnea_tree(model, q, qd, qdd):
+    """Inverse dynamics (with gravity) of every kinematic tree of a packed model
+    from the dense Eq. 2a-2d over the parent array."""
+    from . import dense
+    q, qd, qdd = _c64(q), _c64(qd), _c64(qdd)
+    out = np.full(q.shape[0], np.nan)
+    for p in range(model.n_chains):
+        a, z = int(model.offsets[p]), int(model.offsets[p + 1])
+        if z > a:
+            out[a:z] = dense.inverse_dynamics(model.chain(p), q[a:z], qd[a:z], qdd[a:z])
+    return out
 
 
 def fd_cfa_w(model, q, qd, tau, W=None, return_fc=False):

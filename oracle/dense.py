@@ -9,6 +9,9 @@ only steps, so that the C oracle's recursions can be checked against them:
   ad term is the reading in which it equals ad_{V_i}(S_i qd_i) link by link
   (Eq. 1 and Eq. 2b disagree on the sign convention of ad).
 * Eq. 3 (definition after Eq. eq-motion): M(q) = S^T (I-Gamma)^{-T} J (I-Gamma)^{-1} S.
+* Kinematic trees (beyond the paper's serial chains): the same equations with
+  X_i in Gamma's block (i, parent(i)) and the base acceleration entering every
+  link on the base.
 * Eq. cfa-eq2 and Eq. fijany-final: T = (I-Gamma) J^{-1} (I-Gamma)^T,
   A = W^T T W, B = W^T T S, C = S^T T S, M^{-1} = C - B^T A^{-1} B.
 """
@@ -55,16 +58,25 @@ def link_operators(model, q):
     return X, S
 
 
+def parent_of(model, i):
+    """The link that link i's joint attaches to (-1: the base): i - 1 on a serial
+    chain, ``model.parents[i]`` on a kinematic tree."""
+    parents = getattr(model, "parents", None)
+    return i - 1 if parents is None else int(parents[i])
+
+
 def global_matrices(model, q):
-    """Gamma (6n x 6n, block sub-diagonal X_i), S (6n x n), J (6n x 6n)."""
+    """Gamma (6n x 6n: X_i in block row i, column parent(i); the block sub-
+    diagonal on a serial chain), S (6n x n), J (6n x 6n)."""
     n = model.axes.shape[0]
     X, S = link_operators(model, q)
     G = np.zeros((6 * n, 6 * n))
     Sg = np.zeros((6 * n, n))
     Jg = np.zeros((6 * n, 6 * n))
     for i in range(n):
-        if i > 0:
-            G[6 * i:6 * i + 6, 6 * (i - 1):6 * i] = X[i]
+        l = parent_of(model, i)
+        if l >= 0:
+            G[6 * i:6 * i + 6, 6 * l:6 * l + 6] = X[i]
         Sg[6 * i:6 * i + 6, i] = S[i]
         Jg[6 * i:6 * i + 6, 6 * i:6 * i + 6] = model.inertias[i].reshape(6, 6)
     return G, Sg, Jg, X
@@ -91,7 +103,9 @@ def inverse_dynamics(model, q, qd, qdd, gravity=None):
     for i in range(n):
         adterm[6 * i:6 * i + 6] = -_ad(Sqd[6 * i:6 * i + 6]) @ GV[6 * i:6 * i + 6]
     c = np.zeros(6 * n)
-    c[:6] = X[0] @ np.concatenate([np.zeros(3), -g])
+    for i in range(n):  # every link on the base takes the base's acceleration (0; -g)
+        if parent_of(model, i) < 0:
+            c[6 * i:6 * i + 6] = X[i] @ np.concatenate([np.zeros(3), -g])
     Vd = np.linalg.solve(I - G, S @ qdd + adterm + c)
     rhs = J @ Vd
     for i in range(n):
@@ -100,6 +114,13 @@ def inverse_dynamics(model, q, qd, qdd, gravity=None):
         rhs[6 * i:6 * i + 6] -= _ad(Vi).T @ (Ji @ Vi)
     F = np.linalg.solve((I - G).T, rhs)
     return S.T @ F
+
+
+def forward_dynamics(model, q, qd, tau):
+    """qdd = M^{-1} (tau - ID(q, qd, 0)) with M and ID from the definitions above
+    (Eq. 4), for a chain or a kinematic tree."""
+    n = model.axes.shape[0]
+    return np.linalg.solve(mass_matrix(model, q), tau - inverse_dynamics(model, q, qd, np.zeros(n)))
 
 
 def projection(model, rng=None):

@@ -132,9 +132,14 @@ int pow2_floor(long long v) {
 // rec[0 .. n*REC). Clears *rigid if an inertia is not of the rigid-body form.
 fd_status fdk_pack_chain(int64_t first, int64_t n, const double *joint_axes,
                          const double *link_frames, const double *spatial_inertias, double *rec,
-                         bool *rigid) {
-  double Qprev[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+                         bool *rigid, const int32_t *parents) {
+  // the canonical rotation of every link of this chain: a child's home
+  // transform is re-expressed between its parent's canonical frame and its own
+  std::vector<double> Qs(static_cast<size_t>(std::max<int64_t>(n, 1)) * 9);
   for (int64_t i = first; i < first + n; ++i) {
+    const int64_t par = parents ? parents[i] : i - first - 1;
+    double Qprev[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (par >= 0) std::memcpy(Qprev, Qs.data() + 9 * par, sizeof Qprev);
     const double *ax = joint_axes + 3 * i;
     const double *fr = link_frames + 12 * i;
     const double *J = spatial_inertias + 36 * i;
@@ -211,7 +216,7 @@ fd_status fdk_pack_chain(int64_t first, int64_t n, const double *joint_axes,
         rc[fdk::REC_J + s6(r, c)] = Jc[6 * r + c];
         rc[fdk::REC_JI + s6(r, c)] = 0.5 * (Ji[6 * r + c] + Ji[6 * c + r]);
       }
-    std::memcpy(Qprev, Q, sizeof Qprev);
+    std::memcpy(Qs.data() + 9 * (i - first), Q, 9 * sizeof(double));
   }
   return FD_OK;
 }
@@ -252,9 +257,11 @@ const char *fd_last_error(void) { return g_err.c_str(); }
 
 int32_t fd_abi_version(void) { return FD_ABI_VERSION; }
 
-fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const double *joint_axes,
-                          const double *link_frames, const double *spatial_inertias,
-                          const double gravity[3], int32_t device, fd_chain_t *out) {
+// fd_create_chain, and fd_create_tree with parents (validated by the caller)
+static fd_status create_set(int32_t n_chains, const int64_t *link_offsets,
+                            const int32_t *parents, const double *joint_axes,
+                            const double *link_frames, const double *spatial_inertias,
+                            const double gravity[3], int32_t device, fd_chain_t *out) {
   if (!out) return fail(FD_ERR_INVALID_ARG, "fd_create_chain: out is NULL");
   *out = nullptr;
   if (n_chains < 0) return fail(FD_ERR_INVALID_ARG, "fd_create_chain: n_chains < 0");
@@ -295,7 +302,8 @@ fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const d
         for (int32_t k = k0; k < std::min(n_chains, k0 + 256); ++k) {
           const fd_status st = fdk_pack_chain(
               link_offsets[k], link_offsets[k + 1] - link_offsets[k], joint_axes, link_frames,
-              spatial_inertias, rec64.data() + static_cast<size_t>(link_offsets[k]) * fdk::REC, &rg);
+              spatial_inertias, rec64.data() + static_cast<size_t>(link_offsets[k]) * fdk::REC, &rg,
+              parents);
           if (st != FD_OK) {
             sts[t] = st;
             msgs[t] = g_err;
@@ -345,17 +353,66 @@ fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const d
       (e = cudaMalloc(reinterpret_cast<void **>(&c->d_off), boff)) != cudaSuccess ||
       (e = cudaMemcpy(c->d_model64, rec64.data(), b64, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(c->d_model32, rec32.data(), b32, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(c->d_off, link_offsets, boff, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      (e = cudaMemcpy(c->d_off, link_offsets, boff, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (parents && L > 0 &&
+       ((e = cudaMalloc(reinterpret_cast<void **>(&c->d_parent), L * sizeof(int32_t))) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(c->d_parent, parents, L * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+            cudaSuccess))) {
     cudaFree(c->d_model64);
     cudaFree(c->d_model32);
     cudaFree(c->d_off);
+    cudaFree(c->d_parent);
     delete c;
     cudaSetDevice(prev);
     return cuda_fail(e, "fd_create_chain: device copy");
   }
+  if (parents && L == 0) {  // an empty tree set: keep it marked as trees
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&c->d_parent), sizeof(int32_t))) != cudaSuccess) {
+      cudaFree(c->d_model64);
+      cudaFree(c->d_model32);
+      cudaFree(c->d_off);
+      delete c;
+      cudaSetDevice(prev);
+      return cuda_fail(e, "fd_create_tree: device allocation");
+    }
+  }
   cudaSetDevice(prev);
   *out = c;
   return FD_OK;
+}
+
+fd_status fd_create_chain(int32_t n_chains, const int64_t *link_offsets, const double *joint_axes,
+                          const double *link_frames, const double *spatial_inertias,
+                          const double gravity[3], int32_t device, fd_chain_t *out) {
+  return create_set(n_chains, link_offsets, nullptr, joint_axes, link_frames, spatial_inertias,
+                    gravity, device, out);
+}
+
+fd_status fd_create_tree(int32_t n_trees, const int64_t *link_offsets, const int32_t *parents,
+                         const double *joint_axes, const double *link_frames,
+                         const double *spatial_inertias, const double gravity[3], int32_t device,
+                         fd_chain_t *out) {
+  if (!out) return fail(FD_ERR_INVALID_ARG, "fd_create_tree: out is NULL");
+  *out = nullptr;
+  if (n_trees < 0 || !link_offsets)
+    return fail(FD_ERR_INVALID_ARG, "fd_create_tree: n_trees < 0 or link_offsets is NULL");
+  if (link_offsets[0] != 0)
+    return fail(FD_ERR_INVALID_ARG, "fd_create_tree: link_offsets[0] must be 0");
+  for (int32_t k = 0; k < n_trees; ++k) {
+    const int64_t a = link_offsets[k], z = link_offsets[k + 1];
+    if (z < a) return fail(FD_ERR_INVALID_ARG, "fd_create_tree: tree %d has %lld links", k,
+                           static_cast<long long>(z - a));
+    if (z > a && !parents) return fail(FD_ERR_INVALID_ARG, "fd_create_tree: parents is NULL");
+    for (int64_t i = a; i < z; ++i)
+      if (parents[i] < -1 || parents[i] >= i - a)
+        return fail(FD_ERR_INVALID_ARG,
+                    "fd_create_tree: link %lld of tree %d has parent %d (need -1 <= parent < "
+                    "its own index in the tree)", static_cast<long long>(i - a), k, parents[i]);
+  }
+  static const int32_t none = 0;
+  return create_set(n_trees, link_offsets, parents ? parents : &none, joint_axes, link_frames,
+                    spatial_inertias, gravity, device, out);
 }
 
 fd_status fd_destroy_chain(fd_chain_t c) {
@@ -366,6 +423,7 @@ fd_status fd_destroy_chain(fd_chain_t c) {
   cudaFree(c->d_model64);
   cudaFree(c->d_model32);
   cudaFree(c->d_off);
+  cudaFree(c->d_parent);
   cudaSetDevice(prev);
   cudaGetLastError();  // leave no error state behind for other users of the runtime
   delete c;
@@ -507,6 +565,12 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int /*team: no l
   const size_t as = prec == FD_FP32 ? 4 : 8;
   const size_t L = static_cast<size_t>(b->n_state_links);
   WsPlan w{align256(L * fdk::NT * ts), 0};
+  if (b->chain->d_parent) {  // kinematic trees
+    if (algo == FD_ABIA) w.a_bytes = align256(L * fdk::NA_TREE * as);
+    if (algo == FD_JSIIA)
+      w.a_bytes = align256((L * fdk::NA_TREE + static_cast<size_t>(b->sum_sq)) * as);
+    return w;
+  }
   if (algo == FD_CFA || algo == FD_CFA_CR || algo == FD_CFA_HYBRID)
     w.a_bytes = L * fdk::NA_CFA * as;
   if (algo == FD_JSIIA)
@@ -606,9 +670,21 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   if (algo == FD_ABIA_SCAN && (prec != FD_FP64 || (team > 0 && !fdk::abia_scan_team_ok(team))))
     return fail(FD_ERR_UNSUPPORTED, "%s: the ABI scan runs in FP64 on teams of 8 .. 256 lanes",
                 who);
+  const bool tree = b->chain->d_parent != nullptr;
+  if (tree) {
+    if ((algo != FD_ABIA && algo != FD_JSIIA && algo != -1) || wmode != 0)
+      return fail(FD_ERR_UNSUPPORTED,
+                  "%s: kinematic trees run ABIA, JSIIA and inverse dynamics (CFA's system is "
+                  "block tri-diagonal only on a serial chain)", who);
+    if (prec == FD_MIXED)
+      return fail(FD_ERR_UNSUPPORTED, "%s: kinematic trees run in FP64 or FP32", who);
+    if (team > 1 || only_class >= 0)
+      return fail(FD_ERR_UNSUPPORTED, "%s: kinematic trees run one thread per tree (team 1)",
+                  who);
+  }
   if (b->n_problems == 0 || b->n_state_links == 0) return FD_OK;
   if (!q || !qd || !in3 || !out) return fail(FD_ERR_INVALID_ARG, "%s: NULL state array", who);
-  const int t = resolve_team(b, algo, prec, team);
+  const int t = tree ? 1 : resolve_team(b, algo, prec, team);
   const WsPlan w = ws_plan(b, algo, prec, t);
   if (!ws || ws_bytes < w.t_bytes + w.a_bytes)
     return fail(FD_ERR_INVALID_ARG, "%s: workspace of %zu bytes, %zu needed", who, ws_bytes,
@@ -635,13 +711,16 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   a.status = status;
   a.wq = wq;
   a.wmode = wmode;
+  a.parent = b->chain->d_parent;
   std::memcpy(a.grav, b->chain->grav, sizeof a.grav);
   int prev = 0;
   cudaGetDevice(&prev);
   cudaError_t e = cudaSetDevice(b->chain->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   auto s = static_cast<cudaStream_t>(stream);
-  if (wmode != 0) {
+  if (tree) {
+    e = fdk::launch_tree(a, algo == FD_ABIA ? 0 : (algo == FD_JSIIA ? 1 : -1), prec_k, s);
+  } else if (wmode != 0) {
     e = fdk::launch_cfa_w(a, prec_k, t, s);
   } else if (only_class >= 0 || use_classes(b, algo, team)) {
     std::vector<int> teams(b->classes.size());
@@ -749,6 +828,8 @@ fd_status fd_solve_cfa_projected(fd_batch_t b, const void *q, const void *qdot, 
                                  int32_t *status, void *stream) {
   const char *who = "fd_solve_cfa_projected";
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
+  if (b->chain->d_parent)
+    return fail(FD_ERR_UNSUPPORTED, "%s: serial chains only (not kinematic trees)", who);
   if (proj != FD_PROJ_CANONICAL && proj != FD_PROJ_GIVEN && proj != FD_PROJ_BLOCK_JACOBI)
     return fail(FD_ERR_INVALID_ARG, "%s: bad projection %d", who, static_cast<int>(proj));
   if (prec == FD_MIXED)
@@ -787,6 +868,8 @@ fd_status fd_solve_adjoint(fd_batch_t b, const void *q, const void *qdot, const 
                            int32_t *status, void *stream) {
   const char *who = "fd_solve_adjoint";
   if (!b) return fail(FD_ERR_INVALID_ARG, "%s: NULL batch", who);
+  if (b->chain->d_parent)
+    return fail(FD_ERR_UNSUPPORTED, "%s: serial chains only (not kinematic trees)", who);
   if (algo != FD_ABIA && algo != FD_JSIIA && algo != FD_CFA && algo != FD_CFA_CR &&
       algo != FD_CFA_HYBRID && algo != FD_ABIA_SCAN)
     return fail(FD_ERR_INVALID_ARG, "%s: bad algorithm %d", who, static_cast<int>(algo));
@@ -1021,8 +1104,12 @@ extern "C" fd_status fd_autotune(fd_batch_t b, fd_algo algo, fd_prec prec, const
     return fail(FD_ERR_UNSUPPORTED, "%s: the ABI scan runs in FP64", who);
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fail(FD_ERR_INVALID_ARG, "%s: bad precision", who);
-  if (b->n_problems == 0 || b->n_state_links == 0) {
-    if (best_team) *best_team = 1;
+  if (b->chain->d_parent && algo != FD_ABIA && algo != FD_JSIIA)
+    return fail(FD_ERR_UNSUPPORTED, "%s: kinematic trees run ABIA and JSIIA", who);
+  if (b->chain->d_parent && prec == FD_MIXED)
+    return fail(FD_ERR_UNSUPPORTED, "%s: kinematic trees run in FP64 or FP32", who);
+  if (b->n_problems == 0 || b->n_state_links == 0 || b->chain->d_parent) {
+    if (best_team) *best_team = 1;  // one thread per tree: nothing to choose
     return FD_OK;
   }
   int prev = 0;

@@ -18,6 +18,7 @@ struct fd_chain_s {
   void *d_model32 = nullptr;
   int64_t *d_off = nullptr;
   bool rigid = true;  // every inertia has the rigid-body form (mass gradients)
+  int32_t *d_parent = nullptr;  // kinematic trees: [n_links] parent within the tree; null: chains
 };
 
 struct fd_batch_s {
@@ -53,7 +54,9 @@ int fdk_default_team(int32_t algo, int64_t n_problems, int32_t max_links);
 // Team sizes the kernels are built for: powers of two from 1 to 256.
 bool fdk_valid_team(int t);
 
-// Packs one chain's model records in canonical link frames (see fd_abi.cu).
+// Packs one chain's (or tree's) model records in canonical link frames (see
+// fd_abi.cu). parents: null for a serial chain, else each link's parent within
+// its tree (-1: the base), indexed like the other arrays.
 fd_status fdk_pack_chain(int64_t first, int64_t n, const double *joint_axes,
                          const double *link_frames, const double *spatial_inertias, double *rec,
-                         bool *rigid);
+                         bool *rigid, const int32_t *parents = nullptr);

@@ -71,6 +71,10 @@ constexpr int A_UU = 7;
 constexpr int A_UU2 = 8;
 constexpr int NA_ABIA = 9;
 
+// Kinematic trees (ABIA, JSIIA): per-link TA entries (the layout is in
+// fd_tree.cuh); JSIIA adds n*n entries (M) per problem.
+constexpr int NA_TREE = 41;
+
 // Adjoint (reverse inverse dynamics) per-link workspace of T.
 constexpr int J_G = 0;    // g_i (12)
 constexpr int J_V = 12;   // V_i
@@ -139,6 +143,9 @@ struct KArgs {
   // D_i = L_i L_i^T
   const double *wq;
   int32_t wmode;
+  // kinematic trees: each link's parent within its tree (-1: the base), by the
+  // model's link index; null for serial chains
+  const int32_t *parent;
 };
 
 constexpr int WPROJ_GIVEN = 1;

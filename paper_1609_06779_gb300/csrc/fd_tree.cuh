@@ -1,0 +1,304 @@
+// Branched robots (kinematic trees): inverse dynamics, ABIA and JSIIA over a
+// parent array, one thread per tree. The paper treats serial chains only
+// (its building blocks are block bi- and tri-diagonal systems, Sections II-IV);
+// on a tree the same recursions run over each link's parent instead of link
+// i-1: the twist and acceleration recursions read the parent's values (Eq. 2a,
+// 2b), and the force, articulated-inertia and composite-inertia recursions add
+// each link's transported contribution into its parent's (Eq. 2c, Section II-C).
+// Links are numbered so that a parent precedes its children, so one ascending
+// and one descending sweep over the links visit every parent before (after) its
+// children. CFA's A stops being block tri-diagonal on a tree, so OEE has no
+// tree form here.
+#pragma once
+
+#include "fd_kernels.cuh"
+
+namespace fdk {
+
+// T workspace of a tree link (NT entries): g (12), V (6), F (6: f_i, then the
+// subtree's force as children add into it), tau_delta (1), Vd (6).
+constexpr int TW_G = 0;
+constexpr int TW_V = 12;
+constexpr int TW_F = 18;
+constexpr int TW_TD = 24;
+constexpr int TW_A = 25;
+static_assert(TW_A + 6 <= NT, "tree link record");
+
+// TA workspace of a tree link: P (21: the articulated inertia for ABIA, the
+// composite inertia for JSIIA, children adding into it), the bias force (6),
+// h = P S (6), 1 / D (1), u / D (1), the acceleration (6); JSIIA keeps its
+// right-hand side in the 1 / D slot and M after the per-link records.
+constexpr int TA_P = 0;
+constexpr int TA_PB = 21;
+constexpr int TA_H = 27;
+constexpr int TA_DD = 33;
+constexpr int TA_UU = 34;
+constexpr int TA_AC = 35;
+static_assert(TA_AC + 6 <= NA_TREE, "tree link record");
+
+// Eq. 2a-2b forward over the parent array, f_i = J_i Vd_i - ad_{V_i}^T J_i V_i,
+// then Eq. 2c-2d backward: F_i = f_i + sum over children c of Ad_{g_c^-1}^T F_c,
+// tau_i = F_i[0]. Writes tau_delta (MODE_FD: tau - tau_bias; MODE_ID: tau) to
+// TW_TD. With init_P, TA_P of every link starts as J_i and TA_PB as zero.
+template <class T, class TA>
+__device__ __forceinline__ void tree_id(const KArgs &A, const Prob<T> &pb, const int32_t *par,
+                                        TA *wa, int mode, bool init_P) {
+  const int n = pb.n;
+  const T *qdd_in = mode == MODE_ID ? pb.in3 : nullptr;
+  for (int i = 0; i < n; ++i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+    SE3<T> g;
+    joint_transform(rec, pb.q[i], g);
+    st_se3(w + TW_G, g);
+    const int l = par[i];
+    T V[6], Vd[6];
+    if (l >= 0) {
+      const T *wl = pb.wt + static_cast<int64_t>(l) * NT;
+      ldv<T, 6>(wl + TW_V, V);
+      ldv<T, 6>(wl + TW_A, Vd);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) V[k] = T(0);
+      Vd[0] = Vd[1] = Vd[2] = T(0);  // the base's acceleration (0; -g): gravity
+      Vd[3] = T(-A.grav[0]);
+      Vd[4] = T(-A.grav[1]);
+      Vd[5] = T(-A.grav[2]);
+    }
+    const T qdi = pb.qd[i];
+    adinv(g, V, V);
+    V[0] += qdi;
+    adinv(g, Vd, Vd);
+    // ad_V e_1 qd = (0, w_z, -w_y; 0, v_z, -v_y) qd
+    Vd[1] += V[2] * qdi;
+    Vd[2] -= V[1] * qdi;
+    Vd[4] += V[5] * qdi;
+    Vd[5] -= V[4] * qdi;
+    if (qdd_in) Vd[0] += qdd_in[i];
+    stv<T, 6>(w + TW_V, V);
+    stv<T, 6>(w + TW_A, Vd);
+    T JV[6], f[6];
+    sym6_apply(rec + REC_J, V, JV);
+    sym6_apply(rec + REC_J, Vd, f);
+    adT_sub(V, JV, f);
+    stv<T, 6>(w + TW_F, f);
+    if (init_P) {
+      TA *ra = wa + static_cast<int64_t>(i) * NA_TREE;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) ra[TA_P + k] = TA(rec[REC_J + k]);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) ra[TA_PB + k] = TA(0);
+    }
+  }
+  const bool fdm = mode != MODE_ID;
+  for (int i = n - 1; i >= 0; --i) {
+    T *w = pb.wt + static_cast<int64_t>(i) * NT;
+    T F[6];
+    ldv<T, 6>(w + TW_F, F);
+    w[TW_TD] = fdm ? pb.in3[i] - F[0] : F[0];
+    const int l = par[i];
+    if (l >= 0) {
+      SE3<T> g;
+      ld_se3(w + TW_G, g);
+      T t[6];
+      adinvT(g, F, t);
+      T *wl = pb.wt + static_cast<int64_t>(l) * NT;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) wl[TW_F + k] += t[k];
+    }
+  }
+}
+
+// ABIA on a tree (Section II-C over a parent array): backward, link i's
+// articulated inertia P_i (J_i plus its children's X^T Pa X) gives h = P_i S,
+// D = S^T h, u = tau_delta_i - S^T p_i, and adds X_i^T Pa_i X_i, X_i^T pa_i into
+// its parent's; forward, a_i = X_i a_parent, qdd_i = (u - h . a_i) / D,
+// a_i += S qdd_i.
+template <class T, class TA>
+__device__ __forceinline__ void tree_abia_body(const KArgs &A, const Range &rg) {
+  Team<1> tm;
+  Prob<T> pb;
+  if (!load_problem<T, 1>(A, rg, tm, pb, NT)) return;
+  const int n = pb.n;
+  const int32_t *par = A.parent + pb.m0;
+  TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_TREE;
+  bool bad = false;
+  tree_id<T, TA>(A, pb, par, wa, A.mode, true);
+  for (int i = n - 1; i >= 0; --i) {
+    TA *ra = wa + static_cast<int64_t>(i) * NA_TREE;
+    TA Pm[21], pbias[6], h[6];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Pm[k] = ra[TA_P + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pbias[k] = ra[TA_PB + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = Pm[s6(0, k)];
+    const TA D = h[0];
+    const TA u = TA(pb.wt[static_cast<int64_t>(i) * NT + TW_TD]) - pbias[0];
+    bad |= !pos_t(D);
+    const TA Dinv = rcp_t(D);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ra[TA_H + k] = h[k];
+    ra[TA_DD] = Dinv;
+    ra[TA_UU] = u * Dinv;
+    const int l = par[i];
+    if (l < 0) continue;
+    // Pa = P - h h^T / D (row and column 0 vanish), pa = p + h u / D
+    TA Pa[21], pa[6], hs[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hs[k] = h[k] * Dinv;
+#pragma unroll
+    for (int r = 1; r < 6; ++r)
+#pragma unroll
+      for (int c = r; c < 6; ++c) Pa[s6(r, c)] = Pm[s6(r, c)] - h[r] * hs[c];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pa[k] = pbias[k] + hs[k] * u;
+    SE3<TA> ga;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, ga);
+    TA *rl = wa + static_cast<int64_t>(l) * NA_TREE;
+    TA Pl[21], t[6];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Pl[k] = rl[TA_P + k];
+    congruence_add<TA, true>(ga, Pa, Pl);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) rl[TA_P + k] = Pl[k];
+    adinvT(ga, pa, t);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rl[TA_PB + k] += t[k];
+  }
+  for (int i = 0; i < n; ++i) {
+    TA *ra = wa + static_cast<int64_t>(i) * NA_TREE;
+    SE3<TA> ga;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, ga);
+    TA acc[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    const int l = par[i];
+    if (l >= 0) {
+      const TA *al = wa + static_cast<int64_t>(l) * NA_TREE + TA_AC;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] = al[k];
+      adinv(ga, acc, acc);
+    }
+    TA s = TA(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s += ra[TA_H + k] * acc[k];
+    const TA qdd = ra[TA_UU] - s * ra[TA_DD];
+    acc[0] += qdd;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ra[TA_AC + k] = acc[k];
+    const T v = T(qdd);
+    pb.out[i] = v;
+    if (!finite_t(v)) bad = true;
+  }
+  set_status(A.status, pb.p, bad ? 2 : 0);
+}
+
+// JSIIA on a tree (Section II-C over a parent array): composite inertias
+// I^c_i = J_i + sum over children c of X_c^T I^c_c X_c (backward), then
+// M[i][j] = S_j^T X_{j'}^T ... X_i^T I^c_i S_i for every ancestor j of i (the
+// composite force of i's subtree carried up the path to j; zero off the paths),
+// a dense Cholesky factor of M and two triangular solves.
+template <class T, class TA>
+__device__ __forceinline__ void tree_jsiia_body(const KArgs &A, const Range &rg) {
+  Team<1> tm;
+  Prob<T> pb;
+  if (!load_problem<T, 1>(A, rg, tm, pb, NT)) return;
+  const int n = pb.n;
+  const int32_t *par = A.parent + pb.m0;
+  const int64_t s0 = A.state_off[pb.p];
+  TA *wa = static_cast<TA *>(A.ws_a) + s0 * NA_TREE + A.sq_off[pb.p];
+  TA *M = wa + static_cast<int64_t>(n) * NA_TREE;  // n x n, column-major, lower triangle
+  auto Mat = [&](int i, int j) -> TA & { return M[static_cast<int64_t>(j) * n + i]; };
+  bool bad = false;
+  tree_id<T, TA>(A, pb, par, wa, A.mode, true);
+  for (int i = n - 1; i >= 0; --i) {
+    TA *ra = wa + static_cast<int64_t>(i) * NA_TREE;
+    TA Pm[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Pm[k] = ra[TA_P + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ra[TA_H + k] = Pm[s6(0, k)];
+    ra[TA_DD] = TA(pb.wt[static_cast<int64_t>(i) * NT + TW_TD]);  // the right-hand side
+    const int l = par[i];
+    if (l < 0) continue;
+    SE3<TA> ga;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, ga);
+    TA *rl = wa + static_cast<int64_t>(l) * NA_TREE;
+    TA Pl[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Pl[k] = rl[TA_P + k];
+    congruence_add<TA>(ga, Pm, Pl);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) rl[TA_P + k] = Pl[k];
+  }
+  for (int j = 0; j < n; ++j)
+    for (int i = j; i < n; ++i) Mat(i, j) = TA(0);
+  for (int i = 0; i < n; ++i) {
+    TA F[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) F[k] = wa[static_cast<int64_t>(i) * NA_TREE + TA_H + k];
+    Mat(i, i) = F[0];
+    for (int j = i; par[j] >= 0;) {
+      SE3<TA> ga;
+      ld_se3(pb.wt + static_cast<int64_t>(j) * NT + TW_G, ga);
+      adinvT(ga, F, F);
+      j = par[j];
+      Mat(i, j) = F[0];
+    }
+  }
+  // M = L L^T (left-looking by columns; 1 / L_jj kept in the h slot)
+  for (int j = 0; j < n; ++j) {
+    TA d = Mat(j, j);
+    for (int k = 0; k < j; ++k) d -= Mat(j, k) * Mat(j, k);
+    bad |= !pos_t(d);
+    const TA r = rsqrt_t(d);
+    wa[static_cast<int64_t>(j) * NA_TREE + TA_H] = r;  // L_jj itself is never read
+    for (int i = j + 1; i < n; ++i) {
+      TA x = Mat(i, j);
+      for (int k = 0; k < j; ++k) x -= Mat(i, k) * Mat(j, k);
+      Mat(i, j) = x * r;
+    }
+  }
+  // L y = b, L^T x = y, in the right-hand side slot
+  for (int i = 0; i < n; ++i) {
+    TA x = wa[static_cast<int64_t>(i) * NA_TREE + TA_DD];
+    for (int k = 0; k < i; ++k) x -= Mat(i, k) * wa[static_cast<int64_t>(k) * NA_TREE + TA_DD];
+    wa[static_cast<int64_t>(i) * NA_TREE + TA_DD] = x * wa[static_cast<int64_t>(i) * NA_TREE + TA_H];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    TA x = wa[static_cast<int64_t>(i) * NA_TREE + TA_DD];
+    for (int k = i + 1; k < n; ++k) x -= Mat(k, i) * wa[static_cast<int64_t>(k) * NA_TREE + TA_DD];
+    x *= wa[static_cast<int64_t>(i) * NA_TREE + TA_H];
+    wa[static_cast<int64_t>(i) * NA_TREE + TA_DD] = x;
+    const T v = T(x);
+    pb.out[i] = v;
+    if (!finite_t(v)) bad = true;
+  }
+  set_status(A.status, pb.p, bad ? 2 : 0);
+}
+
+// Inverse dynamics alone (MODE_ID): tau = ID(q, qd, qdd) on a tree.
+template <class T>
+__device__ __forceinline__ void tree_id_body(const KArgs &A, const Range &rg) {
+  Team<1> tm;
+  Prob<T> pb;
+  if (!load_problem<T, 1>(A, rg, tm, pb, NT)) return;
+  tree_id<T, T>(A, pb, A.parent + pb.m0, static_cast<T *>(nullptr), MODE_ID, false);
+  for (int i = 0; i < pb.n; ++i) pb.out[i] = pb.wt[static_cast<int64_t>(i) * NT + TW_TD];
+}
+
+template <class T, class TA>
+__global__ void __launch_bounds__(128, 4) tree_abia_kernel(KArgs A) {
+  tree_abia_body<T, TA>(A, Range{0, 0, A.n_problems});
+}
+
+template <class T, class TA>
+__global__ void __launch_bounds__(128, 4) tree_jsiia_kernel(KArgs A) {
+  tree_jsiia_body<T, TA>(A, Range{0, 0, A.n_problems});
+}
+
+template <class T>
+__global__ void __launch_bounds__(128, 4) tree_id_kernel(KArgs A) {
+  tree_id_body<T>(A, Range{0, 0, A.n_problems});
+}
+
+}  // namespace fdk

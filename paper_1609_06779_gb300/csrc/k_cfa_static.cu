@@ -56,6 +56,8 @@ extern "C" fd_status fd_solve_cfa_static(fd_chain_t chain, const void *q, const 
                                          const void *tau, void *qddot, fd_prec prec,
                                          int32_t team, int32_t *status, void *stream) {
   if (!chain) return fdk_fail(FD_ERR_INVALID_ARG, "fd_solve_cfa_static: NULL chain");
+  if (chain->d_parent)
+    return fdk_fail(FD_ERR_UNSUPPORTED, "fd_solve_cfa_static: serial chains only (not trees)");
   if (prec != FD_FP64 && prec != FD_FP32 && prec != FD_MIXED)
     return fdk_fail(FD_ERR_INVALID_ARG, "fd_solve_cfa_static: bad precision");
   if (team < 0 || (team > 0 && !fdk_valid_team(team)))

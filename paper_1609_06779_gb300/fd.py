@@ -55,6 +55,8 @@ def load(build_if_missing: bool = True):
         lib.fd_last_error.restype = ctypes.c_char_p
         lib.fd_abi_version.restype = i32
         lib.fd_create_chain.argtypes = [i32, i64p, dp, dp, dp, dp, i32, ctypes.POINTER(vp)]
+        lib.fd_create_tree.argtypes = [i32, i64p, i32p, dp, dp, dp, dp, i32,
+                                       ctypes.POINTER(vp)]
         lib.fd_destroy_chain.argtypes = [vp]
         lib.fd_chain_info.argtypes = [vp, i32p, i64p, i32p]
         lib.fd_batch_create.argtypes = [vp, i32, i32p, ctypes.POINTER(vp)]
@@ -82,7 +84,7 @@ def load(build_if_missing: bool = True):
         lib.fd_autotune_cache_load.argtypes = [ctypes.c_char_p, i32p]
         lib.fd_autotune_cache_save.argtypes = [ctypes.c_char_p]
         lib.fd_autotune_cache_clear.argtypes = []
-        for f in ("fd_create_chain", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
+        for f in ("fd_create_chain", "fd_create_tree", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
                   "fd_batch_destroy", "fd_batch_info", "fd_solve_batch", "fd_inverse_dynamics",
                   "fd_solve_cfa_static", "fd_projection_to_canonical",
                   "fd_solve_cfa_projected", "fd_batch_classes", "fd_autotune_cache_load",
@@ -102,7 +104,9 @@ def _dptr(a: np.ndarray):
 
 
 class ChainSet:
-    """A set of serial chains resident on one GPU (fd_create_chain)."""
+    """A set of serial chains resident on one GPU (fd_create_chain), or of
+    kinematic trees when ``model.parents`` is set (fd_create_tree: each link's
+    parent within its tree, -1 for the base)."""
 
     def __init__(self, model, device: int = 0):
         lib = load()
@@ -113,10 +117,22 @@ class ChainSet:
         J = np.ascontiguousarray(model.inertias, dtype=np.float64)
         g = np.ascontiguousarray(model.gravity, dtype=np.float64)
         h = ctypes.c_void_p()
-        _check(lib.fd_create_chain(int(off.shape[0] - 1),
-                                   off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                   _dptr(ax), _dptr(fr), _dptr(J), _dptr(g), int(device),
-                                   ctypes.byref(h)))
+        parents = getattr(model, "parents", None)
+        if parents is None:
+            _check(lib.fd_create_chain(int(off.shape[0] - 1),
+                                       off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       _dptr(ax), _dptr(fr), _dptr(J), _dptr(g), int(device),
+                                       ctypes.byref(h)))
+        else:
+            par = np.ascontiguousarray(parents, dtype=np.int32)
+            if par.shape != (int(off[-1]),):
+                raise FDError(1, f"parents: need {int(off[-1])} entries, got {par.shape}")
+            _check(lib.fd_create_tree(int(off.shape[0] - 1),
+                                      off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      par.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      _dptr(ax), _dptr(fr), _dptr(J), _dptr(g), int(device),
+                                      ctypes.byref(h)))
+        self.is_tree = parents is not None
         self.handle = h
         self.device = device
         self.offsets = off.copy()

@@ -27,6 +27,10 @@ Distributions (one seed, drawn in this order for the whole batch of L links):
   8. homerot   L x 4  standard normal, normalised (only drawn when
                        ``random_home_rotation``; else every home rotation is I).
 States: q ~ U[-pi, pi], qdot ~ N(0, 1), tau ~ N(0, 10^2), drawn in that order.
+Kinematic trees (``random_trees``): the same links, joined by a parent array
+drawn from seed + 1 (``random_parents``: a link continues the previous link's
+branch, or branches off a uniformly drawn earlier link with probability 0.3, or
+starts on the base with probability 0.05).
 Chain lengths for uneven batches: n = round(exp(U[ln lo, ln hi])) clamped to
 [lo, hi].
 """
@@ -46,6 +50,7 @@ class ChainModel:
     inertias: np.ndarray    # [L, 36]
     offsets: np.ndarray     # [K + 1] int64
     gravity: np.ndarray     # [3]
+    parents: np.ndarray | None = None  # kinematic trees: [L] int32 parent within the tree
 
     @property
     def n_chains(self) -> int:
@@ -62,7 +67,8 @@ class ChainModel:
         a, b = int(self.offsets[k]), int(self.offsets[k + 1])
         return ChainModel(self.axes[a:b].copy(), self.frames[a:b].copy(),
                           self.inertias[a:b].copy(),
-                          np.array([0, b - a], dtype=np.int64), self.gravity.copy())
+                          np.array([0, b - a], dtype=np.int64), self.gravity.copy(),
+                          None if self.parents is None else self.parents[a:b].copy())
 
 
 @dataclass
@@ -153,6 +159,42 @@ def random_chains(lengths, seed: int = 0, random_home_rotation: bool = False,
     return ChainModel(axes=np.ascontiguousarray(axes), frames=frames,
                       inertias=np.ascontiguousarray(J.reshape(L, 36)),
                       offsets=off, gravity=np.asarray(gravity, dtype=np.float64).copy())
+
+
+def random_parents(lengths, seed: int = 0, p_branch: float = 0.3, p_base: float = 0.05):
+    """Parent arrays of kinematic trees with the given link counts (links
+    numbered parents first): link 0 sits on the base; link i > 0 continues the
+    branch of link i-1, or with probability ``p_branch`` branches off a uniformly
+    drawn earlier link, or with probability ``p_base`` starts a new branch on the
+    base. One uniform draw per link, in link order, from its own stream."""
+    if np.isscalar(lengths):
+        lengths = [int(lengths)]
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in lengths:
+        n = int(n)
+        u = rng.uniform(size=max(n, 1))
+        v = rng.uniform(size=max(n, 1))
+        par = np.empty(n, dtype=np.int32)
+        for i in range(n):
+            if i == 0 or u[i] < p_base:
+                par[i] = -1
+            elif u[i] < p_base + p_branch:
+                par[i] = int(v[i] * i)  # an earlier link, uniformly
+            else:
+                par[i] = i - 1
+        out.append(par)
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.int32)
+
+
+def random_trees(lengths, seed: int = 0, random_home_rotation: bool = False,
+                 gravity=GRAVITY, p_branch: float = 0.3, p_base: float = 0.05) -> ChainModel:
+    """Kinematic trees: the links of :func:`random_chains` (same draws, same
+    seed) joined by :func:`random_parents` (seed + 1)."""
+    m = random_chains(lengths, seed=seed, random_home_rotation=random_home_rotation,
+                      gravity=gravity)
+    m.parents = random_parents(m.lengths(), seed=seed + 1, p_branch=p_branch, p_base=p_base)
+    return m
 
 
 def random_states(n_links_total: int, seed: int = 0, qdot_std: float = 1.0,

@@ -172,3 +172,26 @@ def test_projection_to_canonical(lib):
     with pytest.raises(fd.FDError, match="rank"):
         fd.projection_to_canonical(model.axes, low)
     assert fd.projection_to_canonical(np.zeros((0, 3)), np.zeros((0, 6, 5))).shape == (0, 5, 5)
+
+
+def test_create_tree_validates_parents_before_any_device_call(lib):
+    """fd_create_tree: each link's parent must be -1 or an earlier link of the
+    same tree; a NULL parent array with links is rejected."""
+    m = synth.random_chains([4, 3], seed=2)
+    off = np.ascontiguousarray(m.offsets, dtype=np.int64)
+    dp = lambda a: np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(
+        ctypes.POINTER(ctypes.c_double))
+
+    def create(parents):
+        h = ctypes.c_void_p()
+        par = None if parents is None else np.ascontiguousarray(parents, dtype=np.int32)
+        return lib.fd_create_tree(2, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  None if par is None else par.ctypes.data_as(
+                                      ctypes.POINTER(ctypes.c_int32)),
+                                  dp(m.axes), dp(m.frames), dp(m.inertias), dp(m.gravity), 0,
+                                  ctypes.byref(h))
+    assert create([-1, 0, 1, 3, -1, 0, 0]) == 1      # link 3 is its own parent
+    assert create([-1, 0, 1, 1, -1, 0, 5]) == 1      # parent beyond the link
+    assert create([-1, 0, -2, 1, -1, 0, 0]) == 1     # parent below -1
+    assert create(None) == 1
+    assert b"parent" in lib.fd_last_error()

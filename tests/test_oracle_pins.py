@@ -468,3 +468,123 @@ def test_batch_and_shared_model_layouts():
         sl = slice(5 * p, 5 * p + 5)
         np.testing.assert_allclose(out[sl], oracle.fd(one, s2.q[sl], s2.qdot[sl], s2.tau[sl]),
                                    rtol=1e-10)
+
+
+# ------------------------------------------------------------ kinematic trees
+
+def _tree_world(model, q):
+    """World rotation and position of every link of one tree by forward
+    kinematics over the parent array, written here."""
+    n = model.axes.shape[0]
+    Rw, pw = [None] * n, [None] * n
+    for i in range(n):
+        a = model.axes[i]
+        K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+        Rq = np.eye(3) + np.sin(q[i]) * K + (1 - np.cos(q[i])) * K @ K
+        R0 = model.frames[i, :9].reshape(3, 3)
+        l = int(model.parents[i])
+        Rl, pl = (np.eye(3), np.zeros(3)) if l < 0 else (Rw[l], pw[l])
+        pw[i] = pl + Rl @ model.frames[i, 9:]
+        Rw[i] = Rl @ R0 @ Rq
+    return Rw, pw
+
+
+def _tree_potential(model, q):
+    Rw, pw = _tree_world(model, q)
+    U = 0.0
+    for i in range(model.axes.shape[0]):
+        m, c = _com_of(model.inertias[i].reshape(6, 6))
+        U -= m * model.gravity @ (pw[i] + Rw[i] @ c)
+    return U
+
+
+def _tree_kinetic(model, q, qd):
+    """1/2 sum V_i^T J_i V_i with each link's twist (omega; v) in its own frame
+    from the world velocities of forward kinematics (omega_i = omega_parent +
+    R_i a_i qd_i, v of the frame origin by the rigid-body transport)."""
+    Rw, pw = _tree_world(model, q)
+    n = model.axes.shape[0]
+    w_w, v_w = [None] * n, [None] * n
+    T = 0.0
+    for i in range(n):
+        l = int(model.parents[i])
+        wl, vl, pl = (np.zeros(3), np.zeros(3), np.zeros(3)) if l < 0 else (w_w[l], v_w[l], pw[l])
+        w_w[i] = wl + Rw[i] @ model.axes[i] * qd[i]
+        v_w[i] = vl + np.cross(wl, pw[i] - pl)   # the joint sits at the link origin
+        V = np.concatenate([Rw[i].T @ w_w[i], Rw[i].T @ v_w[i]])
+        T += 0.5 * V @ model.inertias[i].reshape(6, 6) @ V
+    return T
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tree_chain_special_case(seed):
+    """parents = i - 1 is the serial chain: the tree definitions reproduce the
+    chain oracle's recursions (inverse dynamics, forward dynamics)."""
+    model = synth.random_chains([6, 4], seed=seed, random_home_rotation=True)
+    st = synth.random_states(model.n_links_total, seed=seed + 3)
+    tree = synth.random_chains([6, 4], seed=seed, random_home_rotation=True)
+    tree.parents = np.concatenate([np.arange(n) - 1 for n in tree.lengths()]).astype(np.int32)
+    np.testing.assert_allclose(oracle.fd_tree(tree, st.q, st.qdot, st.tau),
+                               oracle.fd(model, st.q, st.qdot, st.tau), rtol=1e-9, atol=1e-9)
+    qdd = np.random.default_rng(seed).standard_normal(model.n_links_total)
+    ref = np.concatenate([oracle.rnea(model.chain(p), st.q[a:z], st.qdot[a:z], qdd[a:z])
+                          for p, (a, z) in enumerate(zip(model.offsets[:-1], model.offsets[1:]))])
+    np.testing.assert_allclose(oracle.rnea_tree(tree, st.q, st.qdot, qdd), ref, rtol=1e-10,
+                               atol=1e-10 * np.abs(ref).max())
+
+
+def test_tree_of_two_branches_on_the_base_is_two_chains():
+    """Two serial branches both on the base are two independent chains: M is
+    block diagonal with the chains' mass matrices, qdd the chains' results."""
+    c = synth.random_chains([4, 3], seed=9)
+    st = synth.random_states(7, seed=10)
+    tree = synth.ChainModel(c.axes, c.frames, c.inertias, np.array([0, 7], dtype=np.int64),
+                            c.gravity, np.array([-1, 0, 1, 2, -1, 4, 5], dtype=np.int32))
+    M = dense.mass_matrix(tree, st.q)
+    np.testing.assert_allclose(M[:4, :4], oracle.mass_matrix(c.chain(0), st.q[:4]), rtol=1e-10)
+    np.testing.assert_allclose(M[4:, 4:], oracle.mass_matrix(c.chain(1), st.q[4:]), rtol=1e-10)
+    assert np.abs(M[:4, 4:]).max() == 0.0
+    np.testing.assert_allclose(oracle.fd_tree(tree, st.q, st.qdot, st.tau),
+                               oracle.fd(c, st.q, st.qdot, st.tau), rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tree_mass_matrix_is_kinetic_energy(seed):
+    """1/2 qd^T M qd equals the kinetic energy of the links' twists from forward
+    kinematics over the parent array; M is symmetric positive definite and
+    zero between links on different paths to the base."""
+    tree = synth.random_trees([12], seed=seed, random_home_rotation=True)
+    assert len(set(tree.parents.tolist())) < 12  # it branches
+    st = synth.random_states(12, seed=seed + 5)
+    M = dense.mass_matrix(tree, st.q)
+    np.testing.assert_allclose(0.5 * st.qdot @ M @ st.qdot, _tree_kinetic(tree, st.q, st.qdot),
+                               rtol=1e-10)
+    np.testing.assert_allclose(M, M.T, atol=1e-12)
+    assert np.linalg.eigvalsh(M).min() > 0
+    anc = [set() for _ in range(12)]
+    for i in range(12):
+        l = int(tree.parents[i])
+        anc[i] = ({l} | anc[l]) if l >= 0 else set()
+    for i in range(12):
+        for j in range(12):
+            if i != j and j not in anc[i] and i not in anc[j]:
+                assert M[i, j] == 0.0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tree_power_balance(seed):
+    """qd . tau_bias = 1/2 qd^T dM/dt qd + dU/dt on a tree, U by forward
+    kinematics over the parent array (central differences along qd)."""
+    tree = synth.random_trees([9], seed=seed + 4)
+    st = synth.random_states(9, seed=seed + 11)
+    q, qd = st.q, st.qdot
+    bias = oracle.rnea_tree(tree, q, qd, np.zeros(9))
+    h = 1e-6
+    dM = (dense.mass_matrix(tree, q + h * qd) - dense.mass_matrix(tree, q - h * qd)) / (2 * h)
+    dU = (_tree_potential(tree, q + h * qd) - _tree_potential(tree, q - h * qd)) / (2 * h)
+    assert qd @ bias == pytest.approx(0.5 * qd @ dM @ qd + dU, rel=1e-6, abs=1e-6)
+    # gravity alone: the bias at rest is the gradient of U
+    g = oracle.rnea_tree(tree, q, np.zeros(9), np.zeros(9))
+    grad = np.array([(_tree_potential(tree, q + h * e) - _tree_potential(tree, q - h * e)) / (2 * h)
+                     for e in np.eye(9)])
+    np.testing.assert_allclose(g, grad, rtol=1e-6, atol=1e-6)
