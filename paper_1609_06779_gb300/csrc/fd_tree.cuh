@@ -196,7 +196,7 @@ __device__ __forceinline__ void tree_abia_body(const KArgs &A, const Range &rg) 
 // I^c_i = J_i + sum over children c of X_c^T I^c_c X_c (backward), then
 // M[i][j] = S_j^T X_{j'}^T ... X_i^T I^c_i S_i for every ancestor j of i (the
 // composite force of i's subtree carried up the path to j; zero off the paths),
-// a dense Cholesky factor of M and two triangular solves.
+// M = L^T L without fill-in and two triangular solves along the same paths.
 template <class T, class TA>
 __device__ __forceinline__ void tree_jsiia_body(const KArgs &A, const Range &rg) {
   Team<1> tm;
@@ -230,8 +230,7 @@ __device__ __forceinline__ void tree_jsiia_body(const KArgs &A, const Range &rg)
 #pragma unroll
     for (int k = 0; k < 21; ++k) rl[TA_P + k] = Pl[k];
   }
-  for (int j = 0; j < n; ++j)
-    for (int i = j; i < n; ++i) Mat(i, j) = TA(0);
+  // entries on the paths to the base only: the factorisation below reads no other
   for (int i = 0; i < n; ++i) {
     TA F[6];
 #pragma unroll
@@ -245,30 +244,33 @@ __device__ __forceinline__ void tree_jsiia_body(const KArgs &A, const Range &rg)
       Mat(i, j) = F[0];
     }
   }
-  // M = L L^T (left-looking by columns; 1 / L_jj kept in the h slot)
-  for (int j = 0; j < n; ++j) {
-    TA d = Mat(j, j);
-    for (int k = 0; k < j; ++k) d -= Mat(j, k) * Mat(j, k);
+  // M = L^T L factored from the leaves (row k of L has entries only at k's
+  // ancestors, as M does: no fill-in; on a serial chain it is the Cholesky
+  // factor of M with the links in reverse order). 1 / L_kk is kept in the h slot.
+  for (int k = n - 1; k >= 0; --k) {
+    const TA d = Mat(k, k);
     bad |= !pos_t(d);
     const TA r = rsqrt_t(d);
-    wa[static_cast<int64_t>(j) * NA_TREE + TA_H] = r;  // L_jj itself is never read
-    for (int i = j + 1; i < n; ++i) {
-      TA x = Mat(i, j);
-      for (int k = 0; k < j; ++k) x -= Mat(i, k) * Mat(j, k);
-      Mat(i, j) = x * r;
+    wa[static_cast<int64_t>(k) * NA_TREE + TA_H] = r;  // L_kk itself is never read
+    for (int i = par[k]; i >= 0; i = par[i]) Mat(k, i) *= r;
+    for (int i = par[k]; i >= 0; i = par[i]) {
+      const TA lki = Mat(k, i);
+      for (int j = i; j >= 0; j = par[j]) Mat(i, j) -= lki * Mat(k, j);
     }
   }
-  // L y = b, L^T x = y, in the right-hand side slot
-  for (int i = 0; i < n; ++i) {
-    TA x = wa[static_cast<int64_t>(i) * NA_TREE + TA_DD];
-    for (int k = 0; k < i; ++k) x -= Mat(i, k) * wa[static_cast<int64_t>(k) * NA_TREE + TA_DD];
-    wa[static_cast<int64_t>(i) * NA_TREE + TA_DD] = x * wa[static_cast<int64_t>(i) * NA_TREE + TA_H];
-  }
+  // L^T y = b from the leaves, then L x = y from the base, in the right-hand
+  // side slot
+  auto rhs = [&](int i) -> TA & { return wa[static_cast<int64_t>(i) * NA_TREE + TA_DD]; };
   for (int i = n - 1; i >= 0; --i) {
-    TA x = wa[static_cast<int64_t>(i) * NA_TREE + TA_DD];
-    for (int k = i + 1; k < n; ++k) x -= Mat(k, i) * wa[static_cast<int64_t>(k) * NA_TREE + TA_DD];
+    const TA y = rhs(i) * wa[static_cast<int64_t>(i) * NA_TREE + TA_H];
+    rhs(i) = y;
+    for (int j = par[i]; j >= 0; j = par[j]) rhs(j) -= Mat(i, j) * y;
+  }
+  for (int i = 0; i < n; ++i) {
+    TA x = rhs(i);
+    for (int j = par[i]; j >= 0; j = par[j]) x -= Mat(i, j) * rhs(j);
     x *= wa[static_cast<int64_t>(i) * NA_TREE + TA_H];
-    wa[static_cast<int64_t>(i) * NA_TREE + TA_DD] = x;
+    rhs(i) = x;
     const T v = T(x);
     pb.out[i] = v;
     if (!finite_t(v)) bad = true;
