@@ -505,6 +505,32 @@ def extra_configs(dev, keep=None):
     ru["adjoint_solves_per_s"] = 100000 / (adj_ms * 1e-3)
     res["100000_uneven_6_512_mixed"] = ru
     keep.append(ku)
+    del cs, b, q, qd, tau, w
+    torch.cuda.empty_cache()
+
+    # kinematic trees (fd_create_tree; branched robots, beyond the paper's serial
+    # chains): 65 536 random trees of 32 links, ABIA and JSIIA over the parent
+    # array, one thread per tree, FP64; the first 256 trees against the oracle
+    m = synth.random_trees([32] * 65536, seed=0)
+    st = synth.random_states(m.n_links_total, seed=1000)
+    cs = fd.ChainSet(m, device=dev.index or 0)
+    b = fd.Batch(cs)
+    q, qd, tau = t64(st.q), t64(st.qdot), t64(st.tau)
+    local = np.concatenate([np.arange(32) - 1] * 65536)
+    rt = {"trees": 65536, "links": 32,
+          "branching_links": int((m.parents != local).sum()),
+          "links_on_the_base": int((m.parents < 0).sum())}
+    kt = {"config": "65536_trees_32_links_fp64", "model": m, "st": st, "tree": True,
+          "chain_index": None, "problems": list(range(256)), "outs": {}}
+    for a in ("abia", "jsiia"):
+        ws = fd.workspace(b, a, "fp64", 1, dev)
+        out = torch.empty_like(q)
+        ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo=a, out=out, ws=ws), 5, 2)
+        kt["outs"][a] = out[:256 * 32].cpu().numpy()
+        rt[a] = {"team": 1, "ms": ms, "solves_per_s": 65536 / (ms * 1e-3)}
+        del ws, out
+    res["65536_trees_32_links_fp64"] = rt
+    keep.append(kt)
     return res
 
 
@@ -517,6 +543,30 @@ def config_accuracy(keep):
     out = {}
     for k in keep:
         m, st = k["model"], k["st"]
+        if k.get("tree"):
+            # kinematic trees: the oracle's dense definitions over the parent
+            # array (one route, one core) on the first sampled trees
+            probs = k["problems"]
+            z = int(m.offsets[len(probs)])
+            sub = synth.ChainModel(m.axes[:z], m.frames[:z], m.inertias[:z],
+                                   m.offsets[:len(probs) + 1].copy(), m.gravity, m.parents[:z])
+            t0 = time.perf_counter()
+            ref = oracle.fd_tree(sub, st.q[:z], st.qdot[:z], st.tau[:z])
+            t1 = time.perf_counter()
+            r = {"sampled_problems": len(probs),
+                 "cpu_oracle": {"kind": "oracle (dense definitions over the parent array)",
+                                "cores": 1, "problems": len(probs),
+                                "dense_solves_per_s": len(probs) / max(t1 - t0, 1e-9),
+                                "sample": f"the first {len(probs)} of {m.n_chains} trees, FP64"}}
+            for name, x in k["outs"].items():
+                e = 0.0
+                for p in range(len(probs)):
+                    a, b = int(m.offsets[p]), int(m.offsets[p + 1])
+                    e = max(e, float(np.abs(x[a:b] - ref[a:b]).max()
+                                     / max(np.abs(ref[a:b]).max(), 1.0)))
+                r[name] = e
+            out[k["config"]] = r
+            continue
         ci = k["chain_index"]
         probs = k["problems"]
         n_prob = len(ci) if ci is not None else m.n_chains
