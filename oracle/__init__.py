@@ -158,6 +158,23 @@ def fd_tree(model, q, qd, tau):
     return out
 
 
+def fd_looped(model, q, qd, tau, loops):
+    """Forward dynamics of kinematic trees closed by revolute loop joints
+    (``loops`` as ``synth.random_loops`` returns; tree p = problem p): the KKT
+    system of ``dense.forward_dynamics_looped`` per tree."""
+    from . import dense
+    q, qd, tau = _c64(q), _c64(qd), _c64(tau)
+    out = np.full(q.shape[0], np.nan)
+    for p in range(model.n_chains):
+        a, z = int(model.offsets[p]), int(model.offsets[p + 1])
+        if z == a:
+            continue
+        sel = np.nonzero(np.asarray(loops["tree"]) == p)[0]
+        lp = {k: np.asarray(loops[k])[sel] for k in ("a", "b", "frame_a", "frame_b")}
+        out[a:z] = dense.forward_dynamics_looped(model.chain(p), q[a:z], qd[a:z], tau[a:z], lp)
+    return out
+
+
 def rnea_tree(model, q, qd, qdd):
     """Inverse dynamics (with gravity) of every kinematic tree of a packed model
     from the dense Eq. 2a-2d over the parent array."""

@@ -160,3 +160,94 @@ def fd_cfa(model, q, qd, tau, W=None):
     td = tau - inverse_dynamics(model, q, qd, np.zeros_like(q))
     Fc = np.linalg.solve(m["A"], -m["B"] @ td)
     return m["C"] @ td + m["B"].T @ Fc
+
+
+# ------------------------------------------------------ closed kinematic loops
+
+def _pose(R, p):
+    T = np.eye(4)
+    T[:3, :3], T[:3, 3] = R, p
+    return T
+
+
+def world_poses(model, q):
+    """Pose of every link frame in the base frame (4 x 4), by composing each
+    link's home transform and joint rotation onto its parent's pose."""
+    n = model.axes.shape[0]
+    out = []
+    for i in range(n):
+        fr = model.frames[i]
+        gi = _pose(fr[:9].reshape(3, 3) @ _rot(model.axes[i], q[i]), fr[9:])
+        l = parent_of(model, i)
+        out.append(gi if l < 0 else out[l] @ gi)
+    return out
+
+
+def _ancestors_or_self(model, i):
+    path = []
+    while i >= 0:
+        path.append(i)
+        i = parent_of(model, i)
+    return path
+
+
+def loop_constraints(model, q, qd, loops):
+    """Constraint rows of revolute loop joints closing a tree (beyond the
+    paper). Loop k joins frame F_a (pose loops["frame_a"][k] in link a's frame,
+    a = -1: the base) and frame F_b (loops["frame_b"][k] in link b's frame) by a
+    revolute joint about their x axes: the relative twist
+    V_rel = V_Fb - Ad_{g_{Fb<-Fa}} V_Fa (body twist of F_b relative to F_a, in F_b
+    coordinates) may only turn about x, so components 1..5 vanish. Returns G
+    (5K x n) with V_rel[1..5] = G qd, and gamma (5K) = (dG/dt) qd, the velocity
+    product of the constraint acceleration G qdd + gamma = 0, both from world
+    quantities: with s_j = Ad_{g_0j} S_j (joint axes as world twists) and the
+    links' world twists V^s_j = sum over j's path of s_i qd_i,
+      V_rel = Ad_{g_0Fb^{-1}} (V^s_b - V^s_a),
+      d/dt V_rel|_{qdd=0} = -ad_{V_Fb} V_rel + Ad_{g_0Fb^{-1}} sum +-ad_{V^s_j} s_j qd_j."""
+    n = model.axes.shape[0]
+    g0 = world_poses(model, q)
+    s = []
+    for j in range(n):
+        R, p = g0[j][:3, :3], g0[j][:3, 3]
+        w = R @ model.axes[j]
+        s.append(np.concatenate([w, np.cross(p, w)]))
+    Vs = [None] * n
+    for j in range(n):
+        l = parent_of(model, j)
+        Vs[j] = (np.zeros(6) if l < 0 else Vs[l]) + s[j] * qd[j]
+    K = len(loops["a"])
+    G = np.zeros((5 * K, n))
+    gamma = np.zeros(5 * K)
+    for k in range(K):
+        a, b = int(loops["a"][k]), int(loops["b"][k])
+        Ta, Tb = loops["frame_a"][k], loops["frame_b"][k]
+        gFb = g0[b] @ _pose(Tb[:9].reshape(3, 3), Tb[9:])
+        Rb, pb = gFb[:3, :3], gFb[:3, 3]
+        AdInv = _Ad(Rb.T, -Rb.T @ pb)
+        Gf = np.zeros((6, n))
+        drift = np.zeros(6)
+        for sign, link in ((1.0, b), (-1.0, a)):
+            for j in _ancestors_or_self(model, link):
+                Gf[:, j] += sign * s[j]
+                drift += sign * _ad(Vs[j]) @ s[j] * qd[j]
+        Vb_s = Vs[b]
+        Va_s = Vs[a] if a >= 0 else np.zeros(6)
+        Vrel = AdInv @ (Vb_s - Va_s)
+        VFb = AdInv @ Vb_s
+        G[5 * k:5 * k + 5] = (AdInv @ Gf)[1:]
+        gamma[5 * k:5 * k + 5] = (-_ad(VFb) @ Vrel + AdInv @ drift)[1:]
+    return G, gamma
+
+
+def forward_dynamics_looped(model, q, qd, tau, loops):
+    """qdd of a tree closed by revolute loop joints: the KKT system
+    M qdd + G^T lam = tau - ID(q, qd, 0), G qdd = -gamma, solved densely."""
+    n = model.axes.shape[0]
+    M = mass_matrix(model, q)
+    f = tau - inverse_dynamics(model, q, qd, np.zeros(n))
+    G, gamma = loop_constraints(model, q, qd, loops)
+    m = G.shape[0]
+    KKT = np.zeros((n + m, n + m))
+    KKT[:n, :n], KKT[:n, n:], KKT[n:, :n] = M, G.T, G
+    sol = np.linalg.solve(KKT, np.concatenate([f, -gamma]))
+    return sol[:n]

@@ -197,6 +197,50 @@ def random_trees(lengths, seed: int = 0, random_home_rotation: bool = False,
     return m
 
 
+def random_loops(model: ChainModel, per_tree: int = 1, seed: int = 0, min_joints: int = 6):
+    """Revolute loop joints closing each tree of ``model`` (``per_tree`` each):
+    link b uniform over the tree's links, link a uniform over the tree's links
+    and the base (-1), redrawn until the two paths to the base differ by at
+    least ``min_joints`` joints, five of them in no other loop of the tree (so
+    the loops' constraints are independent);
+    the joint frames on either side are a rotation from a normalised normal
+    quaternion and an offset U[-0.1, 0.1]^3 m. Returns a dict of arrays: tree,
+    a, b (int32, link indices within the tree), frame_a, frame_b (K x 12, R
+    row-major then p, in link a's (the base's) and link b's frames)."""
+    rng = np.random.default_rng(seed)
+    par = model.parents
+    tree, A, B, FA, FB = [], [], [], [], []
+    for t in range(model.n_chains):
+        o, z = int(model.offsets[t]), int(model.offsets[t + 1])
+        n = z - o
+
+        def path(i):
+            out = set()
+            while i >= 0:
+                out.add(i)
+                i = int(par[o + i]) if par is not None else i - 1
+            return out
+        used = set()
+        for _ in range(per_tree):
+            for _try in range(1000):
+                b = int(rng.integers(0, n))
+                a = int(rng.integers(-1, n))
+                joints = path(a) ^ path(b)
+                if a != b and len(joints) >= min_joints and len(joints - used) >= 5:
+                    used |= joints
+                    break
+            else:
+                raise ValueError(f"tree {t} has no pair of links {min_joints} joints apart")
+            fr = []
+            for _side in range(2):
+                R = _quat_to_rot(_unit(rng.standard_normal(4)))
+                fr.append(np.concatenate([R.reshape(9), rng.uniform(-0.1, 0.1, size=3)]))
+            tree.append(t); A.append(a); B.append(b); FA.append(fr[0]); FB.append(fr[1])
+    return {"tree": np.array(tree, dtype=np.int32), "a": np.array(A, dtype=np.int32),
+            "b": np.array(B, dtype=np.int32), "frame_a": np.array(FA).reshape(-1, 12),
+            "frame_b": np.array(FB).reshape(-1, 12)}
+
+
 def random_states(n_links_total: int, seed: int = 0, qdot_std: float = 1.0,
                   tau_std: float = 10.0) -> States:
     rng = np.random.default_rng(seed)

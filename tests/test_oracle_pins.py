@@ -588,3 +588,74 @@ def test_tree_power_balance(seed):
     grad = np.array([(_tree_potential(tree, q + h * e) - _tree_potential(tree, q - h * e)) / (2 * h)
                      for e in np.eye(9)])
     np.testing.assert_allclose(g, grad, rtol=1e-6, atol=1e-6)
+
+
+# ------------------------------------------------------ closed kinematic loops
+
+def _loop_setup(seed, n=24):
+    tree = synth.random_trees([n], seed=seed, random_home_rotation=True)
+    loops = synth.random_loops(tree, per_tree=2, seed=seed + 1)
+    st = synth.random_states(n, seed=seed + 2)
+    return tree, loops, st
+
+
+def _rel_pose(model, q, loops, k):
+    """h = g_0Fa^-1 g_0Fb of loop k, by forward kinematics written here."""
+    Rw, pw = _tree_world(model, q)
+    def frame(link, T):
+        R0, p0 = (np.eye(3), np.zeros(3)) if link < 0 else (Rw[link], pw[link])
+        H = np.eye(4)
+        H[:3, :3] = R0 @ T[:9].reshape(3, 3)
+        H[:3, 3] = p0 + R0 @ T[9:]
+        return H
+    Ha = frame(int(loops["a"][k]), loops["frame_a"][k])
+    Hb = frame(int(loops["b"][k]), loops["frame_b"][k])
+    return np.linalg.inv(Ha) @ Hb
+
+
+def _twist_of(H):
+    """The twist (omega; v) whose exponential is the small motion H."""
+    from scipy.linalg import logm
+    X = np.real(logm(H))
+    return np.array([X[2, 1], X[0, 2], X[1, 0], X[0, 3], X[1, 3], X[2, 3]])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_loop_constraint_rows_are_the_relative_motion(seed):
+    """G's rows are components 1..5 of the body twist of F_b relative to F_a:
+    central differences of the relative pose along each joint (forward
+    kinematics written in the test) give its columns; gamma = (dG/dt) qd by
+    central differences of G along qd."""
+    tree, loops, st = _loop_setup(seed)
+    G, gamma = dense.loop_constraints(tree, st.q, st.qdot, loops)
+    h = 1e-6
+    for k in range(len(loops["a"])):
+        for j in range(tree.axes.shape[0]):
+            e = np.zeros_like(st.q); e[j] = h
+            H = np.linalg.inv(_rel_pose(tree, st.q - e, loops, k)) @ _rel_pose(tree, st.q + e, loops, k)
+            col = _twist_of(H) / (2 * h)
+            np.testing.assert_allclose(G[5 * k:5 * k + 5, j], col[1:], atol=1e-6)
+    h = 1e-5
+    Gp, _ = dense.loop_constraints(tree, st.q + h * st.qdot, st.qdot, loops)
+    Gm, _ = dense.loop_constraints(tree, st.q - h * st.qdot, st.qdot, loops)
+    np.testing.assert_allclose(gamma, (Gp - Gm) @ st.qdot / (2 * h), rtol=1e-6,
+                               atol=1e-7 * np.abs(gamma).max())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_looped_dynamics_satisfy_the_constraints(seed):
+    """The KKT solution accelerates along the loops (G qdd = -gamma), its joint
+    torques differ from the open tree's only by constraint forces (M qdd - (tau -
+    bias) lies in the range of G^T), and without loops it is the tree's."""
+    tree, loops, st = _loop_setup(seed)
+    qdd = oracle.fd_looped(tree, st.q, st.qdot, st.tau,
+                           dict(loops, tree=np.zeros(len(loops["a"]), dtype=np.int32)))
+    G, gamma = dense.loop_constraints(tree, st.q, st.qdot, loops)
+    np.testing.assert_allclose(G @ qdd, -gamma, atol=1e-9 * max(np.abs(gamma).max(), 1))
+    M = dense.mass_matrix(tree, st.q)
+    r = M @ qdd - (st.tau - oracle.rnea_tree(tree, st.q, st.qdot, np.zeros_like(st.q)))
+    lam, *_ = np.linalg.lstsq(G.T, r, rcond=None)
+    np.testing.assert_allclose(G.T @ lam, r, atol=1e-8 * np.abs(r).max())
+    none = {k: v[:0] for k, v in loops.items()}
+    np.testing.assert_allclose(oracle.fd_looped(tree, st.q, st.qdot, st.tau, none),
+                               oracle.fd_tree(tree, st.q, st.qdot, st.tau), rtol=1e-12, atol=1e-12)
