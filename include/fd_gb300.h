@@ -142,6 +142,26 @@ fd_status fd_create_tree(int32_t n_trees, const int64_t *link_offsets, const int
                          const double *spatial_inertias, const double gravity[3],
                          int32_t device, fd_chain_t *out);
 
+/*
+ * fd_tree_add_loops -- close a set of kinematic trees by revolute loop joints
+ * (looped robots; not in the paper). Loop k joins a joint frame on link
+ * link_a[k] (-1: the base) and one on link link_b[k] of tree loop_tree[k] (link
+ * indices within the tree), turning about the frames' x axes: frame_a[k],
+ * frame_b[k] [12] (host) are the frames' poses in those links' frames (R
+ * row-major, then p) as given to fd_create_tree. The relative twist of the two
+ * frames may only turn about x, so each loop adds five constraints G qd = 0;
+ * forward dynamics then solves M qdd + G^T lam = tau - bias, G qdd = -gamma
+ * (gamma the constraint's velocity product) with JSIIA's factor of M. At most
+ * four loops a tree, whose constraints must be independent (else that problem's
+ * status is FD_ERR_NOT_SPD); once per set, before or after fd_batch_create. A
+ * set with loops solves with FD_JSIIA in FD_FP64 only; other algorithms and
+ * fd_inverse_dynamics return FD_ERR_UNSUPPORTED. FD_ERR_INVALID_ARG for a set
+ * of chains, bad indices, frames that are not rotations, or too many loops.
+ */
+fd_status fd_tree_add_loops(fd_chain_t chain, int32_t n_loops, const int32_t *loop_tree,
+                            const int32_t *link_a, const int32_t *link_b, const double *frame_a,
+                            const double *frame_b);
+
 fd_status fd_destroy_chain(fd_chain_t chain);
 
 /* Number of chains, total links and the longest chain's link count. */

@@ -377,6 +377,10 @@ static fd_status create_set(int32_t n_chains, const int64_t *link_offsets,
       return cuda_fail(e, "fd_create_tree: device allocation");
     }
   }
+  if (parents) {
+    c->h_axes.assign(joint_axes, joint_axes + 3 * L);
+    c->h_parent.assign(parents, parents + L);
+  }
   cudaSetDevice(prev);
   *out = c;
   return FD_OK;
@@ -424,9 +428,92 @@ fd_status fd_destroy_chain(fd_chain_t c) {
   cudaFree(c->d_model32);
   cudaFree(c->d_off);
   cudaFree(c->d_parent);
+  cudaFree(c->d_loop_off);
+  cudaFree(c->d_loop_ab);
+  cudaFree(c->d_loop_T);
   cudaSetDevice(prev);
   cudaGetLastError();  // leave no error state behind for other users of the runtime
   delete c;
+  return FD_OK;
+}
+
+fd_status fd_tree_add_loops(fd_chain_t c, int32_t n_loops, const int32_t *loop_tree,
+                            const int32_t *link_a, const int32_t *link_b, const double *frame_a,
+                            const double *frame_b) {
+  const char *who = "fd_tree_add_loops";
+  if (!c) return fail(FD_ERR_INVALID_ARG, "%s: NULL chain set", who);
+  if (!c->d_parent) return fail(FD_ERR_INVALID_ARG, "%s: not a set of kinematic trees", who);
+  if (c->n_loops > 0) return fail(FD_ERR_INVALID_ARG, "%s: the set already has its loops", who);
+  if (n_loops < 0 || (n_loops > 0 && (!loop_tree || !link_a || !link_b || !frame_a || !frame_b)))
+    return fail(FD_ERR_INVALID_ARG, "%s: bad count or NULL array", who);
+  if (n_loops == 0) return FD_OK;
+  // loops grouped by tree (stable), frames to canonical link coordinates
+  std::vector<int32_t> cnt(static_cast<size_t>(c->n_chains) + 1, 0);
+  for (int32_t k = 0; k < n_loops; ++k) {
+    const int32_t t = loop_tree[k];
+    if (t < 0 || t >= c->n_chains) return fail(FD_ERR_INVALID_ARG, "%s: loop %d: tree %d", who, k, t);
+    const int64_t n = c->h_off[t + 1] - c->h_off[t];
+    if (link_b[k] < 0 || link_b[k] >= n || link_a[k] < -1 || link_a[k] >= n || link_a[k] == link_b[k])
+      return fail(FD_ERR_INVALID_ARG, "%s: loop %d: links %d, %d of a %lld-link tree", who, k,
+                  link_a[k], link_b[k], static_cast<long long>(n));
+    for (int h = 0; h < 2; ++h) {
+      const double *fr = (h ? frame_b : frame_a) + 12 * k;
+      double RtR[9];
+      m3_tmul(fr, fr, RtR);
+      for (int r = 0; r < 9; ++r)
+        if (!(std::fabs(RtR[r] - (r % 4 == 0 ? 1.0 : 0.0)) < 1e-9))
+          return fail(FD_ERR_INVALID_ARG, "%s: loop %d: a joint frame is not a rotation", who, k);
+    }
+    if (++cnt[t + 1] > fdk::MAX_LOOPS_PER_TREE)
+      return fail(FD_ERR_INVALID_ARG, "%s: tree %d has more than %d loops", who, t,
+                  fdk::MAX_LOOPS_PER_TREE);
+  }
+  for (int32_t t = 0; t < c->n_chains; ++t) cnt[t + 1] += cnt[t];
+  std::vector<int32_t> ab(2 * static_cast<size_t>(n_loops));
+  std::vector<double> Tc(24 * static_cast<size_t>(n_loops));
+  std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+  for (int32_t k = 0; k < n_loops; ++k) {
+    const int32_t t = loop_tree[k], at = fill[t]++;
+    ab[2 * at] = link_a[k];
+    ab[2 * at + 1] = link_b[k];
+    for (int h = 0; h < 2; ++h) {
+      const int32_t link = h ? link_b[k] : link_a[k];
+      const double *fr = (h ? frame_b : frame_a) + 12 * k;
+      double *dst = Tc.data() + 24 * at + 12 * h;
+      if (link < 0) {  // the base keeps its frame
+        std::memcpy(dst, fr, 12 * sizeof(double));
+        continue;
+      }
+      const double *ax = c->h_axes.data() + 3 * (c->h_off[t] + link);
+      const double na = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+      const double a3[3] = {ax[0] / na, ax[1] / na, ax[2] / na};
+      double Q[9];
+      axis_frame(a3, Q);  // user link coordinates = Q canonical ones
+      m3_tmul(Q, fr, dst);  // R_c = Q^T R
+      for (int r = 0; r < 3; ++r)
+        dst[9 + r] = Q[r] * fr[9] + Q[3 + r] * fr[10] + Q[6 + r] * fr[11];  // p_c = Q^T p
+    }
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  if ((e = cudaMalloc(reinterpret_cast<void **>(&c->d_loop_off), cnt.size() * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void **>(&c->d_loop_ab), ab.size() * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void **>(&c->d_loop_T), Tc.size() * sizeof(double))) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_loop_off, cnt.data(), cnt.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_loop_ab, ab.data(), ab.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_loop_T, Tc.data(), Tc.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(c->d_loop_off);
+    cudaFree(c->d_loop_ab);
+    cudaFree(c->d_loop_T);
+    c->d_loop_off = c->d_loop_ab = nullptr;
+    c->d_loop_T = nullptr;
+    cudaSetDevice(prev);
+    return cuda_fail(e, who);
+  }
+  c->n_loops = n_loops;
+  cudaSetDevice(prev);
   return FD_OK;
 }
 
@@ -568,7 +655,8 @@ WsPlan ws_plan(const fd_batch_s *b, int32_t algo, fd_prec prec, int /*team: no l
   if (b->chain->d_parent) {  // kinematic trees
     if (algo == FD_ABIA) w.a_bytes = align256(L * fdk::NA_TREE * as);
     if (algo == FD_JSIIA)
-      w.a_bytes = align256((L * fdk::NA_TREE + static_cast<size_t>(b->sum_sq)) * as);
+      w.a_bytes = align256((L * fdk::NA_TREE + static_cast<size_t>(b->sum_sq) +
+                            (b->chain->n_loops > 0 ? L * fdk::NA_LOOP_LINK : 0)) * as);
     return w;
   }
   if (algo == FD_CFA || algo == FD_CFA_CR || algo == FD_CFA_HYBRID)
@@ -681,6 +769,10 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
     if (team > 1 || only_class >= 0)
       return fail(FD_ERR_UNSUPPORTED, "%s: kinematic trees run one thread per tree (team 1)",
                   who);
+    if (b->chain->n_loops > 0 && (algo != FD_JSIIA || prec != FD_FP64))
+      return fail(FD_ERR_UNSUPPORTED,
+                  "%s: trees closed by loops run JSIIA in FP64 (its factor of M solves the "
+                  "constrained system)", who);
   }
   if (b->n_problems == 0 || b->n_state_links == 0) return FD_OK;
   if (!q || !qd || !in3 || !out) return fail(FD_ERR_INVALID_ARG, "%s: NULL state array", who);
@@ -720,6 +812,13 @@ static fd_status launch_common(fd_batch_t b, const void *q, const void *qd, cons
   auto s = static_cast<cudaStream_t>(stream);
   if (tree) {
     e = fdk::launch_tree(a, algo == FD_ABIA ? 0 : (algo == FD_JSIIA ? 1 : -1), prec_k, s);
+    if (e == cudaSuccess && b->chain->n_loops > 0) {
+      a.loop_off = b->chain->d_loop_off;
+      a.loop_ab = b->chain->d_loop_ab;
+      a.loop_T = b->chain->d_loop_T;
+      a.loop_ws = static_cast<int64_t>(b->n_state_links) * fdk::NA_TREE + b->sum_sq;
+      e = fdk::launch_tree_loops(a, s);
+    }
   } else if (wmode != 0) {
     e = fdk::launch_cfa_w(a, prec_k, t, s);
   } else if (only_class >= 0 || use_classes(b, algo, team)) {

@@ -19,6 +19,14 @@ struct fd_chain_s {
   int64_t *d_off = nullptr;
   bool rigid = true;  // every inertia has the rigid-body form (mass gradients)
   int32_t *d_parent = nullptr;  // kinematic trees: [n_links] parent within the tree; null: chains
+  std::vector<double> h_axes;   // kinematic trees: the joint axes as given ([n_links][3])
+  std::vector<int32_t> h_parent;
+  // closed loops (fd_tree_add_loops): per tree a range of loops, per loop links
+  // a, b and the two joint frames in canonical link coordinates
+  int32_t n_loops = 0;
+  int32_t *d_loop_off = nullptr;  // [n_chains + 1]
+  int32_t *d_loop_ab = nullptr;   // [n_loops][2]
+  double *d_loop_T = nullptr;     // [n_loops][24]
 };
 
 struct fd_batch_s {

@@ -14,6 +14,7 @@ cudaError_t launch_id(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_cfa(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_cfa_w(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_tree(const KArgs &a, int algo, int prec, cudaStream_t s);
+cudaError_t launch_tree_loops(const KArgs &a, cudaStream_t s);
 cudaError_t launch_cfa_cr(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_cfa_hy(const KArgs &a, int prec, int team, cudaStream_t s);
 cudaError_t launch_jsiia(const KArgs &a, int prec, int team, cudaStream_t s);

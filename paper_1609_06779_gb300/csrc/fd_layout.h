@@ -74,6 +74,11 @@ constexpr int NA_ABIA = 9;
 // Kinematic trees (ABIA, JSIIA): per-link TA entries (the layout is in
 // fd_tree.cuh); JSIIA adds n*n entries (M) per problem.
 constexpr int NA_TREE = 41;
+// ... and, for trees closed by loops (JSIIA), per-link loop entries after the
+// JSIIA workspace (g_0i 12, five constraint rows and five solves per loop, at
+// most four loops a tree)
+constexpr int NA_LOOP_LINK = 52;
+constexpr int MAX_LOOPS_PER_TREE = 4;
 
 // Adjoint (reverse inverse dynamics) per-link workspace of T.
 constexpr int J_G = 0;    // g_i (12)
@@ -146,6 +151,14 @@ struct KArgs {
   // kinematic trees: each link's parent within its tree (-1: the base), by the
   // model's link index; null for serial chains
   const int32_t *parent;
+  // closed loops of kinematic trees: loops of chain c are loop_off[c] ..
+  // loop_off[c+1]-1; per loop its links a, b (loop_ab) and the two joint frames
+  // in canonical link coordinates (loop_T, 24 doubles); loop_ws: where the loop
+  // workspace starts in ws_a (elements)
+  const int32_t *loop_off;
+  const int32_t *loop_ab;
+  const double *loop_T;
+  int64_t loop_ws;
 };
 
 constexpr int WPROJ_GIVEN = 1;

@@ -278,6 +278,196 @@ __device__ __forceinline__ void tree_jsiia_body(const KArgs &A, const Range &rg)
   set_status(A.status, pb.p, bad ? 2 : 0);
 }
 
+// Closed loops: revolute loop joints between a frame F_a on link a (or the
+// base) and a frame F_b on link b, turning about their x axes. The relative
+// twist V_rel = V_Fb - Ad_{g_ba} V_Fa (F_b's body twist relative to F_a,
+// g_ba = g_0Fb^-1 g_0Fa) may only turn about x, so its components 1..5 vanish:
+// G qd = 0 with the rows G = (Ad_{g_0Fb^-1} sum over the path of b minus the path
+// of a of s_j e_j^T)[1..5], s_j joint j's axis as a world twist, and at the
+// acceleration level G qdd + gamma = 0 with
+//   gamma = (Vd_Fb - Ad_{g_ba} Vd_Fa + ad_{V_Fb} Ad_{g_ba} V_Fa)[1..5]
+// at qdd = 0 (the base's gravity enters both frames and cancels). JSIIA's
+// factor M = L^T L and its free solution x0 = M^-1 (tau - bias) then give the
+// constrained accelerations qdd = x0 - Y lam, Y = M^-1 G^T,
+// (G Y) lam = G x0 + gamma (M qdd + G^T lam = tau - bias). Runs after the tree
+// JSIIA kernel on its workspace: g_i, V_i, Vd_i of the inverse dynamics, L and
+// 1 / L_kk, x0 in the output.
+constexpr int MAX_LOOPS = MAX_LOOPS_PER_TREE;
+constexpr int NA_LOOP = 12 + 2 * 5 * MAX_LOOPS;  // per link: g_0i, G's rows, Y's rows
+static_assert(NA_LOOP == NA_LOOP_LINK, "loop workspace per link");
+constexpr int LW_G0 = 0, LW_G = 12, LW_Y = 12 + 5 * MAX_LOOPS;
+
+template <class T>
+__device__ __forceinline__ void ad_fwd(const SE3<T> &g, const T *x, T *y) {  // Ad_g x
+  T o[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) o[i] = g.R[3 * i] * x[0] + g.R[3 * i + 1] * x[1] + g.R[3 * i + 2] * x[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) o[3 + i] = g.R[3 * i] * x[3] + g.R[3 * i + 1] * x[4] + g.R[3 * i + 2] * x[5];
+  T c[3];
+  cross3(g.p, o, c);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[i] = o[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[3 + i] = o[3 + i] + c[i];
+}
+
+__device__ __forceinline__ void tree_loop_body(const KArgs &A, const Range &rg) {
+  using T = double;
+  Team<1> tm;
+  Prob<T> pb;
+  if (!load_problem<T, 1>(A, rg, tm, pb, NT)) return;
+  const int n = pb.n;
+  const int c = A.prob_chain ? A.prob_chain[pb.p] : pb.p;
+  const int l0 = A.loop_off[c], nl = A.loop_off[c + 1] - l0;
+  if (nl == 0 || n == 0) return;
+  const int m = 5 * nl;
+  const int32_t *par = A.parent + pb.m0;
+  const int64_t s0 = A.state_off[pb.p];
+  T *wj = static_cast<T *>(A.ws_a) + s0 * NA_TREE + A.sq_off[pb.p];
+  const T *M = wj + static_cast<int64_t>(n) * NA_TREE;
+  auto Lm = [&](int i, int j) -> T { return M[static_cast<int64_t>(j) * n + i]; };
+  auto rinv = [&](int k) -> T { return wj[static_cast<int64_t>(k) * NA_TREE + TA_H]; };
+  T *wl = static_cast<T *>(A.ws_a) + A.loop_ws + s0 * NA_LOOP;
+  auto lw = [&](int i) -> T * { return wl + static_cast<int64_t>(i) * NA_LOOP; };
+  bool bad = false;
+  // world poses
+  for (int i = 0; i < n; ++i) {
+    SE3<T> g, g0;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, g);
+    if (par[i] >= 0) {
+      ld_se3(lw(par[i]) + LW_G0, g0);
+      se3_mul(g0, g, g0);
+    } else {
+      g0 = g;
+    }
+    st_se3(lw(i) + LW_G0, g0);
+#pragma unroll 1
+    for (int r = 0; r < m; ++r) lw(i)[LW_G + r] = T(0);
+  }
+  // G's rows and gamma, loop by loop
+  T gam[5 * MAX_LOOPS];
+  for (int k = 0; k < nl; ++k) {
+    const int a = A.loop_ab[2 * (l0 + k)], b = A.loop_ab[2 * (l0 + k) + 1];
+    const double *Tk = A.loop_T + 24 * static_cast<int64_t>(l0 + k);
+    SE3<T> Ta, Tb, gFa, gFb, gb;
+    ld_se3(Tk, Ta);
+    ld_se3(Tk + 12, Tb);
+    ld_se3(lw(b) + LW_G0, gb);
+    se3_mul(gb, Tb, gFb);
+    if (a >= 0) {
+      SE3<T> ga;
+      ld_se3(lw(a) + LW_G0, ga);
+      se3_mul(ga, Ta, gFa);
+    } else {
+      gFa = Ta;
+    }
+    for (int side = 0; side < 2; ++side) {
+      const T sg = side ? T(-1) : T(1);
+      for (int j = side ? a : b; j >= 0; j = par[j]) {
+        SE3<T> g0;
+        ld_se3(lw(j) + LW_G0, g0);
+        // s_j = Ad_{g_0j} e_1 = (R e_1; p x R e_1)
+        T sj[6] = {g0.R[0], g0.R[3], g0.R[6], T(0), T(0), T(0)};
+        sj[3] = g0.p[1] * sj[2] - g0.p[2] * sj[1];
+        sj[4] = g0.p[2] * sj[0] - g0.p[0] * sj[2];
+        sj[5] = g0.p[0] * sj[1] - g0.p[1] * sj[0];
+        T col[6];
+        adinv(gFb, sj, col);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) lw(j)[LW_G + 5 * k + r] += sg * col[r + 1];
+      }
+    }
+    // gamma: the frames' twists and accelerations from the links' (qdd = 0)
+    T Vb[6], Ab[6], VFb[6], AFb[6], VFa[6], AFa[6];
+    ldv<T, 6>(pb.wt + static_cast<int64_t>(b) * NT + TW_V, Vb);
+    ldv<T, 6>(pb.wt + static_cast<int64_t>(b) * NT + TW_A, Ab);
+    adinv(Tb, Vb, VFb);
+    adinv(Tb, Ab, AFb);
+    if (a >= 0) {
+      T Va[6], Aa[6];
+      ldv<T, 6>(pb.wt + static_cast<int64_t>(a) * NT + TW_V, Va);
+      ldv<T, 6>(pb.wt + static_cast<int64_t>(a) * NT + TW_A, Aa);
+      adinv(Ta, Va, VFa);
+      adinv(Ta, Aa, AFa);
+    } else {
+      const T base[6] = {T(0), T(0), T(0), T(-A.grav[0]), T(-A.grav[1]), T(-A.grav[2])};
+#pragma unroll
+      for (int r = 0; r < 6; ++r) VFa[r] = T(0);
+      adinv(Ta, base, AFa);
+    }
+    T t[6], u[6], w[6];
+    ad_fwd(gFa, AFa, t);   // Ad_{g_ba} = Ad_{g_0Fb^-1} Ad_{g_0Fa}
+    adinv(gFb, t, u);
+    ad_fwd(gFa, VFa, t);
+    adinv(gFb, t, w);
+    ad_apply(VFb, w, t);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) gam[5 * k + r] = AFb[r + 1] - u[r + 1] + t[r + 1];
+  }
+  // Y = M^-1 G^T, row by row of G: L^T y = g from the leaves, L x = y from the base
+  for (int r = 0; r < m; ++r) {
+    for (int i = 0; i < n; ++i) lw(i)[LW_Y + r] = lw(i)[LW_G + r];
+    for (int i = n - 1; i >= 0; --i) {
+      const T y = lw(i)[LW_Y + r] * rinv(i);
+      lw(i)[LW_Y + r] = y;
+      for (int j = par[i]; j >= 0; j = par[j]) lw(j)[LW_Y + r] -= Lm(i, j) * y;
+    }
+    for (int i = 0; i < n; ++i) {
+      T x = lw(i)[LW_Y + r];
+      for (int j = par[i]; j >= 0; j = par[j]) x -= Lm(i, j) * lw(j)[LW_Y + r];
+      lw(i)[LW_Y + r] = x * rinv(i);
+    }
+  }
+  // K = G Y (m x m, symmetric positive definite when the loops are independent),
+  // rhs = G x0 + gamma, K lam = rhs by Cholesky (packed lower, local memory)
+  T K[5 * MAX_LOOPS * (5 * MAX_LOOPS + 1) / 2], lam[5 * MAX_LOOPS];
+  for (int r = 0; r < m; ++r) {
+    T rhs = gam[r];
+    for (int i = 0; i < n; ++i) rhs += lw(i)[LW_G + r] * pb.out[i];
+    lam[r] = rhs;
+    for (int c2 = 0; c2 <= r; ++c2) {
+      T kk = T(0);
+      for (int i = 0; i < n; ++i) kk += lw(i)[LW_G + r] * lw(i)[LW_Y + c2];
+      K[r * (r + 1) / 2 + c2] = kk;
+    }
+  }
+  for (int j = 0; j < m; ++j) {
+    T d = K[j * (j + 1) / 2 + j];
+    for (int k = 0; k < j; ++k) d -= K[j * (j + 1) / 2 + k] * K[j * (j + 1) / 2 + k];
+    bad |= !pos_t(d);
+    const T rr = rsqrt_t(d);
+    K[j * (j + 1) / 2 + j] = rr;  // 1 / L_jj
+    for (int i = j + 1; i < m; ++i) {
+      T x = K[i * (i + 1) / 2 + j];
+      for (int k = 0; k < j; ++k) x -= K[i * (i + 1) / 2 + k] * K[j * (j + 1) / 2 + k];
+      K[i * (i + 1) / 2 + j] = x * rr;
+    }
+  }
+  for (int i = 0; i < m; ++i) {
+    T x = lam[i];
+    for (int k = 0; k < i; ++k) x -= K[i * (i + 1) / 2 + k] * lam[k];
+    lam[i] = x * K[i * (i + 1) / 2 + i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    T x = lam[i];
+    for (int k = i + 1; k < m; ++k) x -= K[k * (k + 1) / 2 + i] * lam[k];
+    lam[i] = x * K[i * (i + 1) / 2 + i];
+  }
+  // qdd = x0 - Y lam
+  for (int i = 0; i < n; ++i) {
+    T x = pb.out[i];
+    for (int r = 0; r < m; ++r) x -= lw(i)[LW_Y + r] * lam[r];
+    pb.out[i] = x;
+    if (!finite_t(x)) bad = true;
+  }
+  if (bad) set_status(A.status, pb.p, 2);
+}
+
+__global__ void __launch_bounds__(128, 4) tree_loop_kernel(KArgs A) {
+  tree_loop_body(A, Range{0, 0, A.n_problems});
+}
+
 // Inverse dynamics alone (MODE_ID): tau = ID(q, qd, qdd) on a tree.
 template <class T>
 __device__ __forceinline__ void tree_id_body(const KArgs &A, const Range &rg) {

@@ -23,4 +23,12 @@ cudaError_t launch_tree(const KArgs &a, int algo, int prec, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// the loop-closure correction after the tree JSIIA (FP64)
+cudaError_t launch_tree_loops(const KArgs &a, cudaStream_t s) {
+  const unsigned g = static_cast<unsigned>((static_cast<int64_t>(a.n_problems) + 127) / 128);
+  if (g == 0) return cudaSuccess;
+  tree_loop_kernel<<<g, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace fdk

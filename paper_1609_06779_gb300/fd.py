@@ -57,6 +57,7 @@ def load(build_if_missing: bool = True):
         lib.fd_create_chain.argtypes = [i32, i64p, dp, dp, dp, dp, i32, ctypes.POINTER(vp)]
         lib.fd_create_tree.argtypes = [i32, i64p, i32p, dp, dp, dp, dp, i32,
                                        ctypes.POINTER(vp)]
+        lib.fd_tree_add_loops.argtypes = [vp, i32, i32p, i32p, i32p, dp, dp]
         lib.fd_destroy_chain.argtypes = [vp]
         lib.fd_chain_info.argtypes = [vp, i32p, i64p, i32p]
         lib.fd_batch_create.argtypes = [vp, i32, i32p, ctypes.POINTER(vp)]
@@ -84,7 +85,7 @@ def load(build_if_missing: bool = True):
         lib.fd_autotune_cache_load.argtypes = [ctypes.c_char_p, i32p]
         lib.fd_autotune_cache_save.argtypes = [ctypes.c_char_p]
         lib.fd_autotune_cache_clear.argtypes = []
-        for f in ("fd_create_chain", "fd_create_tree", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
+        for f in ("fd_create_chain", "fd_create_tree", "fd_tree_add_loops", "fd_destroy_chain", "fd_chain_info", "fd_batch_create",
                   "fd_batch_destroy", "fd_batch_info", "fd_solve_batch", "fd_inverse_dynamics",
                   "fd_solve_cfa_static", "fd_projection_to_canonical",
                   "fd_solve_cfa_projected", "fd_batch_classes", "fd_autotune_cache_load",
@@ -136,6 +137,19 @@ class ChainSet:
         self.handle = h
         self.device = device
         self.offsets = off.copy()
+
+    def add_loops(self, loops):
+        """Close the trees by revolute loop joints (fd_tree_add_loops): ``loops``
+        holds arrays tree, a, b (links within the tree, a = -1: the base) and
+        frame_a, frame_b (K x 12), as ``synth.random_loops`` returns."""
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        arr = {k: np.ascontiguousarray(loops[k], dtype=np.int32) for k in ("tree", "a", "b")}
+        fa = np.ascontiguousarray(loops["frame_a"], dtype=np.float64).reshape(-1, 12)
+        fb = np.ascontiguousarray(loops["frame_b"], dtype=np.float64).reshape(-1, 12)
+        K = arr["a"].shape[0]
+        _check(self._lib.fd_tree_add_loops(self.handle, K, arr["tree"].ctypes.data_as(i32p),
+                                           arr["a"].ctypes.data_as(i32p),
+                                           arr["b"].ctypes.data_as(i32p), _dptr(fa), _dptr(fb)))
 
     def info(self):
         n = ctypes.c_int32(); L = ctypes.c_int64(); m = ctypes.c_int32()

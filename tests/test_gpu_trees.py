@@ -126,3 +126,82 @@ def test_tree_unsupported_options():
     with pytest.raises(fd.FDError):
         fd.adjoint(b, q, qd, tau, torch.ones_like(q), algo="abia")
     assert fd.autotune(b, q, qd, tau, algo="abia") == 1
+
+
+def _looped(sizes, seed, per_tree=1):
+    from paper_1609_06779_gb300 import fd
+    model = synth.random_trees(sizes, seed=seed)
+    loops = synth.random_loops(model, per_tree=per_tree, seed=seed + 1)
+    st = synth.random_states(model.n_links_total, seed=seed + 2)
+    cs = fd.ChainSet(model)
+    cs.add_loops(loops)
+    return fd, model, loops, st, cs
+
+
+def test_looped_trees_jsiia_fp64_parity():
+    """Trees closed by revolute loop joints (fd_tree_add_loops): the GPU's
+    constrained accelerations against the oracle's dense KKT solve, and the
+    constraints G qdd + gamma = 0 (the oracle's G, gamma) on the GPU result."""
+    for sizes, seed, per_tree in (([12, 16, 24, 32, 40] * 3, 61, 1), ([32, 40, 48] * 3, 67, 2)):
+        _check_looped(sizes, seed, per_tree)
+
+
+def _check_looped(sizes, seed, per_tree):
+    fd, model, loops, st, cs = _looped(sizes, seed=seed, per_tree=per_tree)
+    b = fd.Batch(cs)
+    t = lambda x: torch.tensor(x, dtype=torch.float64, device="cuda")
+    status = torch.full((b.n_problems,), -1, dtype=torch.int32, device="cuda")
+    got = fd.solve(b, t(st.q), t(st.qdot), t(st.tau), algo="jsiia", status=status)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    got = got.cpu().numpy()
+    ref = oracle.fd_looped(model, st.q, st.qdot, st.tau, loops)
+    for p in range(model.n_chains):
+        a, z = model.offsets[p], model.offsets[p + 1]
+        sel = np.nonzero(loops["tree"] == p)[0]
+        lp = {k: np.asarray(loops[k])[sel] for k in ("a", "b", "frame_a", "frame_b")}
+        one = model.chain(p)
+        M = dense.mass_matrix(one, st.q[a:z])
+        G, gamma = dense.loop_constraints(one, st.q[a:z], st.qdot[a:z], lp)
+        kkt = np.block([[M, G.T], [G, np.zeros((G.shape[0], G.shape[0]))]])
+        tol = max(1e-10, 10 * np.linalg.cond(kkt) * EPS64)
+        err = np.abs(got[a:z] - ref[a:z]).max() / np.abs(ref[a:z]).max()
+        assert err <= tol, (p, err, tol)
+        res = G @ got[a:z] + gamma
+        assert np.abs(res).max() <= tol * max(np.abs(gamma).max(), np.abs(G).max() * np.abs(ref[a:z]).max())
+
+
+def test_looped_set_trees_without_loops_and_options():
+    """In a set with loops, a tree without one solves as an open tree; the other
+    algorithms and precisions are refused, and loops are added once."""
+    from paper_1609_06779_gb300 import fd
+    sizes = [20, 9, 20]
+    model = synth.random_trees(sizes, seed=63)
+    loops = synth.random_loops(model, per_tree=1, seed=64)
+    keep = loops["tree"] != 1
+    loops = {k: np.asarray(v)[keep] for k, v in loops.items()}
+    st = synth.random_states(model.n_links_total, seed=65)
+    cs = fd.ChainSet(model)
+    cs.add_loops(loops)
+    b = fd.Batch(cs)
+    t = lambda x, dt=torch.float64: torch.tensor(x, dtype=dt, device="cuda")
+    q, qd, tau = t(st.q), t(st.qdot), t(st.tau)
+    got = fd.solve(b, q, qd, tau, algo="jsiia").cpu().numpy()
+    a, z = model.offsets[1], model.offsets[2]
+    ref = oracle.fd_tree(model, st.q, st.qdot, st.tau)
+    assert np.abs(got[a:z] - ref[a:z]).max() <= 1e-10 * np.abs(ref[a:z]).max()
+    with pytest.raises(fd.FDError, match="loops run JSIIA"):
+        fd.solve(b, q, qd, tau, algo="abia")
+    f = lambda x: t(x, torch.float32)
+    with pytest.raises(fd.FDError, match="loops run JSIIA"):
+        fd.solve(b, f(st.q), f(st.qdot), f(st.tau), algo="jsiia", prec="fp32")
+    with pytest.raises(fd.FDError, match="loops run JSIIA"):
+        fd.inverse_dynamics(b, q, qd, tau)
+    with pytest.raises(fd.FDError, match="already"):
+        cs.add_loops(loops)
+    chains = fd.ChainSet(synth.random_chains([20], seed=66))
+    with pytest.raises(fd.FDError, match="not a set of kinematic trees"):
+        chains.add_loops(loops)
+    bad = dict(loops, b=np.full_like(loops["b"], 99))
+    with pytest.raises(fd.FDError, match="links"):
+        fd.ChainSet(model).add_loops(bad)
