@@ -531,6 +531,27 @@ def extra_configs(dev, keep=None):
         del ws, out
     res["65536_trees_32_links_fp64"] = rt
     keep.append(kt)
+    del cs, b, q, qd, tau
+    torch.cuda.empty_cache()
+
+    # the same trees closed by one revolute loop joint each (fd_tree_add_loops):
+    # JSIIA with the constrained solve, FP64; the first 64 against the oracle's
+    # dense KKT solve
+    loops = synth.random_loops(m, per_tree=1, seed=1)
+    cs = fd.ChainSet(m, device=dev.index or 0)
+    cs.add_loops(loops)
+    b = fd.Batch(cs)
+    q, qd, tau = t64(st.q), t64(st.qdot), t64(st.tau)
+    ws = fd.workspace(b, "jsiia", "fp64", 1, dev)
+    out = torch.empty_like(q)
+    ms = _time_ms(lambda: fd.solve(b, q, qd, tau, algo="jsiia", out=out, ws=ws), 5, 2)
+    res["65536_looped_trees_32_links_fp64"] = {
+        "trees": 65536, "links": 32, "loops_per_tree": 1, "algo": "jsiia", "team": 1, "ms": ms,
+        "solves_per_s": 65536 / (ms * 1e-3)}
+    keep.append({"config": "65536_looped_trees_32_links_fp64", "model": m, "st": st,
+                 "tree": True, "loops": loops, "chain_index": None, "problems": list(range(64)),
+                 "outs": {"jsiia": out[:64 * 32].cpu().numpy()}})
+    del cs, b, q, qd, tau, ws, out
     return res
 
 
@@ -551,7 +572,13 @@ def config_accuracy(keep):
             sub = synth.ChainModel(m.axes[:z], m.frames[:z], m.inertias[:z],
                                    m.offsets[:len(probs) + 1].copy(), m.gravity, m.parents[:z])
             t0 = time.perf_counter()
-            ref = oracle.fd_tree(sub, st.q[:z], st.qdot[:z], st.tau[:z])
+            if k.get("loops") is not None:
+                lp = k["loops"]
+                sel = np.asarray(lp["tree"]) < len(probs)
+                ref = oracle.fd_looped(sub, st.q[:z], st.qdot[:z], st.tau[:z],
+                                       {kk: np.asarray(v)[sel] for kk, v in lp.items()})
+            else:
+                ref = oracle.fd_tree(sub, st.q[:z], st.qdot[:z], st.tau[:z])
             t1 = time.perf_counter()
             r = {"sampled_problems": len(probs),
                  "cpu_oracle": {"kind": "oracle (dense definitions over the parent array)",
