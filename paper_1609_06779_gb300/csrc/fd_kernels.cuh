@@ -322,76 +322,112 @@ __device__ __forceinline__ void id_team(const Team<P> &tm, const Prob<T> &pb, co
   const T *qdd_in = mode == MODE_ID ? pb.in3 : (mode == MODE_RES ? pb.out : nullptr);
   SegOp<T> op;
   se3_identity(op.h);
-  // joint transforms and this segment's product h = g_a ... g_{b-1}
-  for (int i = a; i < b; ++i) {
-    SE3<T> g;
-    joint_transform(pb.rec + static_cast<int64_t>(i) * REC, pb.q[i], g);
-    st_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
-    if (P > 1) se3_mul(op.h, g, op.h);
-    if (mode == MODE_LINEAR) pb.wt[static_cast<int64_t>(i) * NT + W_TD] = pb.in3[i];
-  }
-  if (mode == MODE_LINEAR) return;
-  const T zero6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  T x[6];
-
-  // ---- twist: V_i = Ad_{g_i^{-1}} V_{i-1} + e_1 qd_i, V_{-1} = 0 (Eq. 2a)
-  if (P > 1) {
-    for (int k = 0; k < 6; ++k) x[k] = T(0);
+  if constexpr (P == 1) {
+    // one thread: the joint transform, Eq. 2a and Eq. 2b and f_i in one forward
+    // sweep, the twist and acceleration recursions interleaved (two independent
+    // dependency chains) and g_i, V_i used from registers
+    T V[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T Vd[6] = {T(0), T(0), T(0), T(-grav[0]), T(-grav[1]), T(-grav[2])};
+    for (int i = 0; i < pb.n; ++i) {
+      T *w = pb.wt + static_cast<int64_t>(i) * NT;
+      const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+      SE3<T> g;
+      joint_transform(rec, pb.q[i], g);
+      st_se3(w + W_G, g);
+      if (mode == MODE_LINEAR) {
+        w[W_TD] = pb.in3[i];
+        continue;
+      }
+      const T qdi = pb.qd[i];
+      adinv(g, V, V);
+      V[0] += qdi;
+      adinv(g, Vd, Vd);
+      // ad_V e_1 = (0, w_z, -w_y; 0, v_z, -v_y)
+      Vd[1] += V[2] * qdi;
+      Vd[2] -= V[1] * qdi;
+      Vd[4] += V[5] * qdi;
+      Vd[5] -= V[4] * qdi;
+      if (qdd_in) Vd[0] += qdd_in[i];
+      stv<T, 6>(w + W_V, V);
+      T JV[6], f[6];
+      sym6_apply(rec + REC_J, V, JV);
+      sym6_apply(rec + REC_J, Vd, f);
+      adT_sub(V, JV, f);  // J Vd - ad_V^T J V
+      stv<T, 6>(w + W_F, f);
+    }
+    if (mode == MODE_LINEAR) return;
+  } else {
+    // joint transforms and this segment's product h = g_a ... g_{b-1}
     for (int i = a; i < b; ++i) {
       SE3<T> g;
-      ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+      joint_transform(pb.rec + static_cast<int64_t>(i) * REC, pb.q[i], g);
+      st_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+      if (P > 1) se3_mul(op.h, g, op.h);
+      if (mode == MODE_LINEAR) pb.wt[static_cast<int64_t>(i) * NT + W_TD] = pb.in3[i];
+    }
+    if (mode == MODE_LINEAR) return;
+    const T zero6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T x[6];
+
+    // ---- twist: V_i = Ad_{g_i^{-1}} V_{i-1} + e_1 qd_i, V_{-1} = 0 (Eq. 2a)
+    if (P > 1) {
+      for (int k = 0; k < 6; ++k) x[k] = T(0);
+      for (int i = a; i < b; ++i) {
+        SE3<T> g;
+        ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_G, g);
+        adinv(g, x, x);
+        x[0] += pb.qd[i];
+      }
+      for (int k = 0; k < 6; ++k) op.psi[k] = x[k];
+      team_scan_fwd(tm, op, zero6, x);
+    } else {
+      for (int k = 0; k < 6; ++k) x[k] = T(0);
+    }
+    for (int i = a; i < b; ++i) {
+      T *w = pb.wt + static_cast<int64_t>(i) * NT;
+      SE3<T> g;
+      ld_se3(w + W_G, g);
       adinv(g, x, x);
       x[0] += pb.qd[i];
+      stv<T, 6>(w + W_V, x);
     }
-    for (int k = 0; k < 6; ++k) op.psi[k] = x[k];
-    team_scan_fwd(tm, op, zero6, x);
-  } else {
-    for (int k = 0; k < 6; ++k) x[k] = T(0);
-  }
-  for (int i = a; i < b; ++i) {
-    T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    SE3<T> g;
-    ld_se3(w + W_G, g);
-    adinv(g, x, x);
-    x[0] += pb.qd[i];
-    stv<T, 6>(w + W_V, x);
-  }
 
-  // ---- acceleration: Vd_i = Ad_{g_i^{-1}} Vd_{i-1} + e_1 qdd_i + ad_{V_i} e_1 qd_i,
-  //      Vd_{-1} = (0; -g) (Eq. 2b, gravity as base acceleration)
-  const T base[6] = {T(0), T(0), T(0), T(-grav[0]), T(-grav[1]), T(-grav[2])};
-  auto accel_step = [&](int i, T *xx) {
-    const T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    SE3<T> g;
-    ld_se3(w + W_G, g);
-    adinv(g, xx, xx);
-    const T *V = w + W_V;
-    const T qdi = pb.qd[i];
-    // ad_V e_1 = (0, w_z, -w_y; 0, v_z, -v_y)
-    xx[1] += V[2] * qdi;
-    xx[2] -= V[1] * qdi;
-    xx[4] += V[5] * qdi;
-    xx[5] -= V[4] * qdi;
-    if (qdd_in) xx[0] += qdd_in[i];
-  };
-  if (P > 1) {
-    for (int k = 0; k < 6; ++k) x[k] = T(0);
-    for (int i = a; i < b; ++i) accel_step(i, x);
-    for (int k = 0; k < 6; ++k) op.psi[k] = x[k];
-    team_scan_fwd(tm, op, base, x);
-  } else {
-    for (int k = 0; k < 6; ++k) x[k] = base[k];
-  }
-  for (int i = a; i < b; ++i) {
-    accel_step(i, x);
-    T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
-    T V[6], JV[6], JA[6];
-    ldv<T, 6>(w + W_V, V);
-    sym6_apply(rec + REC_J, V, JV);
-    sym6_apply(rec + REC_J, x, JA);
-    adT_sub(V, JV, JA);  // J Vd - ad_V^T J V
-    stv<T, 6>(w + W_F, JA);
+    // ---- acceleration: Vd_i = Ad_{g_i^{-1}} Vd_{i-1} + e_1 qdd_i + ad_{V_i} e_1 qd_i,
+    //      Vd_{-1} = (0; -g) (Eq. 2b, gravity as base acceleration)
+    const T base[6] = {T(0), T(0), T(0), T(-grav[0]), T(-grav[1]), T(-grav[2])};
+    auto accel_step = [&](int i, T *xx) {
+      const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+      SE3<T> g;
+      ld_se3(w + W_G, g);
+      adinv(g, xx, xx);
+      const T *V = w + W_V;
+      const T qdi = pb.qd[i];
+      // ad_V e_1 = (0, w_z, -w_y; 0, v_z, -v_y)
+      xx[1] += V[2] * qdi;
+      xx[2] -= V[1] * qdi;
+      xx[4] += V[5] * qdi;
+      xx[5] -= V[4] * qdi;
+      if (qdd_in) xx[0] += qdd_in[i];
+    };
+    if (P > 1) {
+      for (int k = 0; k < 6; ++k) x[k] = T(0);
+      for (int i = a; i < b; ++i) accel_step(i, x);
+      for (int k = 0; k < 6; ++k) op.psi[k] = x[k];
+      team_scan_fwd(tm, op, base, x);
+    } else {
+      for (int k = 0; k < 6; ++k) x[k] = base[k];
+    }
+    for (int i = a; i < b; ++i) {
+      accel_step(i, x);
+      T *w = pb.wt + static_cast<int64_t>(i) * NT;
+      const T *rec = pb.rec + static_cast<int64_t>(i) * REC;
+      T V[6], JV[6], JA[6];
+      ldv<T, 6>(w + W_V, V);
+      sym6_apply(rec + REC_J, V, JV);
+      sym6_apply(rec + REC_J, x, JA);
+      adT_sub(V, JV, JA);  // J Vd - ad_V^T J V
+      stv<T, 6>(w + W_F, JA);
+    }
   }
 
   // ---- force: F_i = Ad_{g_{i+1}^{-1}}^T F_{i+1} + f_i, F_n = 0 (Eq. 2c), tau = S^T F (2d);
