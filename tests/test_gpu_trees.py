@@ -205,3 +205,26 @@ def test_looped_set_trees_without_loops_and_options():
     bad = dict(loops, b=np.full_like(loops["b"], 99))
     with pytest.raises(fd.FDError, match="links"):
         fd.ChainSet(model).add_loops(bad)
+
+
+def test_tree_edge_cases_empty_and_single_link():
+    """A set with an empty tree, a one-link tree and a link on the base beside a
+    branch solves (status 0 for every problem, the empty tree untouched), and
+    an empty batch is a no-op for the tree and projected solves."""
+    from paper_1609_06779_gb300 import fd
+    m = synth.random_trees([0, 1, 6, 0, 3], seed=71)
+    m.parents[1 + 2] = -1  # a second link on the base in the 6-link tree
+    st = synth.random_states(m.n_links_total, seed=72)
+    ref = oracle.fd_tree(m, st.q, st.qdot, st.tau)
+    for algo in ("abia", "jsiia"):
+        got, status = _solve(m, st, algo, "fp64")
+        assert (status == 0).all()
+        err = _rel_err(got, ref, m.offsets)
+        assert err.max() < 1e-12, (algo, err.max())
+    empty = synth.random_trees([0, 0], seed=73)
+    b = fd.Batch(fd.ChainSet(empty))
+    z = torch.zeros(0, dtype=torch.float64, device="cuda")
+    for algo in ("abia", "jsiia"):
+        assert fd.solve(b, z, z, z, algo=algo).numel() == 0
+    cb = fd.Batch(fd.ChainSet(synth.random_chains([0, 0], seed=74)))
+    assert fd.solve_cfa_projected(cb, z, z, z, projection="block_jacobi").numel() == 0
