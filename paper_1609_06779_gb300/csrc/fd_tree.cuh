@@ -36,13 +36,19 @@ constexpr int TA_UU = 34;
 constexpr int TA_AC = 35;
 static_assert(TA_AC + 6 <= NA_TREE, "tree link record");
 
+template <class T>
+__device__ __forceinline__ T tree_force_step(const Prob<T> &pb, const int32_t *par, int i,
+                                             const SE3<T> &g, bool fdm);
+
 // Eq. 2a-2b forward over the parent array, f_i = J_i Vd_i - ad_{V_i}^T J_i V_i,
 // then Eq. 2c-2d backward: F_i = f_i + sum over children c of Ad_{g_c^-1}^T F_c,
 // tau_i = F_i[0]. Writes tau_delta (MODE_FD: tau - tau_bias; MODE_ID: tau) to
 // TW_TD. With init_P, TA_P of every link starts as J_i and TA_PB as zero.
+// Without force, the backward pass is left to the caller (tree_force_step inside
+// its own backward loop).
 template <class T, class TA>
 __device__ __forceinline__ void tree_id(const KArgs &A, const Prob<T> &pb, const int32_t *par,
-                                        TA *wa, int mode, bool init_P) {
+                                        TA *wa, int mode, bool init_P, bool force = true) {
   const int n = pb.n;
   const T *qdd_in = mode == MODE_ID ? pb.in3 : nullptr;
   for (int i = 0; i < n; ++i) {
@@ -90,23 +96,34 @@ __device__ __forceinline__ void tree_id(const KArgs &A, const Prob<T> &pb, const
       for (int k = 0; k < 6; ++k) ra[TA_PB + k] = TA(0);
     }
   }
+  if (!force) return;
   const bool fdm = mode != MODE_ID;
   for (int i = n - 1; i >= 0; --i) {
-    T *w = pb.wt + static_cast<int64_t>(i) * NT;
-    T F[6];
-    ldv<T, 6>(w + TW_F, F);
-    w[TW_TD] = fdm ? pb.in3[i] - F[0] : F[0];
-    const int l = par[i];
-    if (l >= 0) {
-      SE3<T> g;
-      ld_se3(w + TW_G, g);
-      T t[6];
-      adinvT(g, F, t);
-      T *wl = pb.wt + static_cast<int64_t>(l) * NT;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) wl[TW_F + k] += t[k];
-    }
+    SE3<T> g;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, g);
+    pb.wt[static_cast<int64_t>(i) * NT + TW_TD] = tree_force_step(pb, par, i, g, fdm);
   }
+}
+
+// One step of Eq. 2c-2d over the parent array: link i's force F_i (its f_i plus
+// what its children added), tau_delta_i (or tau_i), and Ad_{g_i^-1}^T F_i added
+// into the parent's. Children have larger indices, so a descending sweep sees
+// every F_i complete.
+template <class T>
+__device__ __forceinline__ T tree_force_step(const Prob<T> &pb, const int32_t *par, int i,
+                                             const SE3<T> &g, bool fdm) {
+  const T *w = pb.wt + static_cast<int64_t>(i) * NT;
+  T F[6];
+  ldv<T, 6>(w + TW_F, F);
+  const int l = par[i];
+  if (l >= 0) {
+    T t[6];
+    adinvT(g, F, t);
+    T *wl = pb.wt + static_cast<int64_t>(l) * NT;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) wl[TW_F + k] += t[k];
+  }
+  return fdm ? pb.in3[i] - F[0] : F[0];
 }
 
 // ABIA on a tree (Section II-C over a parent array): backward, link i's
@@ -123,8 +140,13 @@ __device__ __forceinline__ void tree_abia_body(const KArgs &A, const Range &rg) 
   const int32_t *par = A.parent + pb.m0;
   TA *wa = static_cast<TA *>(A.ws_a) + A.state_off[pb.p] * NA_TREE;
   bool bad = false;
-  tree_id<T, TA>(A, pb, par, wa, A.mode, true);
+  // the force pass runs inside the articulated-inertia sweep (both descend over
+  // the links and share g_i)
+  tree_id<T, TA>(A, pb, par, wa, A.mode, true, false);
   for (int i = n - 1; i >= 0; --i) {
+    SE3<T> g;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, g);
+    const T tdi = tree_force_step(pb, par, i, g, true);
     TA *ra = wa + static_cast<int64_t>(i) * NA_TREE;
     TA Pm[21], pbias[6], h[6];
 #pragma unroll
@@ -134,7 +156,7 @@ __device__ __forceinline__ void tree_abia_body(const KArgs &A, const Range &rg) 
 #pragma unroll
     for (int k = 0; k < 6; ++k) h[k] = Pm[s6(0, k)];
     const TA D = h[0];
-    const TA u = TA(pb.wt[static_cast<int64_t>(i) * NT + TW_TD]) - pbias[0];
+    const TA u = TA(tdi) - pbias[0];
     bad |= !pos_t(D);
     const TA Dinv = rcp_t(D);
 #pragma unroll
@@ -154,7 +176,10 @@ __device__ __forceinline__ void tree_abia_body(const KArgs &A, const Range &rg) 
 #pragma unroll
     for (int k = 0; k < 6; ++k) pa[k] = pbias[k] + hs[k] * u;
     SE3<TA> ga;
-    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, ga);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) ga.R[k] = TA(g.R[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ga.p[k] = TA(g.p[k]);
     TA *rl = wa + static_cast<int64_t>(l) * NA_TREE;
     TA Pl[21], t[6];
 #pragma unroll
@@ -209,19 +234,25 @@ __device__ __forceinline__ void tree_jsiia_body(const KArgs &A, const Range &rg)
   TA *M = wa + static_cast<int64_t>(n) * NA_TREE;  // n x n, column-major, lower triangle
   auto Mat = [&](int i, int j) -> TA & { return M[static_cast<int64_t>(j) * n + i]; };
   bool bad = false;
-  tree_id<T, TA>(A, pb, par, wa, A.mode, true);
+  tree_id<T, TA>(A, pb, par, wa, A.mode, true, false);
   for (int i = n - 1; i >= 0; --i) {
+    SE3<T> g;
+    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, g);
+    const T tdi = tree_force_step(pb, par, i, g, true);
     TA *ra = wa + static_cast<int64_t>(i) * NA_TREE;
     TA Pm[21];
 #pragma unroll
     for (int k = 0; k < 21; ++k) Pm[k] = ra[TA_P + k];
 #pragma unroll
     for (int k = 0; k < 6; ++k) ra[TA_H + k] = Pm[s6(0, k)];
-    ra[TA_DD] = TA(pb.wt[static_cast<int64_t>(i) * NT + TW_TD]);  // the right-hand side
+    ra[TA_DD] = TA(tdi);  // the right-hand side
     const int l = par[i];
     if (l < 0) continue;
     SE3<TA> ga;
-    ld_se3(pb.wt + static_cast<int64_t>(i) * NT + TW_G, ga);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) ga.R[k] = TA(g.R[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ga.p[k] = TA(g.p[k]);
     TA *rl = wa + static_cast<int64_t>(l) * NA_TREE;
     TA Pl[21];
 #pragma unroll
