@@ -8,7 +8,8 @@
 // Links are numbered so that a parent precedes its children, so one ascending
 // and one descending sweep over the links visit every parent before (after) its
 // children. CFA's A stops being block tri-diagonal on a tree, so OEE has no
-// tree form here.
+// tree form here. Trees closed by revolute loop joints take JSIIA and then the
+// constrained correction of tree_loop_kernel (below).
 #pragma once
 
 #include "fd_kernels.cuh"
