@@ -1838,7 +1838,22 @@ __device__ __forceinline__ void jsiia_body(const KArgs &A, const Range &rg) {
 #pragma unroll
       for (int k = 0; k < 21; ++k) Pm[k] = TA(J[k]);
     }
+    // FP64: the forward kinematics g_0j of the base-frame entries below runs in the
+    // same loop, link j = n-1-i beside the congruence of link i (two independent
+    // dependency chains); the lane that owns link j parks g_0j in the link's
+    // twist and force slots, which the inverse dynamics no longer needs
+    constexpr bool fk = std::is_same<T, double>::value;
+    SE3<TA> g0f;
+    se3_identity(g0f);
     for (int i = n - 1; i >= 0; --i) {
+      if constexpr (fk) {
+        const int j = n - 1 - i;
+        SE3<TA> gj, t;
+        load_g(j, gj);
+        se3_mul(g0f, gj, t);
+        g0f = t;
+        if ((j & (P - 1)) == tm.r) st_se3(pb.wt + static_cast<int64_t>(j) * NT + W_V, g0f);
+      }
       if (tm.r == 0) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) H[static_cast<int64_t>(i) * 6 + c] = Pm[s6(0, c)];
@@ -1881,29 +1896,26 @@ __device__ __forceinline__ void jsiia_body(const KArgs &A, const Range &rg) {
     // s_k = Ad_{g_0k} e_1 (joint k's axis as a base-frame twist) and
     // F_i = Ad_{g_0i^{-1}}^T h_i (the composite force h_i in base coordinates),
     // M[i][k] = s_k . F_i, the same power pairing as in frame k: one 6-term dot
-    // product per entry instead of one SE(3) transport. Every lane runs the
-    // forward kinematics g_0i = g_0,i-1 g_{i-1,i}; lane r forms s_i and F_i for
-    // the links i = r mod P (F_i over h_i). The base-frame terms grow with the
-    // distance from the base and cancel in the pairing, which costs digits in
-    // proportion: FP64 only (with joint transforms rounded to FP32, the mixed
-    // mode's entries would lose about two digits).
+    // product per entry instead of one SE(3) transport. The forward kinematics
+    // g_0i = g_0,i-1 g_{i-1,i} runs on every lane (here for P = 1; for teams of
+    // 2 and 4 inside the composite-inertia loop above, each lane keeping the
+    // g_0i of its own links i = r mod P); lane r forms s_i and F_i for its links
+    // (F_i over h_i). The base-frame terms grow with the distance from the base
+    // and cancel in the pairing, which costs digits in proportion: FP64 only
+    // (with joint transforms rounded to FP32, the mixed mode's entries would
+    // lose about two digits).
     SE3<TA> g0;
     se3_identity(g0);
-    for (int i = 0; i < n; ++i) {
-      SE3<TA> gi;
-      load_g(i, gi);
-      SE3<TA> t;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-          t.R[3 * a + b] = (g0.R[3 * a] * gi.R[b] + g0.R[3 * a + 1] * gi.R[3 + b]) +
-                           g0.R[3 * a + 2] * gi.R[6 + b];
-        t.p[a] = ((g0.p[a] + g0.R[3 * a] * gi.p[0]) + g0.R[3 * a + 1] * gi.p[1]) +
-                 g0.R[3 * a + 2] * gi.p[2];
+    for (int i = (P == 1 ? 0 : tm.r); i < n; i += (P == 1 ? 1 : P)) {
+      if constexpr (P == 1) {
+        SE3<TA> gi, t;
+        load_g(i, gi);
+        se3_mul(g0, gi, t);
+        g0 = t;
+      } else {
+        ld_se3(pb.wt + static_cast<int64_t>(i) * NT + W_V, g0);
       }
-      g0 = t;
-      if ((i & (P - 1)) == tm.r) {
+      {
         const TA ax = g0.R[0], ay = g0.R[3], az = g0.R[6];  // R_0i e_1
         TA *sv = Sb + static_cast<int64_t>(i) * 6;
         sv[0] = ax;
